@@ -1,0 +1,322 @@
+"""Benchmark of the FR hot path on one (or N independent) GB300.
+
+Workload: the 3D Navier-Stokes Taylor-Green vortex, Re 1600, Ma 0.1, periodic
+[0, 2 pi]^3 with 32^3 hexahedra at uniform p = 3 (10,485,760 DOF).  One step
+is one pass of the hot path over that state:
+  R(q^n) in FP64 (explicit first ESDIRK stage), the spectral-decay indicator
+  and p-adaptation with rebucketing (degree range fixed at 3 for this
+  workload), then ESDIRK3 stage 2 (dt = 0.01) solved to ||F|| <= 1e-8 ||F0||
+  by pseudo-transient continuation with restarted GMRES(30), FP32 exact JVP,
+  FP64 F, Arnoldi and updates.
+value: residual/JVP DOF-evaluations per second over the whole step
+(N_dof x number of FP64 residuals and FP32 JVPs evaluated / step time),
+summed over ranks; ms_per_step is the GMRES time per ESDIRK stage.
+Ranks (torchrun, N > 1) run independent replicas: no collective on the path.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "residual/JVP GDOF/s (% HBM roofline); GMRES time per ESDIRK stage to 1e-8"
+WORKLOAD = "tgv_ns_32^3_p3"
+DT = 0.01
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1910_03693_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if the
+    kernels have not changed since it was captured."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+        if t.get("csrc_hash") != _csrc_hash():
+            return None
+        v = t.get("kernels", {}).get(kernel)
+        return None if v is None else float(v)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def build_workload(n=32, p=3):
+    import cases
+    m, q, ph = cases.workload_tgv(n, p)
+    return m, q, ph
+
+
+def oracle_sample_throughput(n, reps=1):
+    """The FP64 CPU oracle as it stands: one residual + one exact JVP of the
+    Taylor-Green workload at n^3 elements (p = 3); returns (GDOF/s, threads, seconds)."""
+    import torch
+
+    import cases
+    from oracle import linearize as L
+    from oracle.fr import FR
+    from oracle.physics import Euler
+    m, q, ph = cases.workload_tgv(n, 3)
+    fr = FR(m, Euler(3, ph["gamma"], ph["mu"], ph["Pr"]))
+    q = torch.from_numpy(q)
+    v = torch.from_numpy(cases.uniform(17, q.numel()) - 0.5)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fr.residual(q)
+        L.jvp(fr, q, v)
+    dt = time.perf_counter() - t0
+    return 2 * reps * q.numel() / dt / 1e9, torch.get_num_threads(), dt
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, bounded samples."""
+    if rank != 0:
+        return 0
+    import torch
+    n = 8   # 8^3 elements at p = 3 (1/64 of the workload) per step
+    for _ in range(args.warmup):
+        oracle_sample_throughput(n)
+    t0 = time.perf_counter()
+    tot = 0.0
+    for _ in range(args.steps):
+        g, thr, dt = oracle_sample_throughput(n)
+        tot += dt
+    ndof = 5 * 64 * n ** 3
+    value = 2 * ndof * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"tgv 8^3 p3 ({ndof} DOF): one FP64 residual + one exact JVP per step"},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": f"FP64 oracle residual + exact JVP on tgv 8^3 p3 ({ndof} DOF) per step"},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=32, help="elements per direction (default: the workload's 32)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1910_03693_gb300 import FRContext, esdirk_tableau
+    tab, _ = esdirk_tableau(3)
+
+    m, q, ph = build_workload(args.n, 3)
+    ctx = FRContext(m, gamma=ph["gamma"], mu=ph["mu"], Pr=ph["Pr"], p_min=3, p_max=3)
+    N = ctx.n_dof
+    qn_host = torch.from_numpy(q).pin_memory()
+    qn = torch.empty(ctx.n_dof_capacity, dtype=torch.float64, device="cuda")
+    ctx.pack(qn_host.cuda(), out=qn[:N])
+    qi = torch.empty(N, dtype=torch.float64, device="cuda")
+    R1 = torch.empty_like(qi)
+    R2 = torch.empty_like(qi)
+    eta = torch.empty(ctx.n_elem, dtype=torch.float64, device="cuda")
+    eta_max = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    opts = dict(tol=1e-8, dtau_init=DT / 10, dtau_max=DT, mode="exact", jv_dtype=torch.float32,
+                m=30, rtol=0.1, max_it=100)
+
+    def step(q_in):
+        ctx.indicator(q_in[:N], var=1, eta=eta, eta_max=eta_max)
+        ctx.rebucket(eta, eta_max, q_in, nu_max=0.1, nu_min=0.001, p_min=3, p_max=3)
+        ctx.residual(q_in[:N], out=R1)
+        qi.copy_(q_in[:N])
+        return ctx.esdirk_stage(tab, 2, DT, q_in[:N], [R1, R2, None, None], qi, **opts)
+
+    for _ in range(args.warmup):
+        st = step(qn)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each, events on the launch stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.timing(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    total_ms = 0.0
+    stats = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(step(qn))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    report, launches = ctx.timing_report()
+    ctx.timing(False)
+    clocks = sampler.stop()
+
+    n_evals = sum(v[0] for k, v in report.items() if k.startswith("vol_res") or k.startswith("vol_jvp"))
+    units = N * n_evals                       # DOF-evaluations over the K steps on this rank
+    t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, units = float(tmax[0]), float(tsum[1])
+    value = units / (total_ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    peak, peak_kind = _peaks()
+    kern = max(report, key=lambda k: report[k][1])
+    cnt, ms, nbytes = report[kern]
+    achieved = (nbytes / cnt) / (ms / cnt / 1e3) / 1e9 if nbytes > 0 else 0.0
+    roof = {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": _traffic_for(kern), "peak_source": peak_kind,
+            "share_of_step": ms / total_ms}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4),
+                   "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 and v[2] > 0 else None}
+               for k, v in sorted(report.items(), key=lambda kv: -kv[1][1])}
+
+    # end to end through the public API: host canonical state in, host state out
+    out_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    evals_e2e = 0
+    for _ in range(args.steps):
+        ctx.pack(qn_host.cuda(non_blocking=True), out=qn[:N])
+        step(qn)
+        out_host.copy_(ctx.unpack(qi), non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": (N * n_evals * max(world, 1)) / (e2e_ms / 1e3) / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 JVP + f64 F/Arnoldi/update",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.n == 32 else f"tgv_ns_{args.n}^3_p3", "n_dof": N,
+                   "dt": DT, "tableau": "ESDIRK3 stage 2", "gmres": "GMRES(30), rtol 0.1, <= 100 it",
+                   "jvp": "exact FP32", "tol": 1e-8, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "stage": {"newton": [s["newton"] for s in stats], "gmres": [s["gmres"] for s in stats],
+                  "converged": all(s["converged"] for s in stats),
+                  "rel_final": [s["norm_final"] / s["norm0"] for s in stats]},
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, thr, dt = oracle_sample_throughput(args.n)
+        line["cpu_baseline"] = {"value": g, "unit": "GDOF/s", "cores": thr, "kind": "oracle",
+                                "sample": f"one FP64 residual + one exact JVP of the full workload ({N} DOF), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

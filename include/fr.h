@@ -1,0 +1,260 @@
+/*
+ * fr.h - C ABI of the GB300 flux-reconstruction hot path.
+ *
+ * The library evaluates the flux reconstruction (FR) residual of the
+ * compressible Euler / Navier-Stokes equations on quadrilateral (2D) or
+ * hexahedral (3D) elements of mixed polynomial degree p, its exact
+ * linearisation (JVP) and transpose (VJP), the paper's finite-difference
+ * Jacobian-vector product, restarted GMRES on (sigma I - dR/dq), one ESDIRK
+ * stage by pseudo-transient continuation, the spectral-decay smoothness
+ * indicator and the p-adaptation that reorders elements into per-degree
+ * buckets.  The method is that of Wang, Gobbert & Yu, "A dynamically
+ * load-balanced parallel p-adaptive implicit high-order flux reconstruction
+ * method for under-resolved turbulence simulation" (arXiv:1910.03693):
+ * Sec. 2.1 (equations), Sec. 2.2 (FR/CPR), Sec. 2.3 (ESDIRK, pseudo-transient
+ * continuation, matrix-free GMRES), Sec. 3.1 (p-adaptation).
+ *
+ * Conventions common to every call
+ *  - Pointers named *_dev are device pointers; *_host are host pointers.
+ *    Every device buffer passed in is owned by the caller and must stay valid
+ *    until the work queued on `stream` has finished.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *    only queue kernels return as soon as the work is queued; calls that must
+ *    read a device value to decide (gmres_solve, esdirk_stage, p_rebucket)
+ *    synchronise `stream`.
+ *  - Errors are returned as fr_status, never thrown.  After FR_ERR_CUDA the
+ *    context may be unusable; fr_last_error() gives a message.
+ *  - "State layout" (internal): elements are stored in per-degree buckets in
+ *    ascending (p, element id) order; inside an element the block is
+ *    [nv][n_sp] with the solution point index xi-fastest.  fr_pack/fr_unpack
+ *    convert from/to the canonical layout: element by element in id order,
+ *    n_sp(p_e) = (p_e+1)^nd points (xi fastest) times nv variables (variable
+ *    fastest), FP64.  nv = nd + 2: (rho, rho u_i, rho E).
+ *  - Precision: FR_F64 buffers are double, FR_F32 buffers are float.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FR_OK = 0,
+  FR_ERR_INVALID = -1,        /* bad argument (sizes, pointers, degrees)          */
+  FR_ERR_CUDA = -2,           /* a CUDA call failed                               */
+  FR_ERR_NOMEM = -3,          /* device or host allocation failed                 */
+  FR_ERR_NOT_CONVERGED = -4,  /* a solver hit its iteration limit                 */
+  FR_ERR_NONFINITE = -5,      /* NaN or Inf met in a norm                         */
+  FR_ERR_TIMEOUT = -6         /* a bounded device-side wait gave up               */
+} fr_status;
+
+typedef enum { FR_F64 = 0, FR_F32 = 1 } fr_prec;
+typedef enum { FR_JV_FD = 0, FR_JV_EXACT = 1 } fr_jv_mode;
+
+/* Boundary kinds used in fr_mesh_desc.nbr (negative values). */
+#define FR_BC_WALL (-1)      /* no-slip adiabatic wall            */
+#define FR_BC_FARFIELD (-2)  /* free-stream ghost state           */
+
+/*
+ * Mesh description (host arrays, read during fr_create only).
+ *  nodes    [n_elem][(geom_order+1)^nd][nd]: element map nodes at equispaced
+ *           reference points, xi fastest.  geom_order is 1 or 2.
+ *  nbr      [n_elem][2 nd]: neighbour element through face f = 2 d + s
+ *           (d = reference direction, s = 0 at xi_d = -1, 1 at +1), or a
+ *           FR_BC_* value.
+ *  nbr_face [n_elem][2 nd]: the neighbour's face index (ignored on boundaries).
+ *  orient   [n_elem][2 nd]: maps this side's face point (ia, ib) to the
+ *           neighbour's: bit 0 swaps the axes, then bit 1 flips the first
+ *           (i -> P-1-i), bit 2 the second.  Must be the inverse of the
+ *           neighbour's code.
+ *  p        [n_elem]: initial degree of each element, p_min <= p <= p_max.
+ */
+typedef struct {
+  int32_t nd;
+  int32_t n_elem;
+  int32_t geom_order;
+  const double* nodes;
+  const int32_t* nbr;
+  const int8_t* nbr_face;
+  const int8_t* orient;
+  const int8_t* p;
+} fr_mesh_desc;
+
+/* Physics (Sec. 2.1): gamma, constant mu (0 = Euler) and Pr; q_inf is the
+ * conservative free-stream state used by far-field boundaries (nv values). */
+typedef struct {
+  double gamma;
+  double mu;
+  double Pr;
+  double q_inf[5];
+} fr_physics;
+
+/* Degree range of the context.  1 <= p_min <= p_max <= 5.  Every buffer the
+ * context owns is sized for all elements at p_max, so adaptation never
+ * reallocates. */
+typedef struct {
+  int32_t p_min;
+  int32_t p_max;
+} fr_limits;
+
+typedef struct fr_ctx fr_ctx;
+
+/* Current layout.  n_dof = nv * sum_e n_sp(p_e); n_dof_capacity is the
+ * value at p_max everywhere; bucket_count[p] is the number of elements of
+ * degree p (p = 0..5) and bucket_offset[p] the first value of that bucket in
+ * the state layout. */
+typedef struct {
+  int32_t nd, nv, n_elem;
+  int64_t n_dof;
+  int64_t n_dof_capacity;
+  int32_t bucket_count[6];
+  int64_t bucket_offset[6];
+  int32_t affine;           /* 1 if every element map is affine (constant metrics) */
+} fr_layout_info;
+
+/* Create a context: computes metric terms for every degree in [p_min, p_max],
+ * the per-degree buckets and the face lists.  Device memory is allocated on
+ * the current device.  Returns FR_ERR_INVALID on inconsistent connectivity or
+ * degrees out of range. */
+fr_status fr_create(const fr_mesh_desc* mesh, const fr_physics* phys, const fr_limits* lim,
+                    fr_ctx** out);
+fr_status fr_destroy(fr_ctx* ctx);
+fr_status fr_layout(const fr_ctx* ctx, fr_layout_info* info);
+/* Current degree of every element (host array of n_elem). */
+fr_status fr_get_p(const fr_ctx* ctx, int8_t* p_host);
+const char* fr_last_error(void);
+
+/* Canonical FP64 (device) <-> state layout in `prec`. */
+fr_status fr_pack(fr_ctx* ctx, const double* canon_dev, void* q_dev, fr_prec prec, void* stream);
+fr_status fr_unpack(fr_ctx* ctx, const void* q_dev, fr_prec prec, double* canon_dev, void* stream);
+
+/* R = R(q) = -div f, Sec. 2.2 Eq. (FR_diff) with Rusanov common inviscid
+ * flux, common solution Eq. (com_q) and BR2-type common gradient
+ * Eq. (com_grad_q).  q and R are state-layout device buffers of n_dof. */
+fr_status fr_residual(fr_ctx* ctx, const void* q_dev, void* R_dev, fr_prec prec, void* stream);
+
+/* Jv ~ dR(q)/dq v.  FR_JV_EXACT: the exact directional derivative.
+ * FR_JV_FD: the paper's one-sided difference (R(q + eps v) - R(q)) / eps
+ * (Sec. 2.3), FP64 only; R(q) is evaluated inside. */
+fr_status fr_jvp(fr_ctx* ctx, const void* q_dev, const void* v_dev, void* Jv_dev, fr_prec prec,
+                 fr_jv_mode mode, double eps, void* stream);
+
+/* JTw = (dR(q)/dq)^T w, the exact transpose of FR_JV_EXACT. */
+fr_status fr_vjp(fr_ctx* ctx, const void* q_dev, const void* w_dev, void* JTw_dev, fr_prec prec,
+                 void* stream);
+
+/* Linear operator A x = sigma x - J(q) x of the pseudo-transient Newton step
+ * (Sec. 2.3, Eq. linearized_pseudo_transient_final).  q64_dev is the FP64
+ * state; when jv_prec is FR_F32 the exact JVP runs in FP32 on a rounded copy. */
+typedef struct {
+  double sigma;
+  const double* q64_dev;
+  fr_jv_mode mode;
+  fr_prec jv_prec;
+  double eps;              /* FD step (FR_JV_FD), paper: 1e-6 */
+} fr_shifted_op;
+
+typedef struct {
+  int32_t m;               /* restart length (paper: 60; hot path: 30)      */
+  double rtol;             /* relative tolerance (paper: 1e-1)              */
+  int32_t max_it;          /* total iterations (paper: 100)                 */
+} fr_gmres_opts;
+
+typedef struct {
+  int32_t iterations;
+  int32_t restarts;
+  int32_t converged;
+  double rel_res;
+} fr_gmres_stats;
+
+/* Restarted GMRES(m) from x = 0 in FP64 (classical Gram-Schmidt with
+ * re-orthogonalisation, Givens rotations).  b, x: device FP64, n_dof. */
+fr_status gmres_solve(fr_ctx* ctx, const fr_shifted_op* op, const double* b_dev, double* x_dev,
+                      const fr_gmres_opts* opts, fr_gmres_stats* stats, void* stream);
+
+/* ESDIRK tableau (row-major s x s matrix A, weights b). */
+typedef struct {
+  int32_t s;
+  double A[36];
+  double b[6];
+} fr_tableau;
+
+typedef struct {
+  double tol;              /* ||F|| / ||F(q^{0})|| to reach (hot path: 1e-8)  */
+  double dtau_init, dtau_max;
+  int32_t max_newton;
+  int32_t max_halvings;
+  fr_jv_mode mode;         /* FD (FP64) or exact                             */
+  fr_prec jv_prec;         /* precision of the exact JVP                      */
+  double eps;
+  fr_gmres_opts gmres;
+} fr_newton_opts;
+
+typedef struct {
+  int32_t newton_iterations;
+  int32_t gmres_iterations;
+  int32_t halvings;
+  int32_t converged;
+  double norm0, norm_final;
+} fr_stage_stats;
+
+/* ESDIRK tableaus (Sec. 2.3; the paper cites them but prints no
+ * coefficients).  order 2: three stages, stiffly accurate, L-stable, diagonal
+ * 1 - sqrt(2)/2, c = (0, 2g, 1).  order 3: four stages, explicit first stage,
+ * stiffly accurate, diagonal g the root near 0.4359 of 6g^3 - 18g^2 + 9g - 1
+ * (stability function zero at infinity), c = (0, 2g, 0.6, 1), remaining
+ * coefficients from the order-3 conditions.  FR_ERR_INVALID for other orders. */
+fr_status fr_esdirk_tableau(int32_t order, fr_tableau* out);
+
+/* Solve stage `stage` (1-based like the paper, 2..s) of one ESDIRK step
+ * (Eq. ESDIRK_conservative) by pseudo-transient continuation with SER
+ * (Eqs. pseudo_transient, ser).  qn: q^n; Rstages[j] = R(q^{j+1}) for
+ * j < stage-1 (inputs); qi: in = initial guess, out = q^stage; on return
+ * Rstages[stage-1] (if non-NULL) holds R(q^stage).  All FP64 device buffers
+ * of n_dof in state layout. */
+fr_status esdirk_stage(fr_ctx* ctx, const fr_tableau* tab, int32_t stage, double dt,
+                       const double* qn_dev, double* const* Rstages_dev, double* qi_dev,
+                       const fr_newton_opts* opts, fr_stage_stats* stats, void* stream);
+
+/* Spectral decay indicator (Sec. 3.1): eta_e for variable `var` (paper: 1 =
+ * rho u) and the maximum over elements.  eta_dev: n_elem doubles in element
+ * id order; eta_max_dev: one double.  Deterministic (fixed summation order). */
+fr_status spectral_decay_indicator(fr_ctx* ctx, const void* q_dev, fr_prec prec, int32_t var,
+                                   double* eta_dev, double* eta_max_dev, void* stream);
+
+typedef struct {
+  double nu_max, nu_min;   /* paper: 0.1, 0.001                              */
+  int32_t p_min, p_max;    /* within the context's limits                     */
+} fr_adapt_opts;
+
+/* p-adaptation (Sec. 3.1): decide p from eta, limit neighbour jumps to one
+ * (raise-only fixed point), prolong / project every element's state, and
+ * reorder elements into (p, id) buckets, replacing the paper's repartition.
+ * q_inout is a state-layout buffer of n_dof_capacity values; on return it
+ * holds the state in the new layout.  perm_out (device, optional) receives
+ * the element id at each new bucket position. */
+fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_dev,
+                     const fr_adapt_opts* opts, void* q_inout_dev, fr_prec prec,
+                     int32_t* perm_out_dev, void* stream);
+
+/* Instrumentation (the paper has no counterpart: measurement support).
+ * fr_timing(ctx, 1) synchronises the device, clears the counters and starts
+ * recording a pair of CUDA events on the launch stream around every kernel
+ * the library launches; fr_timing(ctx, 0) stops recording.  The launch
+ * counter runs in both states.  fr_timing_report synchronises the device and
+ * writes one line per kernel, "name launches total_ms algorithmic_bytes" (the
+ * minimum bytes the launches had to move, as counted by each launch site), into buf (len bytes,
+ * FR_ERR_INVALID if too small) and the number of launches since the last
+ * fr_timing call into *launches (optional). */
+fr_status fr_timing(fr_ctx* ctx, int32_t enable);
+fr_status fr_timing_report(fr_ctx* ctx, char* buf, int64_t len, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FR_H */

@@ -45,17 +45,22 @@ class Euler:
         return torch.stack(rows, dim=1)
 
     def wave_speed(self, q, n):
-        """|u.n| + c for unit normals ``n [N, nd, ...]``."""
+        """|u.n| + c for unit normals ``n [N, nd, ...]``.  |x| is written as the
+        branch x < 0 ? -x : x, so its derivative at x = 0 is +1 (reading)."""
         rho, vel, pres = self.primitives(q)
         c = torch.sqrt(self.gamma * pres / rho)
-        return torch.abs((vel * n).sum(1)) + c
+        un = (vel * n).sum(1)
+        return torch.where(un < 0, -un, un) + c
 
     def rusanov(self, qL, qR, n):
         """Rusanov (local Lax-Friedrichs) normal flux: average of the two normal
-        fluxes minus half the largest |u.n|+c times the jump qR - qL."""
+        fluxes minus half the largest |u.n|+c times the jump qR - qL.  The
+        maximum is the branch lamR > lamL ? lamR : lamL, so at a tie the
+        derivative follows the "-" side (reading)."""
         fL = (self.flux(qL) * n[:, :, None]).sum(1)
         fR = (self.flux(qR) * n[:, :, None]).sum(1)
-        lam = torch.maximum(self.wave_speed(qL, n), self.wave_speed(qR, n))
+        lamL, lamR = self.wave_speed(qL, n), self.wave_speed(qR, n)
+        lam = torch.where(lamR > lamL, lamR, lamL)
         return 0.5 * (fL + fR) - 0.5 * lam[:, None] * (qR - qL)
 
     # -- viscous --------------------------------------------------------------

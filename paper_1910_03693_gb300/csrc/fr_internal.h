@@ -1,0 +1,169 @@
+// Internal declarations of the GB300 FR library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fr.h"
+#include "timing.h"
+
+namespace frgb {
+
+constexpr int kMaxDeg = 5;   // highest polynomial degree supported
+constexpr int kPM = 6;       // most solution points per direction (kMaxDeg + 1)
+
+// 1D operators of one degree (P = p + 1 Gauss-Legendre points), Sec. 2.2.
+template <typename T>
+struct BasisTab {
+  T x[kPM], w[kPM];
+  T D[kPM][kPM];        // D[i][k] = l_k'(x_i)
+  T ext[2][kPM];        // l_k(-1), l_k(+1)
+  T dext[2][kPM];       // l_k'(-1), l_k'(+1)
+  T dg[2][kPM];         // g_L'(x_i), g_R'(x_i) of the DG (Radau) correction functions
+  T dgf[2];             // g_L'(-1) = -(p+1)^2/2, g_R'(+1) = (p+1)^2/2
+  T modal[kPM][kPM];    // Legendre coefficients c_m = sum_i modal[m][i] s_i
+  T nodal[kPM][kPM];    // s_i = sum_m nodal[i][m] c_m  (nodal[i][m] = P_m(x_i))
+};
+
+// Mortar operators from Ps slave points to Pm mortar points and back.
+template <typename T>
+struct MortarTab {
+  T I[kPM][kPM];        // I[m][a] = l_a^{slave}(x_m^{mortar})
+  T Pi[kPM][kPM];       // Pi[a][m] = w_m l_a(x_m) / w_a  (L2 projection)
+};
+
+// Host construction of the tables (basis.cpp).
+void build_basis(int p, BasisTab<double>& t);
+void build_mortar(int ps, int pm, MortarTab<double>& t);
+void lagrange_eval(const double* xs, int n, double x, double* out);
+void lagrange_deriv_eval(const double* xs, int n, double x, double* out);
+void gauss_legendre(int P, double* x, double* w);
+double legendre_p(int n, double x);
+
+// Face records.  Offsets are absolute element-face block starts in the
+// trace (t) and face-output (o) workspaces.
+struct FaceRec {
+  int64_t mt, st, mo, so;
+  int32_t me, se;      // element ids (geometry lookup)
+  int32_t mf, sf;      // face indices
+  int32_t orient, idx; // master's orientation code; index of the face in its group
+};
+struct BndRec {
+  int64_t mt, mo;
+  int32_t me, mf;
+};
+
+// Strided view of metric terms S[d][j] (k = d*nd + j) and |J| (k = nd*nd).
+template <typename T>
+struct GeoView {
+  const T* vol;         // value(e, k, sp) = vol[e*ves + k*vks + sp*vps]
+  int64_t ves;
+  int32_t vks, vps;
+  const T* face;        // value(e, f, k, t) = face[e*fes + f*ffs + k*fks + t*fps]
+  int64_t fes;
+  int32_t ffs, fks, fps;
+};
+
+struct Bucket {
+  int p = 0, count = 0, slot_begin = 0;
+  int64_t state_base = 0;   // values
+  int64_t trace_base = 0;   // values
+  int64_t out_base = 0;     // values
+};
+
+struct FaceGroup {
+  int pm = 0, ps = 0, n = 0;
+  FaceRec* d_recs = nullptr;
+  int64_t scratch_base = 0; // values, mixed-degree groups only
+};
+struct BndGroup {
+  int p = 0, kind = 0, n = 0;
+  BndRec* d_recs = nullptr;
+};
+
+struct PhysParams {
+  double gamma, mu, Pr, kappa;
+  double q_inf[5];
+};
+
+}  // namespace frgb
+
+struct fr_ctx {
+  int nd = 0, nv = 0, nf = 0, E = 0, geom_order = 1, p_min = 1, p_max = 1;
+  bool affine = false, visc = false;
+  frgb::PhysParams phys{};
+  int device = 0;
+  // host mesh
+  std::vector<double> nodes;
+  std::vector<int32_t> nbr;
+  std::vector<int8_t> nbr_face, orient, p;
+  // tables (device)
+  frgb::BasisTab<double>* d_basis64 = nullptr;   // [kPM + 1], indexed by P
+  frgb::BasisTab<float>* d_basis32 = nullptr;
+  frgb::MortarTab<double>* d_mortar64 = nullptr; // [(kPM+1)*(kPM+1)], index Pm*(kPM+1)+Ps
+  frgb::MortarTab<float>* d_mortar32 = nullptr;
+  // geometry (device): affine -> per element constants; else per degree
+  double* d_gaff64 = nullptr;
+  float* d_gaff32 = nullptr;
+  double* d_gvol64[frgb::kMaxDeg + 1] = {};
+  float* d_gvol32[frgb::kMaxDeg + 1] = {};
+  double* d_gface64[frgb::kMaxDeg + 1] = {};
+  float* d_gface32[frgb::kMaxDeg + 1] = {};
+  // layout
+  std::vector<frgb::Bucket> buckets;     // one per degree present, ascending p
+  std::vector<int32_t> slot_elem;        // bucket position -> element id
+  int64_t n_dof = 0, n_dof_cap = 0;
+  int32_t* d_slot_elem = nullptr;        // [E]
+  int64_t* d_canon_off = nullptr;        // [E] canonical offset of the element at each slot
+  int64_t* d_state_off = nullptr;        // [E] state offset of the element at each slot
+  int8_t* d_slot_p = nullptr;            // [E] degree at each slot
+  int32_t* d_elem_slot = nullptr;        // [E] slot of each element
+  // workspaces (bytes sized for FP64 at capacity)
+  int nvt = 0;                           // trace components per face point
+  int64_t trace_cap = 0, fout_cap = 0, scratch_cap = 0;
+  void* d_trace_q = nullptr;
+  void* d_trace_v = nullptr;
+  void* d_fout = nullptr;
+  void* d_scratch = nullptr;
+  void* d_fbar = nullptr;                // VJP: adjoints of the face outputs
+  void* d_trbar = nullptr;               // VJP: adjoints of the traces
+  // faces
+  std::vector<frgb::FaceGroup> fgroups;
+  std::vector<frgb::BndGroup> bgroups;
+  int32_t* d_nbr = nullptr;              // [E][nf] for the adaptation smoother
+  // solver workspaces (lazily allocated)
+  double* d_krylov = nullptr;            // (m+1) * n_dof_cap basis
+  int krylov_m = 0;
+  double* d_vec64[12] = {};   // 0-2 FD Jv, 3 Jv, 4-5 GMRES, 6-9 ESDIRK, 10-11 adaptation
+  float* d_vec32[4] = {};
+  double* d_red = nullptr;               // reduction scratch
+  int64_t red_cap = 0;
+  double* h_red = nullptr;               // pinned host mirror
+  frgb::Timing timing;                   // launch counter and optional per-kernel events
+  // adaptation workspaces (lazily allocated)
+  double* d_xfer = nullptr;              // prolongation / projection matrices [Po][Pn][6][6]
+  int* d_adapt_i32 = nullptr;
+  int8_t* d_adapt_i8 = nullptr;
+  double* d_adapt_f64 = nullptr;
+  int64_t* d_old_state_off = nullptr;
+  int64_t* d_new_state_off = nullptr;
+  int32_t* d_old_elem_slot = nullptr;
+  int8_t* d_old_slot_p = nullptr;
+  int* h_flag = nullptr;
+};
+
+namespace frgb {
+// launchers (kernels_*.cu)
+fr_status launch_residual(fr_ctx* c, const void* q, void* R, fr_prec prec, cudaStream_t s);
+fr_status launch_jvp_exact(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec,
+                           cudaStream_t s);
+fr_status launch_vjp(fr_ctx* c, const void* q, const void* w, void* JTw, fr_prec prec,
+                     cudaStream_t s);
+fr_status launch_pack(fr_ctx* c, const double* canon, void* q, fr_prec prec, bool unpack,
+                      cudaStream_t s);
+void set_error(const std::string& msg);
+fr_status cuda_check(cudaError_t e, const char* what);
+}  // namespace frgb

@@ -1,0 +1,650 @@
+// Device kernels of the FR residual and its exact JVP (Sec. 2.2).
+//
+// Data layout (all buckets share it; P = p+1, NSP = P^ND, NFP = P^(ND-1)):
+//   state   [element][var][sp]                 sp = i0 + P*i1 + P*P*i2 (xi fastest)
+//   trace   [element][face][comp][fp]          comp < NV: q at the face point;
+//                                              NV + j*NV + v: physical gradient d_j q_v
+//   fout    [element][face][comp][fp]          comp < NV: common transformed flux
+//                                              F~_d^com; NV..2NV-1: dq = q^com - q;
+//                                              (JVP: 0..NV-1 tangent F~^com, NV.. primal
+//                                              dq, 2NV.. tangent dq)
+// Face point fp = ia + P*ib, (ia, ib) the tangential directions in increasing
+// order.  Element-face blocks have fixed strides (NVT*NFP and 3*NV*NFP values).
+#pragma once
+
+#include "fr_internal.h"
+#include "physics.cuh"
+
+namespace frgb {
+
+template <int ND, int P>
+struct Shape {
+  static constexpr int NV = ND + 2;
+  static constexpr int NF = 2 * ND;
+  static constexpr int NSP = ND == 2 ? P * P : P * P * P;
+  static constexpr int NFP = ND == 2 ? P : P * P;
+};
+
+// solution point index on face (d, s) line: given face point t and position k along d
+template <int ND, int P>
+__device__ __forceinline__ int line_sp(int d, int t, int k) {
+  if (ND == 2) {
+    return d == 0 ? (k + P * t) : (t + P * k);
+  } else {
+    int a = t % P, b = t / P;
+    if (d == 0) return k + P * (a + P * b);
+    if (d == 1) return a + P * (k + P * b);
+    return a + P * (b + P * k);
+  }
+}
+
+// face point index (face direction d) of a solution point with indices i[]
+template <int ND, int P>
+__device__ __forceinline__ int face_pt(int d, const int* i) {
+  if (ND == 2) return d == 0 ? i[1] : i[0];
+  if (d == 0) return i[1] + P * i[2];
+  if (d == 1) return i[0] + P * i[2];
+  return i[0] + P * i[1];
+}
+
+// runtime versions for the face kernels
+__device__ __forceinline__ int orient_map(int code, int t, int P, int nd) {
+  int u, v;
+  if (nd == 2) {
+    u = t;
+    v = 0;
+  } else {
+    int ia = t % P, ib = t / P;
+    if (code & 1) {
+      u = ib;
+      v = ia;
+    } else {
+      u = ia;
+      v = ib;
+    }
+  }
+  if (code & 2) u = P - 1 - u;
+  if ((code & 4) && nd == 3) v = P - 1 - v;
+  return u + P * v;
+}
+__device__ __forceinline__ int orient_inv(int code, int uu, int P, int nd) {
+  int u = uu % P, v = uu / P;
+  if (nd == 2) v = 0;
+  if (code & 2) u = P - 1 - u;
+  if ((code & 4) && nd == 3) v = P - 1 - v;
+  int ia, ib;
+  if (nd == 3 && (code & 1)) {
+    ia = v;
+    ib = u;
+  } else {
+    ia = u;
+    ib = v;
+  }
+  return ia + P * ib;
+}
+
+template <typename T>
+__device__ __forceinline__ T geo_vol(const GeoView<T>& g, int64_t e, int k, int sp) {
+  return g.vol[e * g.ves + (int64_t)k * g.vks + (int64_t)sp * g.vps];
+}
+template <typename T>
+__device__ __forceinline__ T geo_face(const GeoView<T>& g, int64_t e, int f, int k, int t) {
+  return g.face[e * g.fes + (int64_t)f * g.ffs + (int64_t)k * g.fks + (int64_t)t * g.fps];
+}
+
+// ---------------------------------------------------------------------------
+// Trace kernel: q (and for NS the physical gradient) at every face point.
+// One thread per (element, face, face point).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct TraceArgs {
+  const T* q;
+  T* trace;
+  const int32_t* slot_elem;
+  const BasisTab<T>* basis;
+  GeoView<T> geo;
+  int64_t state_base, trace_base;
+  int count, slot_begin, nvt;
+};
+
+template <typename T, int ND, int P, bool VISC>
+__global__ void __launch_bounds__(256) trace_kernel(TraceArgs<T> a) {
+  using Sh = Shape<ND, P>;
+  constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)a.count * NF * NFP;
+  if (gid >= total) return;
+  const int t = (int)(gid % NFP);
+  const int f = (int)((gid / NFP) % NF);
+  const int64_t i = gid / (NFP * NF);
+  const int d = f >> 1, s = f & 1;
+  const BasisTab<T>& B = a.basis[P];
+  const T* qe = a.q + a.state_base + i * NV * NSP;
+  T* out = a.trace + a.trace_base + (i * NF + f) * (int64_t)a.nvt * NFP;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < P; ++k) acc += B.ext[s][k] * qe[v * NSP + line_sp<ND, P>(d, t, k)];
+    out[v * NFP + t] = acc;
+  }
+  if (VISC) {
+    const int64_t e = a.slot_elem[a.slot_begin + i];
+    // reference derivatives at the face point: normal via l'(+-1), tangential by
+    // differentiating along d' at every line point, then extrapolating
+    T dq[ND][NV];
+    int ia = t % P, ib = t / P;   // tangential coordinates
+#pragma unroll
+    for (int dd = 0; dd < ND; ++dd) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T acc = T(0);
+        if (dd == d) {
+#pragma unroll
+          for (int k = 0; k < P; ++k) acc += B.dext[s][k] * qe[v * NSP + line_sp<ND, P>(d, t, k)];
+        } else {
+          // dd is the first (ia) or second (ib) tangential axis of face d
+          int which = 0;
+          if (ND == 3) which = (dd == (d == 0 ? 1 : 0)) ? 0 : 1;
+          const int coord = which == 0 ? ia : ib;
+#pragma unroll
+          for (int k = 0; k < P; ++k) {
+            T inner = T(0);
+#pragma unroll
+            for (int m = 0; m < P; ++m) {
+              int tt = (which == 0) ? (m + P * ib) : (ia + P * m);
+              if (ND == 2) tt = m;
+              inner += B.D[coord][m] * qe[v * NSP + line_sp<ND, P>(d, tt, k)];
+            }
+            acc += B.ext[s][k] * inner;
+          }
+        }
+        dq[dd][v] = acc;
+      }
+    }
+    const T Jf = geo_face(a.geo, e, f, ND * ND, t);
+#pragma unroll
+    for (int j = 0; j < ND; ++j)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T acc = T(0);
+#pragma unroll
+        for (int dd = 0; dd < ND; ++dd) acc += geo_face(a.geo, e, f, dd * ND + j, t) * dq[dd][v];
+        out[(NV + j * NV + v) * NFP + t] = acc / Jf;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Interior face kernel: common flux on the mortar (Pm points per direction).
+// One thread per (face, mortar point).  MODE 0: residual; 1: JVP.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FaceArgs {
+  const FaceRec* recs;
+  const T* trq;        // traces of q
+  const T* trv;        // traces of the tangent (JVP)
+  T* fout;
+  T* scratch;          // mixed-degree groups: [face][comp][NFPm]
+  const BasisTab<T>* basis;
+  const MortarTab<T>* mortar;   // Pm -> Ps tables (nullptr when Pm == Ps)
+  GeoView<T> geo_m, geo_s;
+  T gamma, mu, kappa;
+  int n, Pm, Ps, nvt;
+  int64_t scratch_base;
+};
+
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void load_trace_pt(const T* trq, const T* trv, int64_t base, int comp0,
+                                              int ncomp, int NFP, int t, S* out) {
+  for (int c = 0; c < ncomp; ++c) {
+    T v = trq[base + (int64_t)(comp0 + c) * NFP + t];
+    T dv = trv ? trv[base + (int64_t)(comp0 + c) * NFP + t] : T(0);
+    set_scalar(out[c], v, dv);
+  }
+}
+
+// value of the slave's trace component at mortar point u (slave axes, Pm grid)
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void slave_at_mortar(const FaceArgs<T>& a, int64_t base, int comp0,
+                                                int ncomp, int u, S* out) {
+  const int Ps = a.Ps, Pm = a.Pm;
+  const int NFPs = ND == 2 ? Ps : Ps * Ps;
+  if (Pm == Ps) {
+    load_trace_pt<ND>(a.trq, a.trv, base, comp0, ncomp, NFPs, u, out);
+    return;
+  }
+  const int ua = u % Pm, ub = ND == 2 ? 0 : u / Pm;
+  for (int c = 0; c < ncomp; ++c) set_scalar(out[c], T(0), T(0));
+  for (int bb = 0; bb < (ND == 2 ? 1 : Ps); ++bb) {
+    const T wb = ND == 2 ? T(1) : a.mortar->I[ub][bb];
+    for (int aa = 0; aa < Ps; ++aa) {
+      const T w = a.mortar->I[ua][aa] * wb;
+      const int pt = aa + Ps * bb;
+      for (int c = 0; c < ncomp; ++c) {
+        T v = a.trq[base + (int64_t)(comp0 + c) * NFPs + pt];
+        T dv = a.trv ? a.trv[base + (int64_t)(comp0 + c) * NFPs + pt] : T(0);
+        S x;
+        set_scalar(x, v, dv);
+        out[c] = out[c] + w * x;
+      }
+    }
+  }
+}
+
+template <int ND, typename T>
+__device__ __forceinline__ void slave_coef_at_mortar(const FaceArgs<T>& a, const FaceRec& r, int u,
+                                                     T* cS) {
+  // c = g_s'(face) S_d[j] / |J| at the slave's own points, interpolated to the mortar
+  const int Ps = a.Ps, Pm = a.Pm;
+  const int ds = r.sf >> 1, ss = r.sf & 1;
+  const T g = a.basis[Ps].dgf[ss];
+  for (int j = 0; j < ND; ++j) cS[j] = T(0);
+  if (Pm == Ps) {
+    const T J = geo_face(a.geo_s, r.se, r.sf, ND * ND, u);
+    for (int j = 0; j < ND; ++j) cS[j] = g * geo_face(a.geo_s, r.se, r.sf, ds * ND + j, u) / J;
+    return;
+  }
+  const int ua = u % Pm, ub = ND == 2 ? 0 : u / Pm;
+  for (int bb = 0; bb < (ND == 2 ? 1 : Ps); ++bb) {
+    const T wb = ND == 2 ? T(1) : a.mortar->I[ub][bb];
+    for (int aa = 0; aa < Ps; ++aa) {
+      const T w = a.mortar->I[ua][aa] * wb;
+      const int pt = aa + Ps * bb;
+      const T J = geo_face(a.geo_s, r.se, r.sf, ND * ND, pt);
+      for (int j = 0; j < ND; ++j) cS[j] += w * (g * geo_face(a.geo_s, r.se, r.sf, ds * ND + j, pt) / J);
+    }
+  }
+}
+
+template <typename T, int ND, bool VISC, int MODE>
+__global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
+  constexpr int NV = ND + 2;
+  using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
+  const int Pm = a.Pm;
+  const int NFPm = ND == 2 ? Pm : Pm * Pm;
+  const int NFPs = ND == 2 ? a.Ps : a.Ps * a.Ps;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)a.n * NFPm) return;
+  const int t = (int)(gid % NFPm);
+  const FaceRec r = a.recs[gid / NFPm];
+  const int dm = r.mf >> 1, sm = r.mf & 1, ss = r.sf & 1;
+  const int u = orient_map(r.orient, t, Pm, ND);
+  const T* trv = MODE == 1 ? a.trv : nullptr;
+
+  S qM[NV], qS[NV];
+  load_trace_pt<ND>(a.trq, trv, r.mt, 0, NV, NFPm, t, qM);
+  {
+    FaceArgs<T> b = a;
+    b.trv = trv;
+    slave_at_mortar<ND>(b, r.st, 0, NV, u, qS);
+  }
+  T A[ND], n[ND];
+  T absA2 = T(0);
+  const T sgm = sm ? T(1) : T(-1);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    A[j] = sgm * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t);
+    absA2 += A[j] * A[j];
+  }
+  const T absA = sqrt(absA2);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) n[j] = A[j] / absA;
+  S Fn[NV];
+  rusanov<ND>(qM, qS, n, absA, a.gamma, Fn);
+  S qc[NV];
+  if (VISC) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qS[v]);
+    T cM[ND], cS[ND];
+    const T gM = a.basis[Pm].dgf[sm];
+    const T JM = geo_face(a.geo_m, r.me, r.mf, ND * ND, t);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) cM[j] = gM * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t) / JM;
+    slave_coef_at_mortar<ND>(a, r, u, cS);
+    S GM[ND][NV], GS[ND][NV], Gc[ND][NV];
+    load_trace_pt<ND>(a.trq, trv, r.mt, NV, ND * NV, NFPm, t, &GM[0][0]);
+    {
+      FaceArgs<T> b = a;
+      b.trv = trv;
+      slave_at_mortar<ND>(b, r.st, NV, ND * NV, u, &GS[0][0]);
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j)
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        Gc[j][v] = T(0.5) * (GM[j][v] + cM[j] * (qc[v] - qM[v]) + GS[j][v] + cS[j] * (qc[v] - qS[v]));
+    S fv[ND][NV];
+    flux_viscous<ND>(qc, Gc, a.gamma, a.mu, a.kappa, fv);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      S acc = szero<S>();
+#pragma unroll
+      for (int j = 0; j < ND; ++j) acc = acc + fv[j][v] * A[j];
+      Fn[v] = Fn[v] - acc;
+    }
+  }
+  // master side
+  T* om = a.fout + r.mo;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    S x = sgm * Fn[v];
+    om[v * NFPm + t] = MODE == 1 ? tangent(x) : value(x);
+    if (VISC) {
+      S dq = qc[v] - qM[v];
+      om[(NV + v) * NFPm + t] = value(dq);
+      if (MODE == 1) om[(2 * NV + v) * NFPm + t] = tangent(dq);
+    }
+  }
+  const T sgs = ss ? T(1) : T(-1);
+  if (Pm == a.Ps) {
+    T* os = a.fout + r.so;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      S x = sgs * (T(0) - Fn[v]);
+      os[v * NFPs + u] = MODE == 1 ? tangent(x) : value(x);
+      if (VISC) {
+        S dq = qc[v] - qS[v];
+        os[(NV + v) * NFPs + u] = value(dq);
+        if (MODE == 1) os[(2 * NV + v) * NFPs + u] = tangent(dq);
+      }
+    }
+  } else {
+    // mortar values (master order) for the projection kernel: -Fn, then q^com
+    T* sc = a.scratch + a.scratch_base + (int64_t)r.idx * 4 * NV * NFPm;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      S x = T(0) - Fn[v];
+      sc[v * NFPm + t] = MODE == 1 ? tangent(x) : value(x);
+      if (VISC) {
+        sc[(NV + v) * NFPm + t] = value(qc[v]);
+        if (MODE == 1) sc[(2 * NV + v) * NFPm + t] = tangent(qc[v]);
+      }
+    }
+  }
+}
+
+// L2 projection of the mortar values onto the lower-degree side.
+// One thread per (face, slave point).
+template <typename T, int ND, bool VISC, int MODE>
+__global__ void __launch_bounds__(128) mortar_project_kernel(FaceArgs<T> a) {
+  constexpr int NV = ND + 2;
+  const int Pm = a.Pm, Ps = a.Ps;
+  const int NFPm = ND == 2 ? Pm : Pm * Pm;
+  const int NFPs = ND == 2 ? Ps : Ps * Ps;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)a.n * NFPs) return;
+  const int pt = (int)(gid % NFPs);
+  const FaceRec r = a.recs[gid / NFPs];
+  const int ss = r.sf & 1;
+  const T sgs = ss ? T(1) : T(-1);
+  const int pa = pt % Ps, pb = ND == 2 ? 0 : pt / Ps;
+  const T* sc = a.scratch + a.scratch_base + (int64_t)r.idx * 4 * NV * NFPm;
+  const int ncomp = VISC ? (MODE == 1 ? 3 * NV : 2 * NV) : NV;
+  T acc[3 * NV];
+  for (int c = 0; c < ncomp; ++c) acc[c] = T(0);
+  for (int mb = 0; mb < (ND == 2 ? 1 : Pm); ++mb) {
+    const T wb = ND == 2 ? T(1) : a.mortar->Pi[pb][mb];
+    for (int ma = 0; ma < Pm; ++ma) {
+      const T w = a.mortar->Pi[pa][ma] * wb;
+      const int tm = orient_inv(r.orient, ma + Pm * mb, Pm, ND);
+      for (int c = 0; c < ncomp; ++c) acc[c] += w * sc[c * NFPm + tm];
+    }
+  }
+  T* os = a.fout + r.so;
+  for (int v = 0; v < NV; ++v) {
+    os[v * NFPs + pt] = sgs * acc[v];
+    if (VISC) {
+      const T qs = a.trq[r.st + (int64_t)v * NFPs + pt];
+      os[(NV + v) * NFPs + pt] = acc[NV + v] - qs;
+      if (MODE == 1) {
+        const T qsd = a.trv[r.st + (int64_t)v * NFPs + pt];
+        os[(2 * NV + v) * NFPs + pt] = acc[2 * NV + v] - qsd;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary faces: ghost state (wall / far field).  One thread per (face, point).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BndArgs {
+  const BndRec* recs;
+  const T* trq;
+  const T* trv;
+  T* fout;
+  const BasisTab<T>* basis;
+  GeoView<T> geo;
+  T gamma, mu, kappa;
+  T qinf[5];
+  int n, P, kind;
+};
+
+template <typename T, int ND, bool VISC, int MODE>
+__global__ void __launch_bounds__(128) bnd_kernel(BndArgs<T> a) {
+  constexpr int NV = ND + 2;
+  using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
+  const int P = a.P;
+  const int NFP = ND == 2 ? P : P * P;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)a.n * NFP) return;
+  const int t = (int)(gid % NFP);
+  const BndRec r = a.recs[gid / NFP];
+  const int d = r.mf >> 1, s = r.mf & 1;
+  const T* trv = MODE == 1 ? a.trv : nullptr;
+  S qM[NV], qG[NV];
+  load_trace_pt<ND>(a.trq, trv, r.mt, 0, NV, NFP, t, qM);
+  ghost_state<ND>(qM, a.kind, a.qinf, qG);
+  T A[ND], n[ND];
+  T absA2 = T(0);
+  const T sg = s ? T(1) : T(-1);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    A[j] = sg * geo_face(a.geo, r.me, r.mf, d * ND + j, t);
+    absA2 += A[j] * A[j];
+  }
+  const T absA = sqrt(absA2);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) n[j] = A[j] / absA;
+  S Fn[NV];
+  rusanov<ND>(qM, qG, n, absA, a.gamma, Fn);
+  S qc[NV];
+  if (VISC) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qG[v]);
+    T cM[ND];
+    const T g = a.basis[P].dgf[s];
+    const T J = geo_face(a.geo, r.me, r.mf, ND * ND, t);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) cM[j] = g * geo_face(a.geo, r.me, r.mf, d * ND + j, t) / J;
+    S GM[ND][NV], Gc[ND][NV];
+    load_trace_pt<ND>(a.trq, trv, r.mt, NV, ND * NV, NFP, t, &GM[0][0]);
+#pragma unroll
+    for (int j = 0; j < ND; ++j)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Gc[j][v] = GM[j][v] + cM[j] * (qc[v] - qM[v]);
+    S fv[ND][NV];
+    flux_viscous<ND>(qc, Gc, a.gamma, a.mu, a.kappa, fv);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      S acc = szero<S>();
+#pragma unroll
+      for (int j = 0; j < ND; ++j) acc = acc + fv[j][v] * A[j];
+      if (a.kind == -1 && v == NV - 1) acc = szero<S>();   // adiabatic wall
+      Fn[v] = Fn[v] - acc;
+    }
+  }
+  T* om = a.fout + r.mo;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    S x = sg * Fn[v];
+    om[v * NFP + t] = MODE == 1 ? tangent(x) : value(x);
+    if (VISC) {
+      S dq = qc[v] - qM[v];
+      om[(NV + v) * NFP + t] = value(dq);
+      if (MODE == 1) om[(2 * NV + v) * NFP + t] = tangent(dq);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Volume kernel: corrected gradient, flux, divergence and FR correction.
+// One thread per solution point, EPB elements per block.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct VolArgs {
+  const T* q;
+  const T* v;          // tangent (JVP)
+  T* out;
+  const T* fout;
+  const int32_t* slot_elem;
+  const BasisTab<T>* basis;
+  GeoView<T> geo;
+  T gamma, mu, kappa;
+  int64_t state_base, out_base;
+  int count, slot_begin;
+};
+
+template <int ND, int P>
+struct VolCfg {
+  static constexpr int NSP = Shape<ND, P>::NSP;
+  static constexpr int EPB = NSP >= 256 ? 1 : 256 / NSP;
+  static constexpr int THREADS = EPB * NSP;
+};
+
+template <typename T, int ND, int P, bool VISC, int MODE>
+__global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_kernel(VolArgs<T> a) {
+  using Sh = Shape<ND, P>;
+  using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
+  constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
+  constexpr int EPB = VolCfg<ND, P>::EPB;
+  constexpr int FOUT_STRIDE = 3 * NV * NFP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* sm = reinterpret_cast<S*>(smem_raw);
+  const int le = threadIdx.x / NSP;
+  const int sp = threadIdx.x % NSP;
+  const int64_t i = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = i < a.count;
+  S* sq = sm + le * (NV + ND * NV) * NSP;       // [NV][NSP]
+  S* sF = sq + NV * NSP;                         // [ND][NV][NSP]
+  const BasisTab<T>& B = a.basis[P];
+  int idx[3];
+  idx[0] = sp % P;
+  idx[1] = (sp / P) % P;
+  idx[2] = ND == 3 ? sp / (P * P) : 0;
+  const int64_t e = valid ? a.slot_elem[a.slot_begin + i] : 0;
+  const T* fo = a.fout + (valid ? a.out_base + i * NF * FOUT_STRIDE : 0);
+
+  S q[NV];
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T x = a.q[a.state_base + (i * NV + v) * NSP + sp];
+      T dx = MODE == 1 ? a.v[a.state_base + (i * NV + v) * NSP + sp] : T(0);
+      set_scalar(q[v], x, dx);
+      sq[v * NSP + sp] = q[v];
+    }
+  }
+  __syncthreads();
+
+  T Sm[ND][ND];
+  T J = T(1);
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+      for (int j = 0; j < ND; ++j) Sm[d][j] = geo_vol(a.geo, e, d * ND + j, sp);
+    J = geo_vol(a.geo, e, ND * ND, sp);
+
+    S f[ND][NV];
+    flux_inviscid<ND>(q, a.gamma, f);
+    if (VISC) {
+      S gref[ND][NV];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        const int stride = d == 0 ? 1 : (d == 1 ? P : P * P);
+        const int base = sp - idx[d] * stride;
+        const int tf = face_pt<ND, P>(d, idx);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          S acc = szero<S>();
+#pragma unroll
+          for (int k = 0; k < P; ++k) acc = acc + B.D[idx[d]][k] * sq[v * NSP + base + k * stride];
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const T* blk = fo + (2 * d + s) * FOUT_STRIDE;
+            S dq;
+            set_scalar(dq, blk[(NV + v) * NFP + tf], MODE == 1 ? blk[(2 * NV + v) * NFP + tf] : T(0));
+            acc = acc + B.dg[s][idx[d]] * dq;
+          }
+          gref[d][v] = acc;
+        }
+      }
+      S G[ND][NV];
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          S acc = szero<S>();
+#pragma unroll
+          for (int d = 0; d < ND; ++d) acc = acc + Sm[d][j] * gref[d][v];
+          G[j][v] = acc / J;
+        }
+      S fv[ND][NV];
+      flux_viscous<ND>(q, G, a.gamma, a.mu, a.kappa, fv);
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[j][v] = f[j][v] - fv[j][v];
+    }
+    // transformed flux F~_d = sum_j S[d][j] f_j
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        S acc = szero<S>();
+#pragma unroll
+        for (int j = 0; j < ND; ++j) acc = acc + Sm[d][j] * f[j][v];
+        sF[(d * NV + v) * NSP + sp] = acc;
+      }
+  }
+  __syncthreads();
+  if (!valid) return;
+
+  // divergence D_d F~_d plus the correction g_s'(xi_d) (F~^com - F~(xi_d = +-1))
+  S div[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) div[v] = szero<S>();
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const int stride = d == 0 ? 1 : (d == 1 ? P : P * P);
+    const int base = sp - idx[d] * stride;
+    const int tf = face_pt<ND, P>(d, idx);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const S* line = sF + (d * NV + v) * NSP + base;
+      S acc = szero<S>();
+#pragma unroll
+      for (int k = 0; k < P; ++k) acc = acc + B.D[idx[d]][k] * line[k * stride];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        S loc = szero<S>();
+#pragma unroll
+        for (int k = 0; k < P; ++k) loc = loc + B.ext[s][k] * line[k * stride];
+        S com;
+        const T c = fo[(2 * d + s) * FOUT_STRIDE + v * NFP + tf];
+        if (MODE == 1) set_scalar(com, T(0), c); else set_scalar(com, c, T(0));
+        acc = acc + B.dg[s][idx[d]] * (com - loc);
+      }
+      div[v] = div[v] + acc;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    S r = (T(0) - div[v]) / J;
+    a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
+  }
+}
+
+}  // namespace frgb

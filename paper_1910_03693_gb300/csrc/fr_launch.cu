@@ -1,0 +1,154 @@
+// Launch orchestration of the FR residual and exact JVP, canonical <-> state
+// layout conversion, and the C-ABI entry points fr_pack, fr_unpack,
+// fr_residual and fr_jvp.
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <cstring>
+
+#include "fr_launch.h"
+
+namespace frgb {
+
+Timing& timing_of(fr_ctx* c);
+
+fr_status launch_residual(fr_ctx* c, const void* q, void* R, fr_prec prec, cudaStream_t s) {
+  return prec == FR_F64 ? run_op_f64(c, 0, q, nullptr, R, s) : run_op_f32(c, 0, q, nullptr, R, s);
+}
+
+fr_status launch_jvp_exact(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec,
+                           cudaStream_t s) {
+  return prec == FR_F64 ? run_op_f64(c, 1, q, v, Jv, s) : run_op_f32(c, 1, q, v, Jv, s);
+}
+
+fr_status launch_vjp(fr_ctx* c, const void* q, const void* w, void* JTw, fr_prec prec, cudaStream_t s) {
+  return prec == FR_F64 ? run_op_f64(c, 2, q, w, JTw, s) : run_op_f32(c, 2, q, w, JTw, s);
+}
+
+// One block per element slot; threads walk the element's [v][sp] block.
+template <typename T>
+__global__ void pack_kernel(const double* __restrict__ canon, T* __restrict__ q,
+                            const int64_t* __restrict__ canon_off, const int64_t* __restrict__ state_off,
+                            const int8_t* __restrict__ slot_p, int E, int nd, int nv) {
+  for (int64_t sidx = blockIdx.x; sidx < E; sidx += gridDim.x) {
+    const int P = slot_p[sidx] + 1;
+    const int nsp = nd == 2 ? P * P : P * P * P;
+    const int64_t co = canon_off[sidx], so = state_off[sidx];
+    for (int k = threadIdx.x; k < nsp * nv; k += blockDim.x) {
+      const int v = k / nsp, sp = k % nsp;
+      q[so + k] = (T)canon[co + (int64_t)sp * nv + v];
+    }
+  }
+}
+
+template <typename T>
+__global__ void unpack_kernel(const T* __restrict__ q, double* __restrict__ canon,
+                              const int64_t* __restrict__ canon_off, const int64_t* __restrict__ state_off,
+                              const int8_t* __restrict__ slot_p, int E, int nd, int nv) {
+  for (int64_t sidx = blockIdx.x; sidx < E; sidx += gridDim.x) {
+    const int P = slot_p[sidx] + 1;
+    const int nsp = nd == 2 ? P * P : P * P * P;
+    const int64_t co = canon_off[sidx], so = state_off[sidx];
+    for (int k = threadIdx.x; k < nsp * nv; k += blockDim.x) {
+      const int sp = k / nv, v = k % nv;
+      canon[co + k] = (double)q[so + (int64_t)v * nsp + sp];
+    }
+  }
+}
+
+fr_status launch_pack(fr_ctx* c, const double* canon, void* q, fr_prec prec, bool unpack, cudaStream_t s) {
+  const unsigned g = (unsigned)std::min<int64_t>(c->E, 1 << 20);
+  if (!unpack) {
+    if (prec == FR_F64)
+      FR_LAUNCH_B(c, "pack", s, (double)c->n_dof * (8 + (prec == FR_F64 ? 8 : 4)), pack_kernel<double><<<g, 128, 0, s>>>(canon, (double*)q, c->d_canon_off, c->d_state_off, c->d_slot_p, c->E, c->nd, c->nv));
+    else
+      FR_LAUNCH_B(c, "pack", s, (double)c->n_dof * (8 + (prec == FR_F64 ? 8 : 4)), pack_kernel<float><<<g, 128, 0, s>>>(canon, (float*)q, c->d_canon_off, c->d_state_off, c->d_slot_p, c->E, c->nd, c->nv));
+  } else {
+    if (prec == FR_F64)
+      FR_LAUNCH_B(c, "pack", s, (double)c->n_dof * (8 + (prec == FR_F64 ? 8 : 4)), unpack_kernel<double><<<g, 128, 0, s>>>((const double*)q, const_cast<double*>(canon), c->d_canon_off, c->d_state_off, c->d_slot_p, c->E, c->nd, c->nv));
+    else
+      FR_LAUNCH_B(c, "pack", s, (double)c->n_dof * (8 + (prec == FR_F64 ? 8 : 4)), unpack_kernel<float><<<g, 128, 0, s>>>((const float*)q, const_cast<double*>(canon), c->d_canon_off, c->d_state_off, c->d_slot_p, c->E, c->nd, c->nv));
+  }
+  return cuda_check(cudaGetLastError(), "pack kernel launch");
+}
+
+}  // namespace frgb
+
+namespace frgb {
+Timing& timing_of(fr_ctx* c) { return c->timing; }
+}  // namespace frgb
+
+using namespace frgb;
+
+extern "C" {
+
+fr_status fr_timing(fr_ctx* c, int32_t enable) {
+  if (!c) return FR_ERR_INVALID;
+  cudaDeviceSynchronize();
+  c->timing.collect();
+  c->timing.acc.clear();
+  c->timing.launches = 0;
+  c->timing.on = enable != 0;
+  return FR_OK;
+}
+
+fr_status fr_timing_report(fr_ctx* c, char* buf, int64_t len, int64_t* launches) {
+  if (!c || !buf || len <= 0) return FR_ERR_INVALID;
+  cudaDeviceSynchronize();
+  c->timing.collect();
+  std::string out;
+  char line[256];
+  for (const auto& kv : c->timing.acc) {
+    snprintf(line, sizeof(line), "%s %lld %.6f %.0f\n", kv.first.c_str(), kv.second.count, kv.second.ms,
+             kv.second.bytes);
+    out += line;
+  }
+  if ((int64_t)out.size() + 1 > len) return FR_ERR_INVALID;
+  std::memcpy(buf, out.c_str(), out.size() + 1);
+  if (launches) *launches = c->timing.launches;
+  return FR_OK;
+}
+
+fr_status fr_pack(fr_ctx* c, const double* canon_dev, void* q_dev, fr_prec prec, void* stream) {
+  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32)) return FR_ERR_INVALID;
+  return launch_pack(c, canon_dev, q_dev, prec, false, (cudaStream_t)stream);
+}
+
+fr_status fr_unpack(fr_ctx* c, const void* q_dev, fr_prec prec, double* canon_dev, void* stream) {
+  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32)) return FR_ERR_INVALID;
+  return launch_pack(c, canon_dev, const_cast<void*>(q_dev), prec, true, (cudaStream_t)stream);
+}
+
+fr_status fr_residual(fr_ctx* c, const void* q_dev, void* R_dev, fr_prec prec, void* stream) {
+  if (!c || !q_dev || !R_dev || (prec != FR_F64 && prec != FR_F32)) {
+    set_error("fr_residual: bad argument");
+    return FR_ERR_INVALID;
+  }
+  return launch_residual(c, q_dev, R_dev, prec, (cudaStream_t)stream);
+}
+
+fr_status fr_vjp(fr_ctx* c, const void* q_dev, const void* w_dev, void* JTw_dev, fr_prec prec,
+                 void* stream) {
+  if (!c || !q_dev || !w_dev || !JTw_dev || (prec != FR_F64 && prec != FR_F32)) {
+    set_error("fr_vjp: bad argument");
+    return FR_ERR_INVALID;
+  }
+  return launch_vjp(c, q_dev, w_dev, JTw_dev, prec, (cudaStream_t)stream);
+}
+
+fr_status fr_jvp(fr_ctx* c, const void* q_dev, const void* v_dev, void* Jv_dev, fr_prec prec,
+                 fr_jv_mode mode, double eps, void* stream) {
+  if (!c || !q_dev || !v_dev || !Jv_dev || (prec != FR_F64 && prec != FR_F32)) {
+    set_error("fr_jvp: bad argument");
+    return FR_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (mode == FR_JV_EXACT) return launch_jvp_exact(c, q_dev, v_dev, Jv_dev, prec, s);
+  if (mode != FR_JV_FD || prec != FR_F64 || !(eps > 0.0)) {
+    set_error("fr_jvp: the finite-difference mode is FP64 with eps > 0");
+    return FR_ERR_INVALID;
+  }
+  return launch_fd_jv(c, (const double*)q_dev, (const double*)v_dev, (double*)Jv_dev, eps, nullptr, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,27 @@
+// Internal launch helpers shared by the translation units of the library.
+#pragma once
+
+#include "fr_internal.h"
+
+namespace frgb {
+
+// Device scratch vectors owned by the context, sized n_dof_capacity.
+double* vec64(fr_ctx* c, int k);
+float* vec32(fr_ctx* c, int k);
+
+// y = a*x + b*y ; z = x + a*y ; elementwise casts; scaled difference.
+void vaxpby(fr_ctx* c, double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
+void vadd_scaled(fr_ctx* c, const double* x, double a, const double* y, double* z, int64_t n, cudaStream_t s);
+void vdiff_scaled(fr_ctx* c, const double* x, const double* y, double a, double* z, int64_t n, cudaStream_t s);
+void vcast_f64_f32(fr_ctx* c, const double* x, float* y, int64_t n, cudaStream_t s);
+void vcast_f32_f64(fr_ctx* c, const float* x, double* y, int64_t n, cudaStream_t s);
+
+// op 0: out = R(q); op 1: out = J(q) v (exact); op 2: out = J(q)^T v.
+fr_status run_op_f64(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
+fr_status run_op_f32(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
+
+// Jv = (R(q + eps v) - R0) / eps in FP64; R0 = R(q) is computed when null.
+fr_status launch_fd_jv(fr_ctx* c, const double* q, const double* v, double* Jv, double eps,
+                       const double* R0, cudaStream_t s);
+
+}  // namespace frgb

@@ -1,0 +1,201 @@
+// Pointwise physics of the compressible Navier-Stokes equations (Sec. 2.1),
+// written once over a scalar type S: S = T gives the residual, S = Dual<T>
+// (value + directional derivative) gives the exact JVP by forward-mode
+// differentiation of the same arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace frgb {
+
+template <typename T>
+struct Dual {
+  T v, d;
+};
+
+template <typename T>
+__device__ __forceinline__ T value(T x) { return x; }
+template <typename T>
+__device__ __forceinline__ T value(Dual<T> x) { return x.v; }
+template <typename T>
+__device__ __forceinline__ T tangent(T) { return T(0); }
+template <typename T>
+__device__ __forceinline__ T tangent(Dual<T> x) { return x.d; }
+
+template <typename T>
+__device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
+  T r = a.v / b.v;
+  return {r, (a.d - r * b.d) / b.v};
+}
+template <typename T>
+__device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return {a.v + b, a.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator+(T a, Dual<T> b) { return {a + b.v, b.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return {a.v - b, a.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return {a - b.v, -b.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { return {a.v / b, a.d / b}; }
+
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+template <typename T>
+__device__ __forceinline__ Dual<T> dsqrt(Dual<T> x) {
+  T r = dsqrt(x.v);
+  return {r, x.d / (T(2) * r)};
+}
+// |x| with d|x| = sign(x) dx, sign(0) := +1
+__device__ __forceinline__ double dabs(double x) { return fabs(x); }
+__device__ __forceinline__ float dabs(float x) { return fabsf(x); }
+template <typename T>
+__device__ __forceinline__ Dual<T> dabs(Dual<T> x) { return x.v < T(0) ? Dual<T>{-x.v, -x.d} : x; }
+// max(a, b); at a tie the first argument (the "-" side) is taken
+template <typename T>
+__device__ __forceinline__ T dmax(T a, T b) { return b > a ? b : a; }
+template <typename T>
+__device__ __forceinline__ Dual<T> dmax(Dual<T> a, Dual<T> b) { return b.v > a.v ? b : a; }
+
+template <typename S>
+__device__ __forceinline__ S szero() { return S{}; }
+
+template <typename T>
+__device__ __forceinline__ void set_scalar(T& x, T v, T) { x = v; }
+template <typename T>
+__device__ __forceinline__ void set_scalar(Dual<T>& x, T v, T d) { x.v = v; x.d = d; }
+
+// Inviscid flux f[j][v] (physical direction j) of q = (rho, rho u_i, rho E).
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void flux_inviscid(const S* q, T gamma, S (*f)[ND + 2]) {
+  constexpr int NV = ND + 2;
+  S rho = q[0];
+  S vel[ND];
+  S ke = szero<S>();
+#pragma unroll
+  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] / rho;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) ke = ke + vel[i] * vel[i];
+  S pres = (gamma - T(1)) * (q[NV - 1] - T(0.5) * rho * ke);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    f[j][0] = q[1 + j];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      S fij = q[1 + i] * vel[j];
+      if (i == j) fij = fij + pres;
+      f[j][1 + i] = fij;
+    }
+    f[j][NV - 1] = (q[NV - 1] + pres) * vel[j];
+  }
+}
+
+// |u.n| + c
+template <int ND, typename S, typename T>
+__device__ __forceinline__ S wave_speed(const S* q, const T* n, T gamma) {
+  constexpr int NV = ND + 2;
+  S rho = q[0];
+  S vel[ND];
+  S ke = szero<S>(), un = szero<S>();
+#pragma unroll
+  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] / rho;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) ke = ke + vel[i] * vel[i];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) un = un + vel[i] * n[i];
+  S pres = (gamma - T(1)) * (q[NV - 1] - T(0.5) * rho * ke);
+  S c = dsqrt(gamma * pres / rho);
+  return dabs(un) + c;
+}
+
+// Rusanov normal flux times the face area: ((fL.n + fR.n)/2 - lam/2 (qR - qL)) |A|.
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void rusanov(const S* qL, const S* qR, const T* n, T absA, T gamma,
+                                        S* Fn) {
+  constexpr int NV = ND + 2;
+  S fL[ND][NV], fR[ND][NV];
+  flux_inviscid<ND>(qL, gamma, fL);
+  flux_inviscid<ND>(qR, gamma, fR);
+  S lam = dmax(wave_speed<ND>(qL, n, gamma), wave_speed<ND>(qR, n, gamma));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    S a = szero<S>(), b = szero<S>();
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      a = a + fL[j][v] * n[j];
+      b = b + fR[j][v] * n[j];
+    }
+    Fn[v] = (T(0.5) * (a + b) - T(0.5) * lam * (qR[v] - qL[v])) * absA;
+  }
+}
+
+// Viscous flux fv[j][v] from q and its physical gradient G[j][v]:
+// (0, tau_ij, u_i tau_ij + kappa d_j(p/rho)), kappa = mu gamma / ((gamma-1) Pr).
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void flux_viscous(const S* q, const S (*G)[ND + 2], T gamma, T mu,
+                                             T kappa, S (*fv)[ND + 2]) {
+  constexpr int NV = ND + 2;
+  S rho = q[0];
+  S vel[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] / rho;
+  S Es = q[NV - 1] / rho;
+  S du[ND][ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) du[i][j] = (G[j][1 + i] - vel[i] * G[j][0]) / rho;
+  S dT[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    S dE = (G[j][NV - 1] - Es * G[j][0]) / rho;
+    S s = szero<S>();
+#pragma unroll
+    for (int k = 0; k < ND; ++k) s = s + vel[k] * du[k][j];
+    dT[j] = (gamma - T(1)) * (dE - s);
+  }
+  S div = szero<S>();
+#pragma unroll
+  for (int k = 0; k < ND; ++k) div = div + du[k][k];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    fv[j][0] = szero<S>();
+    S e = szero<S>();
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      S tau = mu * (du[i][j] + du[j][i]);
+      if (i == j) tau = tau - T(2.0 / 3.0) * mu * div;
+      fv[j][1 + i] = tau;
+      e = e + vel[i] * tau;
+    }
+    fv[j][NV - 1] = e + kappa * dT[j];
+  }
+}
+
+// Ghost state of a boundary: wall (-1) reverses momentum, far field (-2) is q_inf.
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void ghost_state(const S* q, int kind, const T* qinf, S* g) {
+  constexpr int NV = ND + 2;
+  if (kind == -1) {
+    g[0] = q[0];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) g[1 + i] = -q[1 + i];
+    g[NV - 1] = q[NV - 1];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) set_scalar(g[v], qinf[v], T(0));
+  }
+}
+
+}  // namespace frgb

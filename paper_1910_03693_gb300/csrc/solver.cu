@@ -1,0 +1,423 @@
+// Matrix-free Newton-Krylov of Sec. 2.3: restarted GMRES(m) on
+// (sigma I - dR/dq) dq = F with FP64 Arnoldi (classical Gram-Schmidt applied
+// twice, Givens rotations), and one ESDIRK stage by pseudo-transient
+// continuation with the SER pseudo-time step and dtau back-off.
+//
+// Reductions are deterministic: every block writes its partial sums to a
+// fixed slot and one block adds the partials in slot order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fr_launch.h"
+
+namespace frgb {
+
+constexpr int kRedBlocks = 304;     // 2 blocks per SM on 152 SMs
+constexpr int kRedThreads = 256;
+constexpr int kMaxK = 64;           // most vectors in one multi-dot (restart length + 1)
+
+static fr_status ensure_red(fr_ctx* c) {
+  if (c->d_red) return FR_OK;
+  c->red_cap = (int64_t)kRedBlocks * kMaxK + 2 * kMaxK;
+  if (cudaMalloc(&c->d_red, sizeof(double) * c->red_cap) != cudaSuccess) return FR_ERR_NOMEM;
+  if (cudaMallocHost(&c->h_red, sizeof(double) * 2 * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
+  return FR_OK;
+}
+
+// partial[block][kk] = sum_i V[kk][i] * w[i]  (kk < k), or ||w||^2 when V == nullptr
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int k,
+                                                           const double* __restrict__ w, int64_t n,
+                                                           double* __restrict__ partial) {
+  __shared__ double red[kRedThreads / 32][kMaxK];
+  double acc[kMaxK];
+  for (int kk = 0; kk < k; ++kk) acc[kk] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    if (V) {
+      for (int kk = 0; kk < k; ++kk) acc[kk] += V[kk * ldv + i] * wi;
+    } else {
+      acc[0] += wi * wi;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int kk = 0; kk < k; ++kk) {
+    double v = acc[kk];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][kk] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+    for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) s += red[wgi][threadIdx.x];
+    partial[(int64_t)blockIdx.x * kMaxK + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int k, double* __restrict__ out) {
+  const int kk = threadIdx.x;
+  if (kk >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * kMaxK + kk];
+  out[kk] = s;
+}
+
+// w -= sum_kk h[kk] V[kk];  optionally partial[block] = ||w_new||^2
+__global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __restrict__ V, int64_t ldv, int k,
+                                                              const double* __restrict__ h, double* __restrict__ w,
+                                                              int64_t n, double* __restrict__ partial) {
+  __shared__ double hs[kMaxK];
+  __shared__ double red[kRedThreads / 32];
+  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = w[i];
+    for (int kk = 0; kk < k; ++kk) x -= hs[kk] * V[kk * ldv + i];
+    w[i] = x;
+    acc += x * x;
+  }
+  if (partial) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) s += red[wgi];
+      partial[(int64_t)blockIdx.x * kMaxK] = s;
+    }
+  }
+}
+
+__global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// x += sum_kk y[kk] V[kk]   (y on the device)
+__global__ void k_combine(const double* __restrict__ V, int64_t ldv, int k, const double* __restrict__ y,
+                          double* __restrict__ x, int64_t n) {
+  __shared__ double ys[kMaxK];
+  if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = x[i];
+    for (int kk = 0; kk < k; ++kk) s += ys[kk] * V[kk * ldv + i];
+    x[i] = s;
+  }
+}
+
+// out = sigma v - J   (J in FP64 or FP32)
+template <typename T>
+__global__ void k_shift(double sigma, const double* __restrict__ v, const T* __restrict__ J,
+                        double* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = sigma * v[i] - (double)J[i];
+}
+
+// F = -q / (w dt) + R + rhs
+__global__ void k_stage_F(const double* __restrict__ q, const double* __restrict__ R,
+                          const double* __restrict__ rhs, double inv_wdt, double* __restrict__ F, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    F[i] = -q[i] * inv_wdt + R[i] + rhs[i];
+}
+
+static unsigned egrid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+}
+
+// k dot products V[0..k)^T w (or ||w||^2 when V is null) -> host array out[k]
+static fr_status multidot(fr_ctx* c, const double* V, int64_t ldv, int k, const double* w, int64_t n,
+                          double* out_host, cudaStream_t s) {
+  double* part = c->d_red;
+  double* dout = c->d_red + (int64_t)kRedBlocks * kMaxK;
+  FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1), k_multidot<<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, V ? k : 1, w, n, part));
+  FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, V ? k : 1, dout));
+  cudaMemcpyAsync(c->h_red, dout, sizeof(double) * (V ? k : 1), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "multidot");
+  std::memcpy(out_host, c->h_red, sizeof(double) * (V ? k : 1));
+  return FR_OK;
+}
+
+static fr_status norm2(fr_ctx* c, const double* w, int64_t n, double* out, cudaStream_t s) {
+  double v;
+  fr_status st = multidot(c, nullptr, 0, 1, w, n, &v, s);
+  *out = std::sqrt(v);
+  return st;
+}
+
+// y = A x = sigma x - J(q) x
+static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, const double* x, double* y,
+                          cudaStream_t s) {
+  const int64_t n = c->n_dof;
+  if (op->mode == FR_JV_FD) {
+    double* J = vec64(c, 3);
+    if (!J) return FR_ERR_NOMEM;
+    fr_status st = launch_fd_jv(c, op->q64_dev, x, J, op->eps, R0, s);
+    if (st != FR_OK) return st;
+    FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_shift<double><<<egrid(n), 256, 0, s>>>(op->sigma, x, J, y, n));
+  } else if (op->jv_prec == FR_F64) {
+    double* J = vec64(c, 3);
+    if (!J) return FR_ERR_NOMEM;
+    fr_status st = launch_jvp_exact(c, op->q64_dev, x, J, FR_F64, s);
+    if (st != FR_OK) return st;
+    FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_shift<double><<<egrid(n), 256, 0, s>>>(op->sigma, x, J, y, n));
+  } else {
+    float* q32 = vec32(c, 0);
+    float* x32 = vec32(c, 1);
+    float* J32 = vec32(c, 2);
+    if (!q32 || !x32 || !J32) return FR_ERR_NOMEM;
+    vcast_f64_f32(c, x, x32, n, s);
+    fr_status st = launch_jvp_exact(c, q32, x32, J32, FR_F32, s);
+    if (st != FR_OK) return st;
+    FR_LAUNCH_B(c, "vec", s, 20.0 * n, k_shift<float><<<egrid(n), 256, 0, s>>>(op->sigma, x, J32, y, n));
+  }
+  return cuda_check(cudaGetLastError(), "shifted operator");
+}
+
+// GMRES(m) with x0 = 0.  R0 (optional) = R(q) for the finite-difference mode.
+static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0, const double* b, double* x,
+                            const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s) {
+  const int m = o->m;
+  const int64_t n = c->n_dof, ld = c->n_dof_cap;
+  if (m < 1 || m + 1 > kMaxK || o->max_it < 1 || !(o->rtol > 0.0)) {
+    set_error("gmres_solve: need 1 <= m < 64, max_it >= 1, rtol > 0");
+    return FR_ERR_INVALID;
+  }
+  if (ensure_red(c) != FR_OK) return FR_ERR_NOMEM;
+  if (!c->d_krylov || c->krylov_m < m) {
+    cudaFree(c->d_krylov);
+    c->d_krylov = nullptr;
+    if (cudaMalloc(&c->d_krylov, sizeof(double) * (m + 1) * ld) != cudaSuccess) {
+      set_error("gmres_solve: Krylov basis allocation failed");
+      return FR_ERR_NOMEM;
+    }
+    c->krylov_m = m;
+  }
+  if (op->mode == FR_JV_EXACT && op->jv_prec == FR_F32) {
+    float* q32 = vec32(c, 0);
+    if (!q32) return FR_ERR_NOMEM;
+    vcast_f64_f32(c, op->q64_dev, q32, n, s);
+  }
+  double* V = c->d_krylov;
+  double* w = vec64(c, 4);
+  double* r = vec64(c, 5);
+  double* ydev = c->d_red + (int64_t)kRedBlocks * kMaxK + kMaxK;
+  if (!w || !r) return FR_ERR_NOMEM;
+  std::memset(st, 0, sizeof(*st));
+  cudaMemsetAsync(x, 0, sizeof(double) * n, s);
+  double beta0;
+  fr_status e = norm2(c, b, n, &beta0, s);
+  if (e != FR_OK) return e;
+  if (!std::isfinite(beta0)) {
+    set_error("gmres_solve: non-finite right-hand side");
+    return FR_ERR_NONFINITE;
+  }
+  if (beta0 == 0.0) {
+    st->converged = 1;
+    return FR_OK;
+  }
+  cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  int it = 0;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(kMaxK), h2(kMaxK);
+  double res = beta0;
+  while (true) {
+    double beta;
+    if ((e = norm2(c, r, n, &beta, s)) != FR_OK) return e;
+    if (beta <= o->rtol * beta0) {
+      st->converged = 1;
+      res = beta;
+      break;
+    }
+    if (it >= o->max_it) {
+      res = beta;
+      break;
+    }
+    FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(r, 1.0 / beta, V, n));
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    res = beta;
+    for (int j = 0; j < m; ++j) {
+      if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s)) != FR_OK) return e;
+      ++it;
+      // classical Gram-Schmidt, twice
+      if ((e = multidot(c, V, ld, j + 1, w, n, h.data(), s)) != FR_OK) return e;
+      cudaMemcpyAsync(ydev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s);
+      FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (j + 3), k_orth_update<<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j + 1, ydev, w, n, nullptr));
+      if ((e = multidot(c, V, ld, j + 1, w, n, h2.data(), s)) != FR_OK) return e;
+      cudaMemcpyAsync(ydev, h2.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s);
+      FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (j + 3), k_orth_update<<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j + 1, ydev, w, n, c->d_red));
+      FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(c->d_red, kRedBlocks, 1, c->d_red + (int64_t)kRedBlocks * kMaxK));
+      cudaMemcpyAsync(c->h_red, c->d_red + (int64_t)kRedBlocks * kMaxK, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
+      const double hn = std::sqrt(c->h_red[0]);
+      for (int i = 0; i <= j; ++i) H[i * m + j] = h[i] + h2[i];
+      H[(j + 1) * m + j] = hn;
+      if (!std::isfinite(hn)) {
+        set_error("gmres_solve: non-finite Arnoldi vector");
+        return FR_ERR_NONFINITE;
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+      if (den == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        cs[j] = H[j * m + j] / den;
+        sn[j] = H[(j + 1) * m + j] / den;
+      }
+      H[j * m + j] = cs[j] * H[j * m + j] + sn[j] * H[(j + 1) * m + j];
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      res = std::fabs(g[j + 1]);
+      k = j + 1;
+      if (hn != 0.0) k_scale<<<egrid(n), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * ld, n);
+      if (res <= o->rtol * beta0 || it >= o->max_it || hn == 0.0) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < k; ++l) t -= H[i * m + l] * y[l];
+      y[i] = t / H[i * m + i];
+    }
+    cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
+    FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (k + 2), k_combine<<<egrid(n), 256, 0, s>>>(V, ld, k, ydev, x, n));
+    st->restarts += 1;
+    if (res <= o->rtol * beta0) {
+      st->converged = 1;
+      break;
+    }
+    if (it >= o->max_it) break;
+    // true residual at restart (not counted as an iteration)
+    if ((e = apply_op(c, op, R0, x, w, s)) != FR_OK) return e;
+    cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    vaxpby(c, -1.0, w, 1.0, r, n, s);
+  }
+  st->iterations = it;
+  st->rel_res = res / beta0;
+  return cuda_check(cudaStreamSynchronize(s), "gmres");
+}
+
+}  // namespace frgb
+
+using namespace frgb;
+
+extern "C" {
+
+fr_status gmres_solve(fr_ctx* c, const fr_shifted_op* op, const double* b_dev, double* x_dev,
+                      const fr_gmres_opts* opts, fr_gmres_stats* stats, void* stream) {
+  if (!c || !op || !op->q64_dev || !b_dev || !x_dev || !opts || !stats) {
+    set_error("gmres_solve: null argument");
+    return FR_ERR_INVALID;
+  }
+  if (op->mode == FR_JV_FD && !(op->eps > 0.0)) {
+    set_error("gmres_solve: finite-difference mode needs eps > 0");
+    return FR_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* R0 = nullptr;
+  if (op->mode == FR_JV_FD) {
+    double* r0 = vec64(c, 2);
+    if (!r0) return FR_ERR_NOMEM;
+    fr_status st = launch_residual(c, op->q64_dev, r0, FR_F64, s);
+    if (st != FR_OK) return st;
+    R0 = r0;
+  }
+  return gmres_impl(c, op, R0, b_dev, x_dev, opts, stats, s);
+}
+
+fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double dt, const double* qn_dev,
+                       double* const* Rstages_dev, double* qi_dev, const fr_newton_opts* o,
+                       fr_stage_stats* st, void* stream) {
+  if (!c || !tab || !qn_dev || !qi_dev || !o || !st || tab->s < 2 || tab->s > 6 || stage < 2 ||
+      stage > tab->s || !(dt > 0.0) || !(o->tol > 0.0) || !(o->dtau_init > 0.0) || !(o->dtau_max > 0.0)) {
+    set_error("esdirk_stage: bad argument");
+    return FR_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int i = stage - 1;
+  const int S = tab->s;
+  const double w = tab->A[i * S + i];
+  if (!(w > 0.0)) {
+    set_error("esdirk_stage: diagonal coefficient must be positive");
+    return FR_ERR_INVALID;
+  }
+  for (int j = 0; j < i; ++j)
+    if (tab->A[i * S + j] != 0.0 && (!Rstages_dev || !Rstages_dev[j])) {
+      set_error("esdirk_stage: missing R(q^j)");
+      return FR_ERR_INVALID;
+    }
+  const int64_t n = c->n_dof;
+  const double inv_wdt = 1.0 / (w * dt);
+  double* rhs = vec64(c, 6);
+  double* R = vec64(c, 7);
+  double* F = vec64(c, 8);
+  double* dq = vec64(c, 9);
+  if (!rhs || !R || !F || !dq) return FR_ERR_NOMEM;
+  fr_status e = ensure_red(c);
+  if (e != FR_OK) return e;
+  // rhs = (q^n + dt sum_{j<i} a_ij R(q^j)) / (w dt)
+  FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(qn_dev, inv_wdt, rhs, n));
+  for (int j = 0; j < i; ++j)
+    if (tab->A[i * S + j] != 0.0) vaxpby(c, dt * tab->A[i * S + j] * inv_wdt, Rstages_dev[j], 1.0, rhs, n, s);
+  std::memset(st, 0, sizeof(*st));
+  auto evalF = [&](double* norm) -> fr_status {
+    fr_status ee = launch_residual(c, qi_dev, R, FR_F64, s);
+    if (ee != FR_OK) return ee;
+    FR_LAUNCH_B(c, "vec", s, 32.0 * n, k_stage_F<<<egrid(n), 256, 0, s>>>(qi_dev, R, rhs, inv_wdt, F, n));
+    return norm2(c, F, n, norm, s);
+  };
+  double norm;
+  if ((e = evalF(&norm)) != FR_OK) return e;
+  if (!std::isfinite(norm)) {
+    set_error("esdirk_stage: non-finite stage residual");
+    return FR_ERR_NONFINITE;
+  }
+  st->norm0 = norm;
+  double dtau = o->dtau_init, norm_prev = -1.0;
+  fr_shifted_op op;
+  op.q64_dev = qi_dev;
+  op.mode = o->mode;
+  op.jv_prec = o->mode == FR_JV_FD ? FR_F64 : o->jv_prec;
+  op.eps = o->eps;
+  for (int m = 0; m < o->max_newton; ++m) {
+    if (norm <= o->tol * st->norm0) {
+      st->converged = 1;
+      break;
+    }
+    if (norm_prev > 0.0) dtau = std::min(dtau * norm_prev / norm, o->dtau_max);
+    fr_gmres_stats gs;
+    for (int h = 0; h <= o->max_halvings; ++h) {
+      op.sigma = inv_wdt + 1.0 / dtau;
+      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s)) != FR_OK) return e;
+      st->gmres_iterations += gs.iterations;
+      if (gs.converged) break;
+      dtau *= 0.5;
+      st->halvings += 1;
+    }
+    vaxpby(c, 1.0, dq, 1.0, qi_dev, n, s);
+    norm_prev = norm;
+    if ((e = evalF(&norm)) != FR_OK) return e;
+    if (!std::isfinite(norm)) {
+      set_error("esdirk_stage: non-finite stage residual");
+      return FR_ERR_NONFINITE;
+    }
+    st->newton_iterations += 1;
+  }
+  if (norm <= o->tol * st->norm0) st->converged = 1;
+  st->norm_final = norm;
+  if (Rstages_dev && Rstages_dev[i])
+    cudaMemcpyAsync(Rstages_dev[i], R, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  e = cuda_check(cudaStreamSynchronize(s), "esdirk_stage");
+  if (e != FR_OK) return e;
+  return st->converged ? FR_OK : FR_ERR_NOT_CONVERGED;
+}
+
+}  // extern "C"

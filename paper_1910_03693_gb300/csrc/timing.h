@@ -1,0 +1,106 @@
+// Per-launch instrumentation: a launch counter that is always kept, and,
+// when enabled, a pair of CUDA events recorded on the launch stream around
+// every kernel so that per-kernel device time can be read after a sync.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+struct fr_ctx;
+
+namespace frgb {
+
+struct TimerRec {
+  const char* name;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct TimerAcc {
+  double ms = 0.0;
+  long long count = 0;
+  double bytes = 0.0;     // algorithmic bytes of all recorded launches
+};
+
+struct Timing {
+  bool on = false;
+  long long launches = 0;
+  std::vector<cudaEvent_t> pool;
+  std::vector<TimerRec> pending;
+  std::map<std::string, TimerAcc> acc;
+  cudaEvent_t take() {
+    cudaEvent_t e;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  void collect() {
+    for (auto& r : pending) {
+      float ms = 0.f;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      auto& x = acc[r.name];
+      x.ms += ms;
+      x.count += 1;
+      x.bytes += r.bytes;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~Timing() {
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+Timing& timing_of(fr_ctx* c);
+
+// RAII scope around one kernel launch.
+struct LaunchScope {
+  Timing& t;
+  const char* name;
+  cudaStream_t s;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  LaunchScope(fr_ctx* c, const char* n, cudaStream_t st, double b = 0.0)
+      : t(timing_of(c)), name(n), s(st), bytes(b) {
+    ++t.launches;
+    if (t.on) {
+      a = t.take();
+      cudaEventRecord(a, s);
+    }
+  }
+  ~LaunchScope() {
+    if (t.on) {
+      cudaEvent_t b = t.take();
+      cudaEventRecord(b, s);
+      t.pending.push_back(TimerRec{name, a, b, bytes});
+    }
+  }
+};
+
+}  // namespace frgb
+
+#define FR_LAUNCH(ctx, name, stream, ...)                   \
+  do {                                                      \
+    ::frgb::LaunchScope _fr_scope((ctx), (name), (stream)); \
+    __VA_ARGS__;                                            \
+  } while (0)
+
+// Same, recording `bytes` algorithmic bytes for the launch.
+#define FR_LAUNCH_B(ctx, name, stream, bytes, ...)                               \
+  do {                                                                           \
+    ::frgb::LaunchScope _fr_scope((ctx), (name), (stream), (double)(bytes));     \
+    __VA_ARGS__;                                                                 \
+  } while (0)

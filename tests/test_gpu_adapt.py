@@ -1,0 +1,96 @@
+"""GPU parity of the spectral-decay indicator and the p-adaptation with
+rebucketing: eta to 1e-12 (relative, per element), the new p-map and the
+bucket permutation bit-exact, the transferred state to 1e-13 of its size."""
+import numpy as np
+import pytest
+import torch
+
+import cases
+from helpers import gpu_ctx, oracle_fr, small_workloads
+
+pytestmark = pytest.mark.gpu
+
+WL = small_workloads()
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1910_03693_gb300 import build as B
+    B.build()
+    return True
+
+
+@pytest.mark.parametrize("name", ["vortex2d_mixed_p1-4", "cylinder_4x12x2_mixed", "naca_24x4x2_mixed",
+                                  "vortex_batch_5", "tgv_5^3_p3"])
+def test_indicator_parity(built, name):
+    from oracle import adapt
+    m, q, ph = WL[name]
+    fr, ctx = oracle_fr(m, ph), gpu_ctx(m, ph)
+    ref = adapt.indicator(fr, torch.from_numpy(q), var=1)
+    for dtype in (torch.float64, torch.float32):
+        qs = ctx.pack(torch.from_numpy(q).cuda(), dtype)
+        eta, emax = ctx.indicator(qs, var=1)
+        eta = eta.cpu().numpy()
+        # eta = sum w (s - s_{p-1})^2 / sum w s^2: the top modes s - s_{p-1} carry a
+        # rounding error ~eps |s|, so |d eta| ~ 2 sqrt(eta) eps; relative 1e-12 plus
+        # that term (it dominates for smooth elements, eta -> 0)
+        tol, eps = (1e-12, 1e-15) if dtype == torch.float64 else (1e-4, 1e-6)
+        assert np.all(np.abs(eta - ref) <= tol * np.abs(ref) + eps * np.sqrt(np.abs(ref))), name
+        assert float(emax) == pytest.approx(ref.max(), rel=tol)
+
+
+def _adapt_case(name, p_min, p_max, nu=(0.1, 0.001)):
+    from oracle import adapt
+    m, q, ph = WL[name]
+    fr = oracle_fr(m, ph)
+    qt = torch.from_numpy(q)
+    p_ref, eta = adapt.adapt_p(fr, qt, nu[0], nu[1], p_min, p_max)
+    m_new = m.with_p(p_ref.astype(np.int8))
+    fr_new = oracle_fr(m_new, ph)
+    q_ref = adapt.transfer(fr, qt, fr_new).numpy()
+    return m, q, ph, p_ref, q_ref, m_new
+
+
+@pytest.mark.parametrize("name,pmin,pmax", [("vortex2d_mixed_p1-4", 1, 5), ("cylinder_4x12x2_mixed", 1, 4),
+                                            ("naca_24x4x2_mixed", 1, 3), ("vortex2d_16x16_p2", 1, 4)])
+def test_rebucket_matches_oracle(built, name, pmin, pmax):
+    from oracle import adapt
+    m, q, ph, p_ref, q_ref, m_new = _adapt_case(name, pmin, pmax)
+    ctx = gpu_ctx(m, ph, p_min=pmin, p_max=pmax)
+    buf = torch.zeros(ctx.n_dof_capacity, dtype=torch.float64, device="cuda")
+    ctx.pack(torch.from_numpy(q).cuda(), out=buf[:ctx.n_dof])
+    eta, emax = ctx.indicator(buf[:ctx.n_dof])
+    perm = torch.empty(ctx.n_elem, dtype=torch.int32, device="cuda")
+    ctx.rebucket(eta, emax, buf, 0.1, 0.001, pmin, pmax, perm=perm)
+    assert np.array_equal(ctx.p_map(), p_ref.astype(np.int8))
+    assert np.array_equal(perm.cpu().numpy(), adapt.bucket_order(p_ref))
+    got = ctx.unpack(buf[:ctx.n_dof]).cpu().numpy()
+    assert got.size == q_ref.size
+    assert np.abs(got - q_ref).max() <= 1e-13 * np.abs(q_ref).max()
+    # the adapted context evaluates the residual of the new discretisation
+    fr_new = oracle_fr(m_new, ph)
+    Rref = fr_new.residual(torch.from_numpy(q_ref)).numpy()
+    R = ctx.unpack(ctx.residual(buf[:ctx.n_dof])).cpu().numpy()
+    assert np.abs(R - Rref).max() <= 1e-11 * np.abs(Rref).max()
+
+
+def test_rebucket_fp32_and_repeat(built):
+    """Two adaptation passes in a row in FP32 keep the p-map equal to the oracle's."""
+    from oracle import adapt
+    m, q, ph = WL["vortex2d_mixed_p1-4"]
+    ctx = gpu_ctx(m, ph, p_min=1, p_max=5)
+    buf = torch.zeros(ctx.n_dof_capacity, dtype=torch.float32, device="cuda")
+    ctx.pack(torch.from_numpy(q).cuda(), torch.float32, out=buf[:ctx.n_dof])
+    mm = m
+    qq = torch.from_numpy(q)
+    for _ in range(2):
+        fr = oracle_fr(mm, ph)
+        p_ref, _ = adapt.adapt_p(fr, qq, 0.1, 0.001, 1, 5)
+        m2 = mm.with_p(p_ref.astype(np.int8))
+        qq = adapt.transfer(fr, qq, oracle_fr(m2, ph))
+        mm = m2
+        eta, emax = ctx.indicator(buf[:ctx.n_dof])
+        ctx.rebucket(eta, emax, buf, 0.1, 0.001, 1, 5)
+        assert np.array_equal(ctx.p_map(), p_ref.astype(np.int8))
+    got = ctx.unpack(buf[:ctx.n_dof]).cpu().numpy()
+    assert np.abs(got - qq.numpy()).max() <= 2e-6 * np.abs(qq.numpy()).max()

@@ -1,0 +1,113 @@
+"""GPU parity: FR residual and exact / finite-difference JVP through the C ABI
+against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP64): max|gpu - oracle| <= 1e-12 max|oracle| over all variables
+(the oracle and the kernels differ only in rounding order), or, for smooth
+states whose residual is small next to the fluxes that cancel in it, the same
+bound on the flux-scaled error max|gpu - oracle| / (max|f| P^2 / h_min).  FP32: 2e-5 of
+max|oracle|: inputs are rounded to float (relative 6e-8) and the residual of
+a state perturbed at the 5 % level amplifies that by the operators' norm
+(~ (p+1)^2 / h times the flux scale, over a residual of the same order times
+the perturbation) -- measured errors are ~1e-6."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import gpu_ctx, oracle_fr, parity_ok, rel_err, small_workloads
+
+pytestmark = pytest.mark.gpu
+
+WL = small_workloads()
+TOL64 = 1e-12
+TOL32 = 2e-5
+# Curved meshes: the metric terms are computed independently on both sides
+# (C++ host code vs. the oracle) and differ by rounding of coordinates of size
+# up to 20 over elements of size 5e-3, i.e. ~1e-13 of the metric; the
+# differentiation operators (~P^2/h) carry that into R at the 1e-12 level.
+CURVED = ("cylinder", "naca", "box_curved")
+
+
+def tol64(name):
+    return 1e-11 if name.startswith(CURVED) else TOL64
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1910_03693_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available()
+    return True
+
+
+def _pair(name):
+    m, q, ph = WL[name]
+    return m, q, ph, oracle_fr(m, ph), gpu_ctx(m, ph)
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_residual_parity_fp64_fp32(built, name):
+    m, q, ph, fr, ctx = _pair(name)
+    Rref = fr.residual(torch.from_numpy(q)).numpy()
+    qd = torch.from_numpy(q).cuda()
+    for dtype, tol in ((torch.float64, tol64(name)), (torch.float32, TOL32)):
+        qs = ctx.pack(qd, dtype)
+        R = ctx.unpack(ctx.residual(qs)).cpu().numpy()
+        assert np.all(np.isfinite(R))
+        ok, rel, fs = parity_ok(R, Rref, m, q, tol)
+        assert ok, (name, str(dtype), rel, fs)
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_exact_jvp_parity(built, name):
+    from oracle import linearize as L
+    m, q, ph, fr, ctx = _pair(name)
+    qt = torch.from_numpy(q)
+    from cases import uniform
+    v = (uniform(901, q.size) - 0.5) * np.abs(q).mean()
+    Jref = L.jvp(fr, qt, torch.from_numpy(v)).numpy()
+    for dtype, tol in ((torch.float64, tol64(name)), (torch.float32, TOL32)):
+        qs = ctx.pack(qt.cuda(), dtype)
+        vs = ctx.pack(torch.from_numpy(v).cuda(), dtype)
+        J = ctx.unpack(ctx.jvp(qs, vs)).cpu().numpy()
+        ok, rel, fs = parity_ok(J, Jref, m, q, tol)
+        assert ok, (name, str(dtype), rel, fs)
+
+
+@pytest.mark.parametrize("name", ["vortex2d_16x16_p2", "tgv_5^3_p3", "cylinder_4x12x2_mixed"])
+def test_fd_jv_parity(built, name):
+    """The paper's one-sided difference with eps = 1e-6 (FP64): R(q + eps v) - R(q)
+    cancels ~6 digits, so the rounding-order differences of the two residuals
+    (~1e-15 of the flux scale) reach ~1e-9..1e-7 of |Jv|; bound 1e-6."""
+    from oracle import linearize as L
+    m, q, ph, fr, ctx = _pair(name)
+    from cases import uniform
+    v = uniform(902, q.size) - 0.5
+    v = v / np.linalg.norm(v)
+    qt = torch.from_numpy(q)
+    Jref = L.fd_jv(fr, qt, torch.from_numpy(v), 1e-6).numpy()
+    qs = ctx.pack(qt.cuda())
+    vs = ctx.pack(torch.from_numpy(v).cuda())
+    J = ctx.unpack(ctx.jvp(qs, vs, mode="fd", eps=1e-6)).cpu().numpy()
+    assert rel_err(J, Jref) <= 1e-6
+
+
+def test_free_stream_on_gpu(built):
+    import cases
+    m = cases.naca_cgrid(24, 4, 2, n_wake=6, p=2)
+    m.nbr = m.nbr.copy()
+    m.nbr[m.nbr == cases.WALL] = cases.FARFIELD
+    qinf = cases.free_stream_q(3, vel=(0.3, 0.2, 0.1), mach=0.3)
+    ctx = gpu_ctx(m, dict(gamma=1.4, mu=1e-2, Pr=0.7, q_inf=qinf))
+    q = torch.from_numpy(cases.freestream_state(m, vel=(0.3, 0.2, 0.1), mach=0.3)).cuda()
+    R = ctx.residual(ctx.pack(q))
+    assert float(R.abs().max()) < 1e-12 * (1 / (1.4 * 0.09)) / 0.002
+
+
+def test_layout_roundtrip_and_buckets(built):
+    m, q, ph = WL["vortex_batch_5"]
+    ctx = gpu_ctx(m, ph)
+    qd = torch.from_numpy(q).cuda()
+    back = ctx.unpack(ctx.pack(qd))
+    assert torch.equal(back, qd)
+    counts = np.bincount(m.p, minlength=6)
+    assert ctx.bucket_count[: len(counts)] == counts.tolist()[:6]

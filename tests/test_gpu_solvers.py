@@ -1,0 +1,122 @@
+"""GPU parity of the VJP, GMRES and the ESDIRK stage against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import cases
+from helpers import gpu_ctx, oracle_fr, parity_ok, small_workloads
+
+pytestmark = pytest.mark.gpu
+
+WL = small_workloads()
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1910_03693_gb300 import build as B
+    B.build()
+    return True
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_vjp_parity(built, name):
+    """J^T w against the oracle's reverse-mode derivative (FP64 1e-12, FP32 2e-5)."""
+    from oracle import linearize as L
+    m, q, ph = WL[name]
+    fr, ctx = oracle_fr(m, ph), gpu_ctx(m, ph)
+    w = cases.uniform(903, q.size) - 0.5
+    ref = L.vjp(fr, torch.from_numpy(q), torch.from_numpy(w)).numpy()
+    tol64 = 1e-11 if name.startswith(("cylinder", "naca", "box_curved")) else 1e-12
+    for dtype, tol in ((torch.float64, tol64), (torch.float32, 2e-5)):
+        qs = ctx.pack(torch.from_numpy(q).cuda(), dtype)
+        ws = ctx.pack(torch.from_numpy(w).cuda(), dtype)
+        got = ctx.unpack(ctx.vjp(qs, ws)).cpu().numpy()
+        ok, rel, fs = parity_ok(got, ref, m, q, tol)
+        assert ok, (name, str(dtype), rel, fs)
+
+
+def test_vjp_dot_product_and_autograd(built):
+    """<w, J v> = <J^T w, v> on the GPU, and torch.autograd through the residual."""
+    from paper_1910_03693_gb300 import autograd_residual
+    m, q, ph = WL["diff_3^3_p4_mu0.05"]
+    ctx = gpu_ctx(m, ph)
+    qs = ctx.pack(torch.from_numpy(q).cuda())
+    v = torch.randn_like(qs)
+    w = torch.randn_like(qs)
+    lhs = float(torch.dot(w, ctx.jvp(qs, v)))
+    rhs = float(torch.dot(ctx.vjp(qs, w), v))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs) * 10
+    qg = qs.clone().requires_grad_(True)
+    R = autograd_residual(ctx, qg)
+    (g,) = torch.autograd.grad(R, qg, w)
+    assert torch.allclose(g, ctx.vjp(qs, w), rtol=0, atol=0)
+
+
+def _small_system():
+    m, q, ph = cases.workload_vortex2d(3, 2)
+    return m, cases.random_state(m, 2), ph
+
+
+def test_gmres_matches_dense_solve(built):
+    from oracle import linearize as L
+    m, q, ph = _small_system()
+    fr, ctx = oracle_fr(m, ph), gpu_ctx(m, ph)
+    qt = torch.from_numpy(q)
+    J = L.dense_jacobian(fr, qt)
+    sigma = 20.0
+    A = sigma * torch.eye(J.shape[0]) - J
+    b = torch.from_numpy(cases.uniform(4, J.shape[0]) - 0.5)
+    xref = torch.linalg.solve(A, b).numpy()
+    qs = ctx.pack(qt.cuda())
+    bs = ctx.pack(b.cuda())
+    x, st = ctx.gmres(qs, bs, sigma, mode="exact", rtol=1e-13, m=30, max_it=3000)
+    assert st["converged"] and st["restarts"] >= 1
+    xg = ctx.unpack(x).cpu().numpy()
+    assert np.abs(xg - xref).max() <= 1e-10 * np.abs(xref).max()
+
+
+def test_gmres_iterates_match_oracle(built):
+    """At the paper's tolerance (1e-1) the GPU (classical GS twice) and the oracle
+    (modified GS) build the same Krylov space: same iteration count, same x."""
+    from oracle import krylov
+    from oracle import linearize as L
+    m, q, ph = cases.workload_vortex2d(6, 2)
+    fr, ctx = oracle_fr(m, ph), gpu_ctx(m, ph)
+    qt = torch.from_numpy(q)
+    b = torch.from_numpy(cases.uniform(5, q.size) - 0.5)
+    sigma = 1.0 / (0.4358665215 * 0.05) + 1.0 / 0.05
+    xo, so = krylov.gmres(lambda v: sigma * v - L.jvp(fr, qt, v), b, m=30, rtol=1e-1, max_it=100)
+    qs = ctx.pack(qt.cuda())
+    x, st = ctx.gmres(qs, ctx.pack(b.cuda()), sigma, mode="exact", rtol=1e-1, m=30, max_it=100)
+    assert st["iterations"] == so["iterations"]
+    xg = ctx.unpack(x).cpu().numpy()
+    assert np.abs(xg - xo.numpy()).max() <= 1e-9 * np.abs(xo.numpy()).max()
+
+
+@pytest.mark.parametrize("mode,jv_dtype", [("fd", torch.float64), ("exact", torch.float64),
+                                           ("exact", torch.float32)])
+def test_esdirk3_stage_matches_oracle(built, mode, jv_dtype):
+    """Stage 2 of ESDIRK3 on the 2D vortex to ||F|| <= 1e-8 ||F0|| (the oracle
+    with the paper's FD Jv); the converged stage values agree to the tolerance."""
+    from oracle import esdirk
+    from oracle import linearize as L
+    m, q, ph = cases.workload_vortex2d(8, 2)
+    fr, ctx = oracle_fr(m, ph), gpu_ctx(m, ph)
+    tab = esdirk.esdirk3()
+    qn = torch.from_numpy(q)
+    Rn = fr.residual(qn)
+    opts = esdirk.NewtonOpts(tol=1e-8, dtau_init=0.05, dtau_max=10.0)
+    jv = lambda qq, v, Rq: L.fd_jv(fr, qq, v, 1e-6, Rq)
+    qo, Ro, so = esdirk.solve_stage(fr.residual, jv, qn, [Rn], 1, tab, 0.05, qn, opts)
+    qns = ctx.pack(qn.cuda())
+    R1 = ctx.residual(qns)
+    qi = qns.clone()
+    R2 = torch.empty_like(qns)
+    st = ctx.esdirk_stage(tab.A, 2, 0.05, qns, [R1, R2, None, None], qi, tol=1e-8, dtau_init=0.05,
+                          dtau_max=10.0, mode=mode, jv_dtype=jv_dtype)
+    assert st["converged"] and st["norm_final"] <= 1e-8 * st["norm0"]
+    qg = ctx.unpack(qi).cpu().numpy()
+    dq = np.abs(qo.numpy() - q).max()
+    assert np.abs(qg - qo.numpy()).max() <= 1e-6 * dq
+    assert abs(st["newton"] - so["newton"]) <= 2
+    assert torch.allclose(R2, ctx.residual(qi), rtol=0, atol=0)
