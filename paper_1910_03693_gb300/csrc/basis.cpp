@@ -89,6 +89,8 @@ void build_basis(int p, BasisTab<double>& t) {
   }
   t.dgf[0] = 0.5 * sgn * (legendre_dp(p, -1.0) - legendre_dp(p + 1, -1.0));
   t.dgf[1] = 0.5 * (legendre_dp(p, 1.0) + legendre_dp(p + 1, 1.0));
+  for (int i = 0; i < P; ++i)
+    for (int k = 0; k < P; ++k) t.Dh[i][k] = t.D[i][k] - t.dg[0][i] * t.ext[0][k] - t.dg[1][i] * t.ext[1][k];
   // modal transform by Gauss quadrature: c_m = (2m+1)/2 sum_i w_i P_m(x_i) s_i
   for (int m = 0; m < P; ++m)
     for (int i = 0; i < P; ++i) {

@@ -61,6 +61,20 @@ static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 
 // ---------------------------------------------------------------------------
 // dispatch helpers
 // ---------------------------------------------------------------------------
+template <typename T, int ND, int P, bool VISC>
+static void launch_trace_p(const TraceArgs<T>& a, cudaStream_t s) {
+  using Cfg = VolCfg<ND, P>;
+  constexpr int NV = ND + 2, NF = 2 * ND;
+  const size_t smem = (size_t)Cfg::EPB * (NV * Cfg::NSP + NF * NV * Shape<ND, P>::NFP) * sizeof(T);
+  auto kern = trace_kernel<T, ND, P, VISC>;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  kern<<<nblocks(a.count, Cfg::EPB), Cfg::THREADS, smem, s>>>(a);
+}
+
 template <typename T, int ND, bool VISC>
 static void launch_trace(fr_ctx* c, const Bucket& b, const T* q, T* trace, cudaStream_t s) {
   TraceArgs<T> a;
@@ -75,16 +89,14 @@ static void launch_trace(fr_ctx* c, const Bucket& b, const T* q, T* trace, cudaS
   a.slot_begin = b.slot_begin;
   a.nvt = c->nvt;
   const int P = b.p + 1;
-  const int64_t n = (int64_t)b.count * 2 * ND * ipow(P, ND - 1);
-  const unsigned g = nblocks(n, 256);
   const double nb = (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
   FR_LAUNCH_B(c, sizeof(T) == 8 ? "trace_f64" : "trace_f32", s, nb, {
     switch (P) {
-      case 2: trace_kernel<T, ND, 2, VISC><<<g, 256, 0, s>>>(a); break;
-      case 3: trace_kernel<T, ND, 3, VISC><<<g, 256, 0, s>>>(a); break;
-      case 4: trace_kernel<T, ND, 4, VISC><<<g, 256, 0, s>>>(a); break;
-      case 5: trace_kernel<T, ND, 5, VISC><<<g, 256, 0, s>>>(a); break;
-      case 6: trace_kernel<T, ND, 6, VISC><<<g, 256, 0, s>>>(a); break;
+      case 2: launch_trace_p<T, ND, 2, VISC>(a, s); break;
+      case 3: launch_trace_p<T, ND, 3, VISC>(a, s); break;
+      case 4: launch_trace_p<T, ND, 4, VISC>(a, s); break;
+      case 5: launch_trace_p<T, ND, 5, VISC>(a, s); break;
+      case 6: launch_trace_p<T, ND, 6, VISC>(a, s); break;
     }
   });
 }
@@ -192,12 +204,14 @@ static void residual_impl(fr_ctx* c, const T* q, T* R, cudaStream_t s) {
   for (const auto& b : c->buckets) launch_vol<T, ND, VISC, 0>(c, b, q, nullptr, R, s);
 }
 
+// JVP; with q_traces_ready the traces of q in d_trace_q are reused (q is
+// fixed during one GMRES solve)
 template <typename T, int ND, bool VISC>
-static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s) {
+static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready = false) {
   T* trq = (T*)c->d_trace_q;
   T* trv = (T*)c->d_trace_v;
   for (const auto& b : c->buckets) {
-    launch_trace<T, ND, VISC>(c, b, q, trq, s);
+    if (!q_traces_ready) launch_trace<T, ND, VISC>(c, b, q, trq, s);
     launch_trace<T, ND, VISC>(c, b, v, trv, s);
   }
   launch_faces<T, ND, VISC, 1>(c, trq, trv, s);
@@ -338,10 +352,12 @@ static fr_status run_op(fr_ctx* c, int op, const void* q, const void* v, void* o
       return FR_ERR_NOMEM;
     }
   }
-#define FR_OPS(ND, VISC)                                  \
-  if (op == 0) residual_impl<T, ND, VISC>(c, qq, oo, s);  \
-  else if (op == 1) jvp_impl<T, ND, VISC>(c, qq, vv, oo, s); \
-  else vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);
+#define FR_OPS(ND, VISC)                                                       \
+  if (op == 0) residual_impl<T, ND, VISC>(c, qq, oo, s);                       \
+  else if (op == 1) jvp_impl<T, ND, VISC>(c, qq, vv, oo, s);                   \
+  else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);                   \
+  else if (op == 3) { for (const auto& b : c->buckets) launch_trace<T, ND, VISC>(c, b, qq, (T*)c->d_trace_q, s); } \
+  else jvp_impl<T, ND, VISC>(c, qq, vv, oo, s, true);
   if (c->nd == 2) {
     if (c->visc) { FR_OPS(2, true) } else { FR_OPS(2, false) }
   } else {

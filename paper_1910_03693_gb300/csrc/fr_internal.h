@@ -26,6 +26,8 @@ struct BasisTab {
   T dgf[2];             // g_L'(-1) = -(p+1)^2/2, g_R'(+1) = (p+1)^2/2
   T modal[kPM][kPM];    // Legendre coefficients c_m = sum_i modal[m][i] s_i
   T nodal[kPM][kPM];    // s_i = sum_m nodal[i][m] c_m  (nodal[i][m] = P_m(x_i))
+  T Dh[kPM][kPM];       // D - g_L' (x) l(-1) - g_R' (x) l(+1): derivative with the local
+                        // end values removed, so div = Dh F + g_L' F^com_L + g_R' F^com_R
 };
 
 // Mortar operators from Ps slave points to Pm mortar points and back.

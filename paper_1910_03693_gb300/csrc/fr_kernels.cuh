@@ -107,71 +107,92 @@ struct TraceArgs {
   int count, slot_begin, nvt;
 };
 
+template <int ND, int P>
+struct VolCfg {
+  static constexpr int NSP = Shape<ND, P>::NSP;
+  static constexpr int EPB = NSP >= 256 ? 1 : 256 / NSP;
+  static constexpr int THREADS = EPB * NSP;
+};
+
+// One thread per solution point for the load, then per face point: the q
+// trace is extrapolated along the normal line (P terms), the normal
+// derivative uses l'(+-1) (P terms), and the two tangential derivatives
+// differentiate the face trace (P terms each); the physical gradient follows
+// from the face metric terms.
 template <typename T, int ND, int P, bool VISC>
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs<T> a) {
+__global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) trace_kernel(TraceArgs<T> a) {
   using Sh = Shape<ND, P>;
   constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)a.count * NF * NFP;
-  if (gid >= total) return;
-  const int t = (int)(gid % NFP);
-  const int f = (int)((gid / NFP) % NF);
-  const int64_t i = gid / (NFP * NF);
-  const int d = f >> 1, s = f & 1;
+  constexpr int EPB = VolCfg<ND, P>::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int le = threadIdx.x / NSP;
+  const int lt = threadIdx.x % NSP;
+  const int64_t i = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = i < a.count;
+  T* sq = sm + le * (NV * NSP + NF * NV * NFP);   // [NV][NSP]
+  T* sqf = sq + NV * NSP;                           // [NF][NV][NFP]
   const BasisTab<T>& B = a.basis[P];
-  const T* qe = a.q + a.state_base + i * NV * NSP;
-  T* out = a.trace + a.trace_base + (i * NF + f) * (int64_t)a.nvt * NFP;
+  if (valid) {
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    T acc = T(0);
-#pragma unroll
-    for (int k = 0; k < P; ++k) acc += B.ext[s][k] * qe[v * NSP + line_sp<ND, P>(d, t, k)];
-    out[v * NFP + t] = acc;
+    for (int v = 0; v < NV; ++v) sq[v * NSP + lt] = a.q[a.state_base + (i * NV + v) * NSP + lt];
   }
-  if (VISC) {
-    const int64_t e = a.slot_elem[a.slot_begin + i];
-    // reference derivatives at the face point: normal via l'(+-1), tangential by
-    // differentiating along d' at every line point, then extrapolating
-    T dq[ND][NV];
-    int ia = t % P, ib = t / P;   // tangential coordinates
-#pragma unroll
-    for (int dd = 0; dd < ND; ++dd) {
+  __syncthreads();
+  T* out = a.trace + a.trace_base + (valid ? i * NF * (int64_t)a.nvt * NFP : 0);
+  if (valid) {
+    for (int fp = lt; fp < NF * NFP; fp += NSP) {
+      const int f = fp / NFP, t = fp % NFP, d = f >> 1, s = f & 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         T acc = T(0);
-        if (dd == d) {
 #pragma unroll
-          for (int k = 0; k < P; ++k) acc += B.dext[s][k] * qe[v * NSP + line_sp<ND, P>(d, t, k)];
-        } else {
-          // dd is the first (ia) or second (ib) tangential axis of face d
-          int which = 0;
-          if (ND == 3) which = (dd == (d == 0 ? 1 : 0)) ? 0 : 1;
-          const int coord = which == 0 ? ia : ib;
-#pragma unroll
-          for (int k = 0; k < P; ++k) {
-            T inner = T(0);
-#pragma unroll
-            for (int m = 0; m < P; ++m) {
-              int tt = (which == 0) ? (m + P * ib) : (ia + P * m);
-              if (ND == 2) tt = m;
-              inner += B.D[coord][m] * qe[v * NSP + line_sp<ND, P>(d, tt, k)];
-            }
-            acc += B.ext[s][k] * inner;
-          }
-        }
-        dq[dd][v] = acc;
+        for (int k = 0; k < P; ++k) acc += B.ext[s][k] * sq[v * NSP + line_sp<ND, P>(d, t, k)];
+        out[(f * a.nvt + v) * NFP + t] = acc;
+        if (VISC) sqf[(f * NV + v) * NFP + t] = acc;
       }
     }
-    const T Jf = geo_face(a.geo, e, f, ND * ND, t);
+  }
+  if (!VISC) return;
+  __syncthreads();
+  if (!valid) return;
+  const int64_t e = a.slot_elem[a.slot_begin + i];
+  for (int fp = lt; fp < NF * NFP; fp += NSP) {
+    const int f = fp / NFP, t = fp % NFP, d = f >> 1, s = f & 1;
+    const int ia = t % P, ib = ND == 3 ? t / P : 0;
+    const int ta = d == 0 ? 1 : 0;              // first tangential direction
+    const int tb = d == 2 ? 1 : 2;              // second (3D)
+    T Sf[ND][ND];
 #pragma unroll
-    for (int j = 0; j < ND; ++j)
+    for (int dd = 0; dd < ND; ++dd)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        T acc = T(0);
+      for (int j = 0; j < ND; ++j) Sf[dd][j] = geo_face(a.geo, e, f, dd * ND + j, t);
+    const T Jinv = T(1) / geo_face(a.geo, e, f, ND * ND, t);
 #pragma unroll
-        for (int dd = 0; dd < ND; ++dd) acc += geo_face(a.geo, e, f, dd * ND + j, t) * dq[dd][v];
-        out[(NV + j * NV + v) * NFP + t] = acc / Jf;
+    for (int v = 0; v < NV; ++v) {
+      T dq[ND];
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) acc += B.dext[s][k] * sq[v * NSP + line_sp<ND, P>(d, t, k)];
+      dq[d] = acc;
+      const T* face = sqf + (f * NV + v) * NFP;
+      acc = T(0);
+#pragma unroll
+      for (int m = 0; m < P; ++m) acc += B.D[ia][m] * face[ND == 2 ? m : m + P * ib];
+      dq[ta] = acc;
+      if (ND == 3) {
+        acc = T(0);
+#pragma unroll
+        for (int m = 0; m < P; ++m) acc += B.D[ib][m] * face[ia + P * m];
+        dq[tb] = acc;
       }
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        T g = T(0);
+#pragma unroll
+        for (int dd = 0; dd < ND; ++dd) g += Sf[dd][j] * dq[dd];
+        out[(f * a.nvt + NV + j * NV + v) * NFP + t] = g * Jinv;
+      }
+    }
   }
 }
 
@@ -506,12 +527,6 @@ struct VolArgs {
   int count, slot_begin;
 };
 
-template <int ND, int P>
-struct VolCfg {
-  static constexpr int NSP = Shape<ND, P>::NSP;
-  static constexpr int EPB = NSP >= 256 ? 1 : 256 / NSP;
-  static constexpr int THREADS = EPB * NSP;
-};
 
 template <typename T, int ND, int P, bool VISC, int MODE>
 __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_kernel(VolArgs<T> a) {
@@ -549,13 +564,13 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_kernel(VolArgs<T> 
   __syncthreads();
 
   T Sm[ND][ND];
-  T J = T(1);
+  T Jinv = T(1);
   if (valid) {
 #pragma unroll
     for (int d = 0; d < ND; ++d)
 #pragma unroll
       for (int j = 0; j < ND; ++j) Sm[d][j] = geo_vol(a.geo, e, d * ND + j, sp);
-    J = geo_vol(a.geo, e, ND * ND, sp);
+    Jinv = T(1) / geo_vol(a.geo, e, ND * ND, sp);
 
     S f[ND][NV];
     flux_inviscid<ND>(q, a.gamma, f);
@@ -589,7 +604,7 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_kernel(VolArgs<T> 
           S acc = szero<S>();
 #pragma unroll
           for (int d = 0; d < ND; ++d) acc = acc + Sm[d][j] * gref[d][v];
-          G[j][v] = acc / J;
+          G[j][v] = acc * Jinv;
         }
       S fv[ND][NV];
       flux_viscous<ND>(q, G, a.gamma, a.mu, a.kappa, fv);
@@ -626,23 +641,20 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_kernel(VolArgs<T> 
       const S* line = sF + (d * NV + v) * NSP + base;
       S acc = szero<S>();
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc = acc + B.D[idx[d]][k] * line[k * stride];
+      for (int k = 0; k < P; ++k) acc = acc + B.Dh[idx[d]][k] * line[k * stride];
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        S loc = szero<S>();
-#pragma unroll
-        for (int k = 0; k < P; ++k) loc = loc + B.ext[s][k] * line[k * stride];
         S com;
         const T c = fo[(2 * d + s) * FOUT_STRIDE + v * NFP + tf];
         if (MODE == 1) set_scalar(com, T(0), c); else set_scalar(com, c, T(0));
-        acc = acc + B.dg[s][idx[d]] * (com - loc);
+        acc = acc + B.dg[s][idx[d]] * com;
       }
       div[v] = div[v] + acc;
     }
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    S r = (T(0) - div[v]) / J;
+    S r = (T(0) - div[v]) * Jinv;
     a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
   }
 }

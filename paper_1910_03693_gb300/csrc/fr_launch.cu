@@ -21,6 +21,14 @@ fr_status launch_jvp_exact(fr_ctx* c, const void* q, const void* v, void* Jv, fr
   return prec == FR_F64 ? run_op_f64(c, 1, q, v, Jv, s) : run_op_f32(c, 1, q, v, Jv, s);
 }
 
+fr_status launch_jvp_prepare(fr_ctx* c, const void* q, fr_prec prec, cudaStream_t s) {
+  return prec == FR_F64 ? run_op_f64(c, 3, q, nullptr, nullptr, s) : run_op_f32(c, 3, q, nullptr, nullptr, s);
+}
+
+fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec, cudaStream_t s) {
+  return prec == FR_F64 ? run_op_f64(c, 4, q, v, Jv, s) : run_op_f32(c, 4, q, v, Jv, s);
+}
+
 fr_status launch_vjp(fr_ctx* c, const void* q, const void* w, void* JTw, fr_prec prec, cudaStream_t s) {
   return prec == FR_F64 ? run_op_f64(c, 2, q, w, JTw, s) : run_op_f32(c, 2, q, w, JTw, s);
 }

@@ -16,9 +16,13 @@ void vdiff_scaled(fr_ctx* c, const double* x, const double* y, double a, double*
 void vcast_f64_f32(fr_ctx* c, const double* x, float* y, int64_t n, cudaStream_t s);
 void vcast_f32_f64(fr_ctx* c, const float* x, double* y, int64_t n, cudaStream_t s);
 
-// op 0: out = R(q); op 1: out = J(q) v (exact); op 2: out = J(q)^T v.
+// op 0: out = R(q); op 1: out = J(q) v (exact); op 2: out = J(q)^T v;
+// op 3: traces of q only (prepares op 4); op 4: J(q) v reusing those traces.
 fr_status run_op_f64(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 fr_status run_op_f32(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
+
+fr_status launch_jvp_prepare(fr_ctx* c, const void* q, fr_prec prec, cudaStream_t s);
+fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec, cudaStream_t s);
 
 // Jv = (R(q + eps v) - R0) / eps in FP64; R0 = R(q) is computed when null.
 fr_status launch_fd_jv(fr_ctx* c, const double* q, const double* v, double* Jv, double eps,

@@ -49,6 +49,11 @@ template <typename T>
 __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
 template <typename T>
 __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { return {a.v / b, a.d / b}; }
+template <typename T>
+__device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) {
+  T r = a / b.v;
+  return {r, -r * b.d / b.v};
+}
 
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
@@ -80,14 +85,14 @@ __device__ __forceinline__ void set_scalar(Dual<T>& x, T v, T d) { x.v = v; x.d 
 template <int ND, typename S, typename T>
 __device__ __forceinline__ void flux_inviscid(const S* q, T gamma, S (*f)[ND + 2]) {
   constexpr int NV = ND + 2;
-  S rho = q[0];
+  const S rinv = T(1) / q[0];
   S vel[ND];
-  S ke = szero<S>();
+  S mu2 = szero<S>();
 #pragma unroll
-  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] / rho;
+  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] * rinv;
 #pragma unroll
-  for (int i = 0; i < ND; ++i) ke = ke + vel[i] * vel[i];
-  S pres = (gamma - T(1)) * (q[NV - 1] - T(0.5) * rho * ke);
+  for (int i = 0; i < ND; ++i) mu2 = mu2 + q[1 + i] * vel[i];
+  const S pres = (gamma - T(1)) * (q[NV - 1] - T(0.5) * mu2);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     f[j][0] = q[1 + j];
@@ -101,43 +106,39 @@ __device__ __forceinline__ void flux_inviscid(const S* q, T gamma, S (*f)[ND + 2
   }
 }
 
-// |u.n| + c
+// Normal flux f(q).n and the wave speed |u.n| + c of one state (one reciprocal,
+// one square root).
 template <int ND, typename S, typename T>
-__device__ __forceinline__ S wave_speed(const S* q, const T* n, T gamma) {
+__device__ __forceinline__ S normal_flux(const S* q, const T* n, T gamma, S* fn) {
   constexpr int NV = ND + 2;
-  S rho = q[0];
-  S vel[ND];
-  S ke = szero<S>(), un = szero<S>();
+  const S rinv = T(1) / q[0];
+  S mn = szero<S>(), mu2 = szero<S>();
 #pragma unroll
-  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] / rho;
+  for (int i = 0; i < ND; ++i) {
+    mn = mn + q[1 + i] * n[i];
+    mu2 = mu2 + q[1 + i] * q[1 + i];
+  }
+  const S un = mn * rinv;
+  const S pres = (gamma - T(1)) * (q[NV - 1] - T(0.5) * mu2 * rinv);
+  fn[0] = mn;
 #pragma unroll
-  for (int i = 0; i < ND; ++i) ke = ke + vel[i] * vel[i];
-#pragma unroll
-  for (int i = 0; i < ND; ++i) un = un + vel[i] * n[i];
-  S pres = (gamma - T(1)) * (q[NV - 1] - T(0.5) * rho * ke);
-  S c = dsqrt(gamma * pres / rho);
-  return dabs(un) + c;
+  for (int i = 0; i < ND; ++i) fn[1 + i] = q[1 + i] * un + pres * n[i];
+  fn[NV - 1] = (q[NV - 1] + pres) * un;
+  return dabs(un) + dsqrt(gamma * pres * rinv);
 }
 
-// Rusanov normal flux times the face area: ((fL.n + fR.n)/2 - lam/2 (qR - qL)) |A|.
+// Rusanov normal flux times the face area: ((fL.n + fR.n)/2 - lam/2 (qR - qL)) |A|,
+// lam = max(|u.n| + c) over the two sides (the "-" side at a tie).
 template <int ND, typename S, typename T>
 __device__ __forceinline__ void rusanov(const S* qL, const S* qR, const T* n, T absA, T gamma,
                                         S* Fn) {
   constexpr int NV = ND + 2;
-  S fL[ND][NV], fR[ND][NV];
-  flux_inviscid<ND>(qL, gamma, fL);
-  flux_inviscid<ND>(qR, gamma, fR);
-  S lam = dmax(wave_speed<ND>(qL, n, gamma), wave_speed<ND>(qR, n, gamma));
+  S fL[NV], fR[NV];
+  const S lamL = normal_flux<ND>(qL, n, gamma, fL);
+  const S lamR = normal_flux<ND>(qR, n, gamma, fR);
+  const S lam = dmax(lamL, lamR);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    S a = szero<S>(), b = szero<S>();
-#pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      a = a + fL[j][v] * n[j];
-      b = b + fR[j][v] * n[j];
-    }
-    Fn[v] = (T(0.5) * (a + b) - T(0.5) * lam * (qR[v] - qL[v])) * absA;
-  }
+  for (int v = 0; v < NV; ++v) Fn[v] = (T(0.5) * (fL[v] + fR[v]) - T(0.5) * lam * (qR[v] - qL[v])) * absA;
 }
 
 // Viscous flux fv[j][v] from q and its physical gradient G[j][v]:
@@ -146,20 +147,20 @@ template <int ND, typename S, typename T>
 __device__ __forceinline__ void flux_viscous(const S* q, const S (*G)[ND + 2], T gamma, T mu,
                                              T kappa, S (*fv)[ND + 2]) {
   constexpr int NV = ND + 2;
-  S rho = q[0];
+  const S rinv = T(1) / q[0];
   S vel[ND];
 #pragma unroll
-  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] / rho;
-  S Es = q[NV - 1] / rho;
+  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] * rinv;
+  const S Es = q[NV - 1] * rinv;
   S du[ND][ND];
 #pragma unroll
   for (int i = 0; i < ND; ++i)
 #pragma unroll
-    for (int j = 0; j < ND; ++j) du[i][j] = (G[j][1 + i] - vel[i] * G[j][0]) / rho;
+    for (int j = 0; j < ND; ++j) du[i][j] = (G[j][1 + i] - vel[i] * G[j][0]) * rinv;
   S dT[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    S dE = (G[j][NV - 1] - Es * G[j][0]) / rho;
+    S dE = (G[j][NV - 1] - Es * G[j][0]) * rinv;
     S s = szero<S>();
 #pragma unroll
     for (int k = 0; k < ND; ++k) s = s + vel[k] * du[k][j];

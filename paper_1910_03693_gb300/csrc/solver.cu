@@ -18,41 +18,88 @@ constexpr int kRedBlocks = 304;     // 2 blocks per SM on 152 SMs
 constexpr int kRedThreads = 256;
 constexpr int kMaxK = 64;           // most vectors in one multi-dot (restart length + 1)
 
+// reduction scratch: per-block partials [kRedBlocks][kMaxK], then the reduced
+// values H1 (first Gram-Schmidt pass), H2 (second pass) and ||w||^2
+constexpr int64_t kOutH1 = (int64_t)kRedBlocks * kMaxK;
+constexpr int64_t kOutH2 = kOutH1 + kMaxK;
+constexpr int64_t kOutN = kOutH2 + kMaxK;
+constexpr int64_t kOutY = kOutN + kMaxK;
+
 static fr_status ensure_red(fr_ctx* c) {
   if (c->d_red) return FR_OK;
-  c->red_cap = (int64_t)kRedBlocks * kMaxK + 2 * kMaxK;
+  c->red_cap = kOutY + kMaxK;
   if (cudaMalloc(&c->d_red, sizeof(double) * c->red_cap) != cudaSuccess) return FR_ERR_NOMEM;
-  if (cudaMallocHost(&c->h_red, sizeof(double) * 2 * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
+  if (cudaMallocHost(&c->h_red, sizeof(double) * 4 * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
   return FR_OK;
 }
 
-// partial[block][kk] = sum_i V[kk][i] * w[i]  (kk < k), or ||w||^2 when V == nullptr
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int k,
-                                                           const double* __restrict__ w, int64_t n,
-                                                           double* __restrict__ partial) {
-  __shared__ double red[kRedThreads / 32][kMaxK];
-  double acc[kMaxK];
-  for (int kk = 0; kk < k; ++kk) acc[kk] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = w[i];
-    if (V) {
-      for (int kk = 0; kk < k; ++kk) acc[kk] += V[kk * ldv + i] * wi;
-    } else {
-      acc[0] += wi * wi;
-    }
-  }
+// block reduction of KC accumulators (kk < k) into partial[block][kk]
+template <int KC>
+__device__ __forceinline__ void block_partials(const double* acc, int k, double* __restrict__ partial) {
+  __shared__ double red[kRedThreads / 32][KC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int kk = 0; kk < k; ++kk) {
-    double v = acc[kk];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][kk] = v;
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) {
+    if (kk < k) {
+      double v = acc[kk];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][kk] = v;
+    }
   }
   __syncthreads();
   if (threadIdx.x < k) {
     double s = 0.0;
+#pragma unroll
     for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) s += red[wgi][threadIdx.x];
     partial[(int64_t)blockIdx.x * kMaxK + threadIdx.x] = s;
   }
+}
+
+// partial[block][kk] = sum_i V[kk][i] w[i] (kk < k); with V == nullptr, ||w||^2
+template <int KC>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int k,
+                                                           const double* __restrict__ w, int64_t n,
+                                                           double* __restrict__ partial) {
+  double acc[KC];
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    if (V) {
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk)
+        if (kk < k) acc[kk] += V[kk * ldv + i] * wi;
+    } else {
+      acc[0] += wi * wi;
+    }
+  }
+  block_partials<KC>(acc, V ? k : 1, partial);
+}
+
+// first pass update fused with the second pass dots:
+// w <- w - sum_kk h[kk] V[kk];  partial[block][kk] = sum_i V[kk][i] w_new[i]
+template <int KC>
+__global__ void __launch_bounds__(kRedThreads) k_update_dot(const double* __restrict__ V, int64_t ldv, int k,
+                                                             const double* __restrict__ h, double* __restrict__ w,
+                                                             int64_t n, double* __restrict__ partial) {
+  __shared__ double hs[KC];
+  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < k ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[KC];
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = w[i];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk)
+      if (kk < k) x -= hs[kk] * V[kk * ldv + i];
+    w[i] = x;
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk)
+      if (kk < k) acc[kk] += V[kk * ldv + i] * x;   // second read of V[kk][i]: an L1 hit
+  }
+  block_partials<KC>(acc, k, partial);
 }
 
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int k, double* __restrict__ out) {
@@ -63,32 +110,33 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nb, in
   out[kk] = s;
 }
 
-// w -= sum_kk h[kk] V[kk];  optionally partial[block] = ||w_new||^2
+// second pass update: w <- w - sum_kk h[kk] V[kk]; partial[block][0] = ||w_new||^2
+template <int KC>
 __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __restrict__ V, int64_t ldv, int k,
                                                               const double* __restrict__ h, double* __restrict__ w,
                                                               int64_t n, double* __restrict__ partial) {
-  __shared__ double hs[kMaxK];
-  __shared__ double red[kRedThreads / 32];
-  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+  __shared__ double hs[KC];
+  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < k ? h[threadIdx.x] : 0.0;
   __syncthreads();
-  double acc = 0.0;
+  double acc[1] = {0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double x = w[i];
-    for (int kk = 0; kk < k; ++kk) x -= hs[kk] * V[kk * ldv + i];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk)
+      if (kk < k) x -= hs[kk] * V[kk * ldv + i];
     w[i] = x;
-    acc += x * x;
+    acc[0] += x * x;
   }
-  if (partial) {
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) s += red[wgi];
-      partial[(int64_t)blockIdx.x * kMaxK] = s;
-    }
-  }
+  block_partials<1>(acc, 1, partial);
 }
+
+#define FR_KC_DISPATCH(k, KERNEL, ...)                                   \
+  do {                                                                   \
+    if ((k) <= 8) KERNEL<8><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);        \
+    else if ((k) <= 16) KERNEL<16><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__); \
+    else if ((k) <= 32) KERNEL<32><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__); \
+    else KERNEL<64><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);                \
+  } while (0)
 
 __global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -131,9 +179,10 @@ static unsigned egrid(int64_t n) {
 static fr_status multidot(fr_ctx* c, const double* V, int64_t ldv, int k, const double* w, int64_t n,
                           double* out_host, cudaStream_t s) {
   double* part = c->d_red;
-  double* dout = c->d_red + (int64_t)kRedBlocks * kMaxK;
-  FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1), k_multidot<<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, V ? k : 1, w, n, part));
-  FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, V ? k : 1, dout));
+  double* dout = c->d_red + kOutH1;
+  const int kk = V ? k : 1;
+  FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1), FR_KC_DISPATCH(kk, k_multidot, V, ldv, kk, w, n, part));
+  FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, kk, dout));
   cudaMemcpyAsync(c->h_red, dout, sizeof(double) * (V ? k : 1), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "multidot");
   std::memcpy(out_host, c->h_red, sizeof(double) * (V ? k : 1));
@@ -160,7 +209,7 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
   } else if (op->jv_prec == FR_F64) {
     double* J = vec64(c, 3);
     if (!J) return FR_ERR_NOMEM;
-    fr_status st = launch_jvp_exact(c, op->q64_dev, x, J, FR_F64, s);
+    fr_status st = launch_jvp_prepared(c, op->q64_dev, x, J, FR_F64, s);
     if (st != FR_OK) return st;
     FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_shift<double><<<egrid(n), 256, 0, s>>>(op->sigma, x, J, y, n));
   } else {
@@ -169,7 +218,7 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
     float* J32 = vec32(c, 2);
     if (!q32 || !x32 || !J32) return FR_ERR_NOMEM;
     vcast_f64_f32(c, x, x32, n, s);
-    fr_status st = launch_jvp_exact(c, q32, x32, J32, FR_F32, s);
+    fr_status st = launch_jvp_prepared(c, q32, x32, J32, FR_F32, s);
     if (st != FR_OK) return st;
     FR_LAUNCH_B(c, "vec", s, 20.0 * n, k_shift<float><<<egrid(n), 256, 0, s>>>(op->sigma, x, J32, y, n));
   }
@@ -182,7 +231,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   const int m = o->m;
   const int64_t n = c->n_dof, ld = c->n_dof_cap;
   if (m < 1 || m + 1 > kMaxK || o->max_it < 1 || !(o->rtol > 0.0)) {
-    set_error("gmres_solve: need 1 <= m < 64, max_it >= 1, rtol > 0");
+    set_error("gmres_solve: need 1 <= m <= 63, max_it >= 1, rtol > 0");
     return FR_ERR_INVALID;
   }
   if (ensure_red(c) != FR_OK) return FR_ERR_NOMEM;
@@ -199,11 +248,16 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     float* q32 = vec32(c, 0);
     if (!q32) return FR_ERR_NOMEM;
     vcast_f64_f32(c, op->q64_dev, q32, n, s);
+    fr_status ps = launch_jvp_prepare(c, q32, FR_F32, s);
+    if (ps != FR_OK) return ps;
+  } else if (op->mode == FR_JV_EXACT) {
+    fr_status ps = launch_jvp_prepare(c, op->q64_dev, FR_F64, s);
+    if (ps != FR_OK) return ps;
   }
   double* V = c->d_krylov;
   double* w = vec64(c, 4);
   double* r = vec64(c, 5);
-  double* ydev = c->d_red + (int64_t)kRedBlocks * kMaxK + kMaxK;
+  double* ydev = c->d_red + kOutY;
   if (!w || !r) return FR_ERR_NOMEM;
   std::memset(st, 0, sizeof(*st));
   cudaMemsetAsync(x, 0, sizeof(double) * n, s);
@@ -243,17 +297,27 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     for (int j = 0; j < m; ++j) {
       if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s)) != FR_OK) return e;
       ++it;
-      // classical Gram-Schmidt, twice
-      if ((e = multidot(c, V, ld, j + 1, w, n, h.data(), s)) != FR_OK) return e;
-      cudaMemcpyAsync(ydev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s);
-      FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (j + 3), k_orth_update<<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j + 1, ydev, w, n, nullptr));
-      if ((e = multidot(c, V, ld, j + 1, w, n, h2.data(), s)) != FR_OK) return e;
-      cudaMemcpyAsync(ydev, h2.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s);
-      FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (j + 3), k_orth_update<<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j + 1, ydev, w, n, c->d_red));
-      FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(c->d_red, kRedBlocks, 1, c->d_red + (int64_t)kRedBlocks * kMaxK));
-      cudaMemcpyAsync(c->h_red, c->d_red + (int64_t)kRedBlocks * kMaxK, sizeof(double), cudaMemcpyDeviceToHost, s);
-      if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
-      const double hn = std::sqrt(c->h_red[0]);
+      // classical Gram-Schmidt, twice; the coefficients stay on the device and
+      // come back to the host once per iteration with ||w||^2
+      {
+        const int kk = j + 1;
+        double* part = c->d_red;
+        FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1), FR_KC_DISPATCH(kk, k_multidot, V, ld, kk, w, n, part));
+        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, kk, c->d_red + kOutH1));
+        FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
+                    FR_KC_DISPATCH(kk, k_update_dot, V, ld, kk, c->d_red + kOutH1, w, n, part));
+        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, kk, c->d_red + kOutH2));
+        FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
+                    FR_KC_DISPATCH(kk, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part));
+        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, 1, c->d_red + kOutN));
+        cudaMemcpyAsync(c->h_red, c->d_red + kOutH1, sizeof(double) * 3 * kMaxK, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
+        for (int i = 0; i <= j; ++i) {
+          h[i] = c->h_red[i];
+          h2[i] = c->h_red[kMaxK + i];
+        }
+      }
+      const double hn = std::sqrt(c->h_red[2 * kMaxK]);
       for (int i = 0; i <= j; ++i) H[i * m + j] = h[i] + h2[i];
       H[(j + 1) * m + j] = hn;
       if (!std::isfinite(hn)) {

@@ -20,11 +20,11 @@ template <int ND, typename T>
 __device__ __forceinline__ void viscous_adjoint_G(const T* q, const T (*fb)[ND + 2], T gamma, T mu,
                                                   T kappa, T (*Gb)[ND + 2]) {
   constexpr int NV = ND + 2;
-  const T rho = q[0];
+  const T rinv = T(1) / q[0];
   T vel[ND];
 #pragma unroll
-  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] / rho;
-  const T Es = q[NV - 1] / rho;
+  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] * rinv;
+  const T Es = q[NV - 1] * rinv;
   T taub[ND][ND], dub[ND][ND], dTb[ND], dEb[ND];
 #pragma unroll
   for (int i = 0; i < ND; ++i)
@@ -51,11 +51,11 @@ __device__ __forceinline__ void viscous_adjoint_G(const T* q, const T (*fb)[ND +
     T g0 = -Es * dEb[j];
 #pragma unroll
     for (int i = 0; i < ND; ++i) {
-      Gb[j][1 + i] = dub[i][j] / rho;
+      Gb[j][1 + i] = dub[i][j] * rinv;
       g0 -= vel[i] * dub[i][j];
     }
-    Gb[j][0] = g0 / rho;
-    Gb[j][NV - 1] = dEb[j] / rho;
+    Gb[j][0] = g0 * rinv;
+    Gb[j][NV - 1] = dEb[j] * rinv;
   }
 }
 

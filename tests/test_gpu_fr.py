@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import gpu_ctx, oracle_fr, parity_ok, rel_err, small_workloads
+from helpers import generic_state, gpu_ctx, oracle_fr, parity_ok, rel_err, small_workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +61,7 @@ def test_residual_parity_fp64_fp32(built, name):
 def test_exact_jvp_parity(built, name):
     from oracle import linearize as L
     m, q, ph, fr, ctx = _pair(name)
+    q = generic_state(q)
     qt = torch.from_numpy(q)
     from cases import uniform
     v = (uniform(901, q.size) - 0.5) * np.abs(q).mean()

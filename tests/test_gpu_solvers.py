@@ -4,7 +4,7 @@ import pytest
 import torch
 
 import cases
-from helpers import gpu_ctx, oracle_fr, parity_ok, small_workloads
+from helpers import generic_state, gpu_ctx, oracle_fr, parity_ok, small_workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -23,6 +23,7 @@ def test_vjp_parity(built, name):
     """J^T w against the oracle's reverse-mode derivative (FP64 1e-12, FP32 2e-5)."""
     from oracle import linearize as L
     m, q, ph = WL[name]
+    q = generic_state(q)
     fr, ctx = oracle_fr(m, ph), gpu_ctx(m, ph)
     w = cases.uniform(903, q.size) - 0.5
     ref = L.vjp(fr, torch.from_numpy(q), torch.from_numpy(w)).numpy()
