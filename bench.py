@@ -115,6 +115,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def reduce_over_ranks(total_ms, units, dist=None):
+    """Replicas: the job time is the slowest rank's, the work is the sum of all
+    ranks' units.  Returns (total_ms, units)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(total_ms), float(units)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def build_workload(n=32, p=3):
     import cases
     m, q, ph = cases.workload_tgv(n, p)
@@ -251,13 +265,7 @@ def main():
 
     n_evals = sum(v[0] for k, v in report.items() if k.startswith("vol_res") or k.startswith("vol_jvp"))
     units = N * n_evals                       # DOF-evaluations over the K steps on this rank
-    t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, units = float(tmax[0]), float(tsum[1])
+    total_ms, units = reduce_over_ranks(total_ms, units, dist if world > 1 else None)
     value = units / (total_ms / 1e3) / 1e9
 
     # roofline of the dominant kernel (largest device time in the timed region)

@@ -137,3 +137,27 @@ def test_pseudo_transient_stage_reaches_tolerance():
     w = tab.A[1][1]
     F = -q2 / (w * 0.05) + fr.residual(q2) + (qn + 0.05 * tab.A[1][0] * Rn) / (w * 0.05)
     assert float(torch.linalg.vector_norm(F)) <= 1.01e-8 * st["norms"][0]
+
+
+def test_symmetric_taylor_green_sits_on_rusanov_ties():
+    """The Taylor-Green state (rho w = 0) puts faces exactly on the kinks of
+    |u.n| and max(lam-, lam+): central differences of R do not converge to the
+    JVP there, while a seeded additive perturbation restores the V-curve."""
+    import cases as C
+    m, q, ph = C.workload_tgv(3, 2)
+    fr = FR(m, Euler(3, ph["gamma"], ph["mu"], ph["Pr"]))
+
+    def best_fd_error(qq):
+        qt = torch.from_numpy(qq)
+        v = torch.from_numpy((C.uniform(901, qq.size) - 0.5) * np.abs(qq).mean())
+        J = L.jvp(fr, qt, v)
+        errs = []
+        for k in range(4, 9):
+            eps = 10.0 ** -k
+            fd = (fr.residual(qt + eps * v) - fr.residual(qt - eps * v)) / (2 * eps)
+            errs.append(float((fd - J).abs().max() / J.abs().max()))
+        return min(errs)
+
+    assert best_fd_error(q) > 1e-6
+    qg = q + 1e-3 * np.abs(q).mean() * (2.0 * C.uniform(77, q.size) - 1.0)
+    assert best_fd_error(qg) < 1e-7
