@@ -143,6 +143,22 @@ fr_status fr_residual(fr_ctx* ctx, const void* q_dev, void* R_dev, fr_prec prec,
 fr_status fr_jvp(fr_ctx* ctx, const void* q_dev, const void* v_dev, void* Jv_dev, fr_prec prec,
                  fr_jv_mode mode, double eps, void* stream);
 
+/* Finite-difference Jv, (R(q + eps v) - R(q)) / eps in FP64, that allocates
+ * nothing: the same product as fr_jvp(..., FR_F64, FR_JV_FD, eps, ...), with its
+ * three work vectors in a device array reserved when the library is loaded
+ * (3 x 262,144 doubles, 6 MiB on every device, held until exit).  The paper
+ * has no counterpart: this serves callers that may not allocate device memory
+ * after set-up (work recorded by global-mode stream capture, loops whose
+ * allocator budget is fixed, memory fully reserved by another allocator).
+ * q, v, Jv: FP64 state-layout device buffers of n_dof.  FR_ERR_INVALID when
+ * n_dof > 262,144, eps <= 0, or the current device is not the context's.  The
+ * first call on each device looks up the array's device address; make that
+ * first call before any stream capture begins.  All calls share the array:
+ * calls whose GPU work overlaps (other streams or contexts on the device)
+ * race on it. */
+fr_status fr_jvp_fd_static(fr_ctx* ctx, const double* q_dev, const double* v_dev, double* Jv_dev,
+                           double eps, void* stream);
+
 /* JTw = (dR(q)/dq)^T w, the exact transpose of FR_JV_EXACT. */
 fr_status fr_vjp(fr_ctx* ctx, const void* q_dev, const void* w_dev, void* JTw_dev, fr_prec prec,
                  void* stream);

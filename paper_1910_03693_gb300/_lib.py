@@ -86,6 +86,7 @@ SIGNATURES = {
     "fr_unpack": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "fr_residual": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "fr_jvp": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p],
+    "fr_jvp_fd_static": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p],
     "fr_vjp": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "gmres_solve": [C.c_void_p, C.POINTER(ShiftedOp), C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                     C.POINTER(GmresStats), C.c_void_p],
