@@ -41,6 +41,28 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# ALU peaks derived from unit counts and the maximum SM clock: 152 SMs x 2 FP64
+# FMA units x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s), and 152 x 128 FP32
+# lanes x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def kernel_roofline(name, launches, ms, nbytes, nflops, hbm_gbs):
+    """Bound, achieved, peak and fraction of one kernel from its algorithmic bytes
+    and operations: the roofline it reaches first decides the bound."""
+    t = ms / 1e3
+    alu_peak = FP64_PEAK_TFLOPS if name.endswith("f64") else FP32_PEAK_TFLOPS
+    t_hbm = nbytes / (hbm_gbs * 1e9)
+    t_alu = nflops / (alu_peak * 1e12)
+    if t_alu > t_hbm:
+        ach = nflops / t / 1e12 if t > 0 else 0.0
+        return {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                "alu": "fp64" if name.endswith("f64") else "fp32"}
+    ach = nbytes / t / 1e9 if t > 0 else 0.0
+    return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs}
+
+
 def _csrc_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1910_03693_gb300", "csrc")
@@ -271,14 +293,17 @@ def main():
     # roofline of the dominant kernel (largest device time in the timed region)
     peak, peak_kind = _peaks()
     kern = max(report, key=lambda k: report[k][1])
-    cnt, ms, nbytes = report[kern]
-    achieved = (nbytes / cnt) / (ms / cnt / 1e3) / 1e9 if nbytes > 0 else 0.0
-    roof = {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": _traffic_for(kern), "peak_source": peak_kind,
-            "share_of_step": ms / total_ms}
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4),
-                   "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 and v[2] > 0 else None}
-               for k, v in sorted(report.items(), key=lambda kv: -kv[1][1])}
+    cnt, ms, nbytes, nflops = report[kern]
+    roof = kernel_roofline(kern, cnt, ms, nbytes, nflops, peak)
+    roof.update({"kernel": kern, "traffic": _traffic_for(kern), "hbm_peak_source": peak_kind,
+                 "share_of_step": ms / total_ms, "per_launch_ms": ms / cnt})
+    kernels = {}
+    for k, v in sorted(report.items(), key=lambda kv: -kv[1][1]):
+        r = kernel_roofline(k, *v, peak) if (v[2] > 0 or v[3] > 0) else None
+        kernels[k] = {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4),
+                      "bound": r["bound"] if r else None,
+                      "achieved": round(r["achieved"], 2) if r else None,
+                      "unit": r["unit"] if r else None, "frac": round(r["frac"], 4) if r else None}
 
     # end to end through the public API: host canonical state in, host state out
     out_host = torch.empty(N, dtype=torch.float64).pin_memory()

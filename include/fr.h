@@ -262,8 +262,10 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
  * recording a pair of CUDA events on the launch stream around every kernel
  * the library launches; fr_timing(ctx, 0) stops recording.  The launch
  * counter runs in both states.  fr_timing_report synchronises the device and
- * writes one line per kernel, "name launches total_ms algorithmic_bytes" (the
- * minimum bytes the launches had to move, as counted by each launch site), into buf (len bytes,
+ * writes one line per kernel, "name launches total_ms algorithmic_bytes
+ * algorithmic_flops" (the minimum bytes the launches had to move and, for the
+ * FP64 residual kernels, the operations of the operator as formulated, as
+ * counted by each launch site), into buf (len bytes,
  * FR_ERR_INVALID if too small) and the number of launches since the last
  * fr_timing call into *launches (optional). */
 fr_status fr_timing(fr_ctx* ctx, int32_t enable);

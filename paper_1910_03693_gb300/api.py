@@ -167,14 +167,15 @@ class FRContext:
         _check(lib().fr_timing(self.h, 1 if enable else 0), "fr_timing")
 
     def timing_report(self):
-        """{kernel name: (launches, total device ms, algorithmic bytes)} and the launch count."""
+        """{kernel name: (launches, total device ms, algorithmic bytes, algorithmic flops)} and
+        the launch count."""
         buf = C.create_string_buffer(1 << 16)
         n = C.c_int64(0)
         _check(lib().fr_timing_report(self.h, buf, len(buf), C.byref(n)), "fr_timing_report")
         out = {}
         for line in buf.value.decode().splitlines():
-            name, cnt, ms, nbytes = line.split()
-            out[name] = (int(cnt), float(ms), float(nbytes))
+            name, cnt, ms, nbytes, nflops = line.split()
+            out[name] = (int(cnt), float(ms), float(nbytes), float(nflops))
         return out, int(n.value)
 
     # --------------------------------------------------------------- solvers

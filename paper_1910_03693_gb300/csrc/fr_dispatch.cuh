@@ -90,7 +90,8 @@ static void launch_trace(fr_ctx* c, const Bucket& b, const T* q, T* trace, cudaS
   a.nvt = c->nvt;
   const int P = b.p + 1;
   const double nb = (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
-  FR_LAUNCH_B(c, sizeof(T) == 8 ? "trace_f64" : "trace_f32", s, nb, {
+  const double nfl = (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC);
+  FR_LAUNCH_BF(c, sizeof(T) == 8 ? "trace_f64" : "trace_f32", s, nb, nfl, {
     switch (P) {
       case 2: launch_trace_p<T, ND, 2, VISC>(a, s); break;
       case 3: launch_trace_p<T, ND, 3, VISC>(a, s); break;
@@ -116,7 +117,8 @@ static void launch_vol_p(fr_ctx* c, const VolArgs<T>& a, cudaStream_t s) {
   const char* name = MODE == 1 ? (sizeof(T) == 8 ? "vol_jvp_f64" : "vol_jvp_f32")
                                : (sizeof(T) == 8 ? "vol_res_f64" : "vol_res_f32");
   const double nb = (double)a.count * (ND + 2) * Cfg::NSP * sizeof(T) * (MODE == 1 ? 3 : 2);
-  FR_LAUNCH_B(c, name, s, nb, kern<<<g, Cfg::THREADS, smem, s>>>(a));
+  const double nfl = MODE == 1 ? 0.0 : (double)a.count * Cfg::NSP * flops_volume(ND, P, VISC);
+  FR_LAUNCH_BF(c, name, s, nb, nfl, kern<<<g, Cfg::THREADS, smem, s>>>(a));
 }
 
 template <typename T, int ND, bool VISC, int MODE>
@@ -167,9 +169,10 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
     a.nvt = c->nvt;
     a.scratch_base = g.scratch_base;
     const int64_t nm = (int64_t)g.n * ipow(a.Pm, ND - 1);
-    FR_LAUNCH(c, MODE == 1 ? (sizeof(T) == 8 ? "face_jvp_f64" : "face_jvp_f32")
-                           : (sizeof(T) == 8 ? "face_res_f64" : "face_res_f32"),
-              s, face_kernel<T, ND, VISC, MODE><<<nblocks(nm, 128), 128, 0, s>>>(a));
+    FR_LAUNCH_BF(c, MODE == 1 ? (sizeof(T) == 8 ? "face_jvp_f64" : "face_jvp_f32")
+                              : (sizeof(T) == 8 ? "face_res_f64" : "face_res_f32"),
+                 s, 0.0, MODE == 1 ? 0.0 : (double)nm * flops_face(ND, VISC),
+                 face_kernel<T, ND, VISC, MODE><<<nblocks(nm, 128), 128, 0, s>>>(a));
     if (g.pm != g.ps) {
       const int64_t ns = (int64_t)g.n * ipow(a.Ps, ND - 1);
       FR_LAUNCH(c, "mortar_project", s,

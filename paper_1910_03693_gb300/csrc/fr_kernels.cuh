@@ -529,7 +529,7 @@ struct VolArgs {
 
 
 template <typename T, int ND, int P, bool VISC, int MODE>
-__global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_kernel(VolArgs<T> a) {
+__global__ void __launch_bounds__(VolCfg<ND, P>::THREADS, sizeof(T) == 4 ? 3 : 1) vol_kernel(VolArgs<T> a) {
   using Sh = Shape<ND, P>;
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
   constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;

@@ -107,8 +107,8 @@ fr_status fr_timing_report(fr_ctx* c, char* buf, int64_t len, int64_t* launches)
   std::string out;
   char line[256];
   for (const auto& kv : c->timing.acc) {
-    snprintf(line, sizeof(line), "%s %lld %.6f %.0f\n", kv.first.c_str(), kv.second.count, kv.second.ms,
-             kv.second.bytes);
+    snprintf(line, sizeof(line), "%s %lld %.6f %.0f %.0f\n", kv.first.c_str(), kv.second.count, kv.second.ms,
+             kv.second.bytes, kv.second.flops);
     out += line;
   }
   if ((int64_t)out.size() + 1 > len) return FR_ERR_INVALID;

@@ -14,7 +14,7 @@
 
 namespace frgb {
 
-constexpr int kRedBlocks = 304;     // 2 blocks per SM on 152 SMs
+constexpr int kRedBlocks = 1216;    // 8 blocks per SM on 152 SMs (grid-stride)
 constexpr int kRedThreads = 256;
 constexpr int kMaxK = 64;           // most vectors in one multi-dot (restart length + 1)
 
@@ -35,7 +35,7 @@ static fr_status ensure_red(fr_ctx* c) {
 
 // block reduction of KC accumulators (kk < k) into partial[block][kk]
 template <int KC>
-__device__ __forceinline__ void block_partials(const double* acc, int k, double* __restrict__ partial) {
+__device__ __forceinline__ void block_partials(const double (&acc)[KC], int k, double* __restrict__ partial) {
   __shared__ double red[kRedThreads / 32][KC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -57,57 +57,52 @@ __device__ __forceinline__ void block_partials(const double* acc, int k, double*
 }
 
 // partial[block][kk] = sum_i V[kk][i] w[i] (kk < k); with V == nullptr, ||w||^2
+// partial[block][kk] = sum_i V[kk][i] w[i] for kk < k, and, when with_norm,
+// partial[block][k] = ||w||^2.  V == nullptr gives ||w||^2 alone in slot 0.
 template <int KC>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int k,
                                                            const double* __restrict__ w, int64_t n,
-                                                           double* __restrict__ partial) {
-  double acc[KC];
+                                                           double* __restrict__ partial, int with_norm) {
+  double acc[KC + 1];
 #pragma unroll
-  for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0;
+  for (int kk = 0; kk <= KC; ++kk) acc[kk] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double wi = w[i];
-    if (V) {
+    if (V) {   // V == nullptr: norm only
 #pragma unroll
       for (int kk = 0; kk < KC; ++kk)
         if (kk < k) acc[kk] += V[kk * ldv + i] * wi;
-    } else {
-      acc[0] += wi * wi;
     }
+    acc[KC] += wi * wi;
   }
-  block_partials<KC>(acc, V ? k : 1, partial);
+  if (!V) {
+    const double one[1] = {acc[KC]};
+    block_partials<1>(one, 1, partial);
+    return;
+  }
+  // slots 0..k-1: the dots; slot k: ||w||^2 (selects only, no runtime indexing)
+  double out[KC + 1];
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) out[kk] = kk < k ? acc[kk] : acc[KC];
+  out[KC] = acc[KC];
+  block_partials<KC + 1>(out, with_norm ? k + 1 : k, partial);
 }
 
-// first pass update fused with the second pass dots:
-// w <- w - sum_kk h[kk] V[kk];  partial[block][kk] = sum_i V[kk][i] w_new[i]
-template <int KC>
-__global__ void __launch_bounds__(kRedThreads) k_update_dot(const double* __restrict__ V, int64_t ldv, int k,
-                                                             const double* __restrict__ h, double* __restrict__ w,
-                                                             int64_t n, double* __restrict__ partial) {
-  __shared__ double hs[KC];
-  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < k ? h[threadIdx.x] : 0.0;
-  __syncthreads();
-  double acc[KC];
-#pragma unroll
-  for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double x = w[i];
-#pragma unroll
-    for (int kk = 0; kk < KC; ++kk)
-      if (kk < k) x -= hs[kk] * V[kk * ldv + i];
-    w[i] = x;
-#pragma unroll
-    for (int kk = 0; kk < KC; ++kk)
-      if (kk < k) acc[kk] += V[kk * ldv + i] * x;   // second read of V[kk][i]: an L1 hit
-  }
-  block_partials<KC>(acc, k, partial);
-}
-
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int k, double* __restrict__ out) {
-  const int kk = threadIdx.x;
-  if (kk >= k) return;
+// out[kk] = sum over blocks of partial[b][kk]: one block per coefficient,
+// fixed-order tree (deterministic)
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partial, int nb, int k,
+                                                          double* __restrict__ out) {
+  __shared__ double red[256];
+  const int kk = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * kMaxK + kk];
-  out[kk] = s;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(int64_t)b * kMaxK + kk];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[kk] = red[0];
 }
 
 // second pass update: w <- w - sum_kk h[kk] V[kk]; partial[block][0] = ||w_new||^2
@@ -132,7 +127,8 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
 
 #define FR_KC_DISPATCH(k, KERNEL, ...)                                   \
   do {                                                                   \
-    if ((k) <= 8) KERNEL<8><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);        \
+    if ((k) <= 4) KERNEL<4><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);        \
+    else if ((k) <= 8) KERNEL<8><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);   \
     else if ((k) <= 16) KERNEL<16><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__); \
     else if ((k) <= 32) KERNEL<32><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__); \
     else KERNEL<64><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);                \
@@ -181,8 +177,8 @@ static fr_status multidot(fr_ctx* c, const double* V, int64_t ldv, int k, const 
   double* part = c->d_red;
   double* dout = c->d_red + kOutH1;
   const int kk = V ? k : 1;
-  FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1), FR_KC_DISPATCH(kk, k_multidot, V, ldv, kk, w, n, part));
-  FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, kk, dout));
+  FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1), FR_KC_DISPATCH(kk, k_multidot, V, ldv, kk, w, n, part, 0));
+  FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<kk, 256, 0, s>>>(part, kRedBlocks, kk, dout));
   cudaMemcpyAsync(c->h_red, dout, sizeof(double) * (V ? k : 1), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "multidot");
   std::memcpy(out_host, c->h_red, sizeof(double) * (V ? k : 1));
@@ -196,22 +192,25 @@ static fr_status norm2(fr_ctx* c, const double* w, int64_t n, double* out, cudaS
   return st;
 }
 
-// y = A x = sigma x - J(q) x
+// y = A x = sigma x - J(q) x, or y = -J(q) x when shifted is false (Arnoldi
+// runs on -J: the Krylov space of sigma I - J is that of -J, and the shift is
+// added to the Hessenberg diagonal; this avoids the cancellation of w ~ sigma v)
 static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, const double* x, double* y,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool shifted = true) {
   const int64_t n = c->n_dof;
+  const double sigma = shifted ? op->sigma : 0.0;
   if (op->mode == FR_JV_FD) {
     double* J = vec64(c, 3);
     if (!J) return FR_ERR_NOMEM;
     fr_status st = launch_fd_jv(c, op->q64_dev, x, J, op->eps, R0, s);
     if (st != FR_OK) return st;
-    FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_shift<double><<<egrid(n), 256, 0, s>>>(op->sigma, x, J, y, n));
+    FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_shift<double><<<egrid(n), 256, 0, s>>>(sigma, x, J, y, n));
   } else if (op->jv_prec == FR_F64) {
     double* J = vec64(c, 3);
     if (!J) return FR_ERR_NOMEM;
     fr_status st = launch_jvp_prepared(c, op->q64_dev, x, J, FR_F64, s);
     if (st != FR_OK) return st;
-    FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_shift<double><<<egrid(n), 256, 0, s>>>(op->sigma, x, J, y, n));
+    FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_shift<double><<<egrid(n), 256, 0, s>>>(sigma, x, J, y, n));
   } else {
     float* q32 = vec32(c, 0);
     float* x32 = vec32(c, 1);
@@ -220,7 +219,7 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
     vcast_f64_f32(c, x, x32, n, s);
     fr_status st = launch_jvp_prepared(c, q32, x32, J32, FR_F32, s);
     if (st != FR_OK) return st;
-    FR_LAUNCH_B(c, "vec", s, 20.0 * n, k_shift<float><<<egrid(n), 256, 0, s>>>(op->sigma, x, J32, y, n));
+    FR_LAUNCH_B(c, "vec", s, 20.0 * n, k_shift<float><<<egrid(n), 256, 0, s>>>(sigma, x, J32, y, n));
   }
   return cuda_check(cudaGetLastError(), "shifted operator");
 }
@@ -295,30 +294,39 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     int k = 0;
     res = beta;
     for (int j = 0; j < m; ++j) {
-      if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s)) != FR_OK) return e;
+      if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s, false)) != FR_OK) return e;
       ++it;
-      // classical Gram-Schmidt, twice; the coefficients stay on the device and
-      // come back to the host once per iteration with ||w||^2
+      // classical Gram-Schmidt with the DGKS criterion: a second pass only when
+      // the first removed more than 1 - 1/sqrt(2) of ||w|| (||w_new|| < 0.7 ||w||)
       {
         const int kk = j + 1;
         double* part = c->d_red;
-        FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1), FR_KC_DISPATCH(kk, k_multidot, V, ld, kk, w, n, part));
-        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, kk, c->d_red + kOutH1));
+        FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1), FR_KC_DISPATCH(kk, k_multidot, V, ld, kk, w, n, part, 1));
+        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<kk + 1, 256, 0, s>>>(part, kRedBlocks, kk + 1, c->d_red + kOutH1));
         FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
-                    FR_KC_DISPATCH(kk, k_update_dot, V, ld, kk, c->d_red + kOutH1, w, n, part));
-        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, kk, c->d_red + kOutH2));
-        FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
-                    FR_KC_DISPATCH(kk, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part));
-        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, kMaxK, 0, s>>>(part, kRedBlocks, 1, c->d_red + kOutN));
+                    FR_KC_DISPATCH(kk, k_orth_update, V, ld, kk, c->d_red + kOutH1, w, n, part));
+        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, 256, 0, s>>>(part, kRedBlocks, 1, c->d_red + kOutN));
         cudaMemcpyAsync(c->h_red, c->d_red + kOutH1, sizeof(double) * 3 * kMaxK, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
+        const double w_old = std::sqrt(c->h_red[kk]);
         for (int i = 0; i <= j; ++i) {
           h[i] = c->h_red[i];
-          h2[i] = c->h_red[kMaxK + i];
+          h2[i] = 0.0;
+        }
+        if (std::sqrt(c->h_red[2 * kMaxK]) < 0.7 * w_old) {
+          FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1), FR_KC_DISPATCH(kk, k_multidot, V, ld, kk, w, n, part, 0));
+          FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<kk, 256, 0, s>>>(part, kRedBlocks, kk, c->d_red + kOutH2));
+          FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
+                      FR_KC_DISPATCH(kk, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part));
+          FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, 256, 0, s>>>(part, kRedBlocks, 1, c->d_red + kOutN));
+          cudaMemcpyAsync(c->h_red + kMaxK, c->d_red + kOutH2, sizeof(double) * 2 * kMaxK, cudaMemcpyDeviceToHost, s);
+          if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
+          for (int i = 0; i <= j; ++i) h2[i] = c->h_red[kMaxK + i];
         }
       }
       const double hn = std::sqrt(c->h_red[2 * kMaxK]);
       for (int i = 0; i <= j; ++i) H[i * m + j] = h[i] + h2[i];
+      H[j * m + j] += op->sigma;          // Hessenberg of sigma I - J from that of -J
       H[(j + 1) * m + j] = hn;
       if (!std::isfinite(hn)) {
         set_error("gmres_solve: non-finite Arnoldi vector");

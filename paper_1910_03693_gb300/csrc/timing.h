@@ -16,13 +16,14 @@ namespace frgb {
 struct TimerRec {
   const char* name;
   cudaEvent_t a, b;
-  double bytes;
+  double bytes, flops;
 };
 
 struct TimerAcc {
   double ms = 0.0;
   long long count = 0;
   double bytes = 0.0;     // algorithmic bytes of all recorded launches
+  double flops = 0.0;     // algorithmic floating-point operations of all recorded launches
 };
 
 struct Timing {
@@ -50,6 +51,7 @@ struct Timing {
       x.ms += ms;
       x.count += 1;
       x.bytes += r.bytes;
+      x.flops += r.flops;
       pool.push_back(r.a);
       pool.push_back(r.b);
     }
@@ -71,10 +73,10 @@ struct LaunchScope {
   Timing& t;
   const char* name;
   cudaStream_t s;
-  double bytes;
+  double bytes, flops;
   cudaEvent_t a = nullptr;
-  LaunchScope(fr_ctx* c, const char* n, cudaStream_t st, double b = 0.0)
-      : t(timing_of(c)), name(n), s(st), bytes(b) {
+  LaunchScope(fr_ctx* c, const char* n, cudaStream_t st, double b = 0.0, double f = 0.0)
+      : t(timing_of(c)), name(n), s(st), bytes(b), flops(f) {
     ++t.launches;
     if (t.on) {
       a = t.take();
@@ -85,7 +87,7 @@ struct LaunchScope {
     if (t.on) {
       cudaEvent_t b = t.take();
       cudaEventRecord(b, s);
-      t.pending.push_back(TimerRec{name, a, b, bytes});
+      t.pending.push_back(TimerRec{name, a, b, bytes, flops});
     }
   }
 };
@@ -104,3 +106,45 @@ struct LaunchScope {
     ::frgb::LaunchScope _fr_scope((ctx), (name), (stream), (double)(bytes));     \
     __VA_ARGS__;                                                                 \
   } while (0)
+
+// Same, recording algorithmic bytes and floating-point operations.
+#define FR_LAUNCH_BF(ctx, name, stream, bytes, flops, ...)                                   \
+  do {                                                                                       \
+    ::frgb::LaunchScope _fr_scope((ctx), (name), (stream), (double)(bytes), (double)(flops)); \
+    __VA_ARGS__;                                                                             \
+  } while (0)
+
+namespace frgb {
+// Algorithmic operation counts of the FR operators as formulated (FMA = 2):
+// per solution point of the volume residual, per face point of the traces,
+// per mortar point of the common flux.
+inline double flops_volume(int nd, int P, bool visc) {
+  const int nv = nd + 2;
+  double f = 1 + nd + 2 * nd + 3 + nd * (nd + 3);                  // inviscid flux
+  f += nd * nv * 2 * nd;                                             // transformed flux
+  f += nd * nv * (2 * P + 4);                                        // divergence + correction
+  f += 2 * nv;                                                       // -div / |J|
+  if (visc) {
+    f += nd * nv * (2 * P + 4);                                      // corrected gradient
+    f += nd * nv * (2 * nd + 1);                                     // physical gradient
+    f += 2 + nd + 3 * nd * nd + 3 * nd + 2 * nd * nd + 2 * nd + (nd - 1) + 3 * nd * nd + 2 * nd * nd + 2 * nd;
+    f += nd * nv;                                                    // f_inv - f_v
+  }
+  return f;
+}
+inline double flops_trace(int nd, int P, bool visc) {
+  const int nv = nd + 2;
+  double f = nv * 2 * P;
+  if (visc) f += nv * 2 * P * nd + nd * nv * (2 * nd + 1) + 1;
+  return f;
+}
+inline double flops_face(int nd, bool visc) {
+  const int nv = nd + 2;
+  double f = 2 * (6 + 3 * nd + 3 * nd) + 1 + 6 * nv + 3 * nd + 2;   // two normal fluxes, Rusanov, area
+  if (visc) {
+    const double fv = 2 + nd + 3 * nd * nd + 3 * nd + 2 * nd * nd + 2 * nd + (nd - 1) + 3 * nd * nd + 2 * nd * nd + 2 * nd;
+    f += 2 * nv + 2 * (2 * nd + 1) + 8 * nd * nv + fv + 2 * nd * nv + nv + 4 * nv;
+  }
+  return f;
+}
+}  // namespace frgb
