@@ -248,6 +248,9 @@ def main():
     opts = dict(tol=1e-8, dtau_init=DT / 10, dtau_max=DT, mode="exact", jv_dtype=torch.float32,
                 m=30, rtol=0.1, max_it=100)
 
+    # launch tuning (elements per CTA, multi-bucket launch), untimed set-up
+    tuning = ctx.autotune(qn[:N])
+
     def step(q_in):
         ctx.indicator(q_in[:N], var=1, eta=eta, eta_max=eta_max)
         ctx.rebucket(eta, eta_max, q_in, nu_max=0.1, nu_min=0.001, p_min=3, p_max=3)
@@ -330,7 +333,10 @@ def main():
         "config": {"workload": WORKLOAD if args.n == 32 else f"tgv_ns_{args.n}^3_p3", "n_dof": N,
                    "dt": DT, "tableau": "ESDIRK3 stage 2", "gmres": "GMRES(30), rtol 0.1, <= 100 it",
                    "jvp": "exact FP32", "tol": 1e-8, "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "launch": {"epb_p3": {k: tuning["epb"][i * 7 + 4] for i, k in enumerate(
+                       ("trace_f64", "vol_res_f64", "vol_jvp_f64", "trace_f32", "vol_res_f32", "vol_jvp_f32"))},
+                       "arnoldi_graph": tuning["graphs"]}},
         "stage": {"newton": [s["newton"] for s in stats], "gmres": [s["gmres"] for s in stats],
                   "converged": all(s["converged"] for s in stats),
                   "rel_final": [s["norm_final"] / s["norm0"] for s in stats]},

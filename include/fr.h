@@ -257,6 +257,31 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
                      const fr_adapt_opts* opts, void* q_inout_dev, fr_prec prec,
                      int32_t* perm_out_dev, void* stream);
 
+/* Launch configuration (the paper has no counterpart: it is the GPU work
+ * decomposition).  The trace and volume kernels process `epb` elements per
+ * CTA (one thread per solution point); with several degree buckets they run
+ * as one persistent launch over a table of (bucket, tile) items ordered by
+ * decreasing cost n_sp (p+1) per tile, the paper's element-weight estimate
+ * (Sec. 3.2).  In GMRES with the exact JVP, each Arnoldi product -J V[j]
+ * (column gather, JVP kernels, sign) is replayed from a CUDA graph captured
+ * once per set of buffers, with j read from device memory.
+ *
+ * fr_autotune times every admissible epb for each degree present and each
+ * kernel (trace, volume residual, volume JVP) in FP64 and FP32 on the state
+ * q64_dev (FP64, state layout, n_dof), then one launch per bucket against the
+ * multi-bucket launch, and keeps the fastest; it synchronises `stream` and
+ * changes no result beyond rounding order.  fr_tuning_get/fr_tuning_set read
+ * and write the table, 2 x 3 x 7 int32 [precision f64,f32][kernel trace,
+ * volume residual, volume JVP][P = p+1], 0 = default (as many whole elements
+ * as fit 256 threads; a value whose elements exceed 256 threads also falls back
+ * to it), and the flags below.  fr_tuning_set with table NULL changes only the
+ * flags; entries outside [0, 256] or unknown flag bits give FR_ERR_INVALID. */
+#define FR_TUNE_MULTI_LAUNCH 1  /* one persistent launch over all degree buckets */
+#define FR_TUNE_GRAPHS 2        /* Arnoldi products replayed from a CUDA graph */
+fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
+fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
+fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);
+
 /* Instrumentation (the paper has no counterpart: measurement support).
  * fr_timing(ctx, 1) synchronises the device, clears the counters and starts
  * recording a pair of CUDA events on the launch stream around every kernel

@@ -96,6 +96,9 @@ SIGNATURES = {
     "spectral_decay_indicator": [C.c_void_p, C.c_void_p, C.c_int, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_void_p],
     "fr_timing": [C.c_void_p, C.c_int32],
+    "fr_autotune": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "fr_tuning_get": [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "fr_tuning_set": [C.c_void_p, C.POINTER(C.c_int32), C.c_int32],
     "fr_esdirk_tableau": [C.c_int32, C.POINTER(Tableau)],
     "fr_timing_report": [C.c_void_p, C.c_char_p, C.c_int64, C.POINTER(C.c_int64)],
     "p_rebucket": [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(AdaptOpts), C.c_void_p, C.c_int,

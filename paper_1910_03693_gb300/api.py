@@ -162,6 +162,26 @@ class FRContext:
         return out
 
 
+    # -------------------------------------------------------- launch tuning
+    def autotune(self, q64):
+        """Time the launch configurations on the FP64 state q64 and keep the fastest."""
+        q64 = _dev(q64, "q64")
+        _check(lib().fr_autotune(self.h, _ptr(q64), _stream()), "fr_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        """{"epb": 42 ints [prec][kernel][P], "multi_launch": bool, "graphs": bool}"""
+        tab = (C.c_int32 * 42)()
+        fl = C.c_int32(0)
+        _check(lib().fr_tuning_get(self.h, tab, C.byref(fl)), "fr_tuning_get")
+        return {"epb": [int(x) for x in tab], "multi_launch": bool(fl.value & 1), "graphs": bool(fl.value & 2)}
+
+    def set_tuning(self, t):
+        """Set what `tuning()` returns; a missing "epb" keeps the table, missing switches default to on."""
+        tab = (C.c_int32 * 42)(*[int(x) for x in t["epb"]]) if "epb" in t else None
+        flags = (1 if t.get("multi_launch", True) else 0) | (2 if t.get("graphs", True) else 0)
+        _check(lib().fr_tuning_set(self.h, tab, flags), "fr_tuning_set")
+
     # ---------------------------------------------------------- instrumentation
     def timing(self, enable=True):
         _check(lib().fr_timing(self.h, 1 if enable else 0), "fr_timing")

@@ -154,8 +154,38 @@ static bool element_is_affine(const fr_ctx* c, int e) {
 // ---------------------------------------------------------------------------
 // Layout: buckets in ascending (p, id) order, offsets, face lists.
 // ---------------------------------------------------------------------------
+void collect_graph_timers(fr_ctx* c) {
+  for (int k = 0; k < 2; ++k)
+    if (c->graph_timers_live[k]) {
+      c->timing.accumulate(c->graph_timers[k]);
+      c->graph_timers_live[k] = false;
+    }
+}
+
+void clear_graphs(fr_ctx* c) {
+  collect_graph_timers(c);
+  for (int k = 0; k < 2; ++k) {
+    if (c->jvp_graph[k]) cudaGraphExecDestroy(c->jvp_graph[k]);
+    c->jvp_graph[k] = nullptr;
+    for (auto& r : c->graph_timers[k]) {
+      c->timing.pool.push_back(r.a);
+      c->timing.pool.push_back(r.b);
+    }
+    c->graph_timers[k].clear();
+    c->graph_timers_live[k] = false;
+    for (auto& p : c->jvp_graph_key[k]) p = nullptr;
+  }
+}
+
+void clear_work_cache(fr_ctx* c) {
+  for (auto& kv : c->work_cache) cudaFree(kv.second.first);
+  c->work_cache.clear();
+  clear_graphs(c);
+}
+
 fr_status build_layout(fr_ctx* c) {
   const int nd = c->nd, nv = c->nv, nf = c->nf, E = c->E;
+  clear_work_cache(c);
   // free previous face groups
   for (auto& g : c->fgroups) cudaFree(g.d_recs);
   for (auto& g : c->bgroups) cudaFree(g.d_recs);
@@ -453,6 +483,10 @@ static void destroy_impl(fr_ctx* c) {
   cudaFree(c->d_nbr);
   for (auto& g : c->fgroups) cudaFree(g.d_recs);
   for (auto& g : c->bgroups) cudaFree(g.d_recs);
+  clear_work_cache(c);
+  cudaFree(c->d_jidx);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->h_jidx) cudaFreeHost(c->h_jidx);
   cudaFree(c->d_krylov);
   for (auto& v : c->d_vec64) cudaFree(v);
   for (auto& v : c->d_vec32) cudaFree(v);

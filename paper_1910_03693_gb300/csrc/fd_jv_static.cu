@@ -92,9 +92,9 @@ extern "C" fr_status fr_jvp_fd_static(fr_ctx* c, const double* q_dev, const doub
   const unsigned grid = (unsigned)((n + 255) / 256 < 4864 ? (n + 255) / 256 : 4864);
   st = launch_residual(c, q_dev, R0, FR_F64, s);
   if (st != FR_OK) return st;
-  k_fd_static_shift<<<grid, 256, 0, s>>>(q_dev, eps, v_dev, qp, n);
+  FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_fd_static_shift<<<grid, 256, 0, s>>>(q_dev, eps, v_dev, qp, n));
   st = launch_residual(c, qp, R1, FR_F64, s);
   if (st != FR_OK) return st;
-  k_fd_static_quotient<<<grid, 256, 0, s>>>(R1, R0, 1.0 / eps, Jv_dev, n);
+  FR_LAUNCH_B(c, "vec", s, 24.0 * n, k_fd_static_quotient<<<grid, 256, 0, s>>>(R1, R0, 1.0 / eps, Jv_dev, n));
   return cuda_check(cudaGetLastError(), "fr_jvp_fd_static");
 }

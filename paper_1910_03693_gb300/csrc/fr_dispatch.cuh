@@ -2,7 +2,9 @@
 // per floating-point type in fr_f64.cu and fr_f32.cu.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "fr_kernels.cuh"
 #include "fr_launch.h"
@@ -61,22 +63,74 @@ static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 
 // ---------------------------------------------------------------------------
 // dispatch helpers
 // ---------------------------------------------------------------------------
-template <typename T, int ND, int P, bool VISC>
-static void launch_trace_p(const TraceArgs<T>& a, cudaStream_t s) {
-  using Cfg = VolCfg<ND, P>;
-  constexpr int NV = ND + 2, NF = 2 * ND;
-  const size_t smem = (size_t)Cfg::EPB * (NV * Cfg::NSP + NF * NV * Shape<ND, P>::NFP) * sizeof(T);
-  auto kern = trace_kernel<T, ND, P, VISC>;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = true;
+static inline int nsp_of(int nd, int P) { return nd == 2 ? P * P : P * P * P; }
+
+// elements per CTA: tuned value, else as many whole elements as fit 256 threads
+static inline int epb_for(fr_ctx* c, int prec, int kind, int P) {
+  const int t = c->epb_tab[prec][kind][P];
+  const int nsp = nsp_of(c->nd, P);
+  const int dflt = nsp >= 256 ? 1 : 256 / nsp;
+  return (t > 0 && t * nsp <= 256) ? t : dflt;
+}
+
+static inline unsigned sm_count(fr_ctx* c) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
+  return n > 0 ? (unsigned)n : 152u;
+}
+
+// Work table of the multi-bucket launch: tiles of epb elements, ordered by
+// decreasing cost n_sp (p+1) per tile (higher degrees first), bucket order.
+static const WorkItem* work_items(fr_ctx* c, int prec, int kind, int* n_items) {
+  const int key = prec * 16 + kind;
+  for (auto& kv : c->work_cache)
+    if (kv.first == key) {
+      *n_items = kv.second.second;
+      return (const WorkItem*)kv.second.first;
+    }
+  std::vector<std::pair<double, WorkItem>> items;
+  for (size_t bi = 0; bi < c->buckets.size(); ++bi) {
+    const Bucket& b = c->buckets[bi];
+    const int P = b.p + 1, e = epb_for(c, prec, kind, P);
+    for (int f = 0; f < b.count; f += e) {
+      const int ne = std::min(e, b.count - f);
+      items.push_back({(double)ne * nsp_of(c->nd, P) * P, WorkItem{(int32_t)bi, (int32_t)f}});
+    }
   }
-  kern<<<nblocks(a.count, Cfg::EPB), Cfg::THREADS, smem, s>>>(a);
+  std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  std::vector<WorkItem> h(items.size());
+  for (size_t i = 0; i < items.size(); ++i) h[i] = items[i].second;
+  void* d = nullptr;
+  if (cudaMalloc(&d, sizeof(WorkItem) * std::max<size_t>(h.size(), 1)) != cudaSuccess) {
+    cudaGetLastError();  // out of memory: the caller launches per bucket instead
+    return nullptr;
+  }
+  cudaMemcpy(d, h.data(), sizeof(WorkItem) * h.size(), cudaMemcpyHostToDevice);
+  c->work_cache.push_back({key, {d, (int)h.size()}});
+  *n_items = (int)h.size();
+  return (const WorkItem*)d;
+}
+
+template <typename KernelT>
+static void ensure_smem(KernelT kern, size_t smem, size_t& configured) {
+  if (smem > configured) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+}
+
+template <typename T, int ND, int P, bool VISC>
+static void launch_trace_p(const TraceArgs<T>& a, int epb, cudaStream_t s) {
+  constexpr int NV = ND + 2, NF = 2 * ND;
+  const size_t smem = (size_t)epb * (NV * Shape<ND, P>::NSP + NF * NV * Shape<ND, P>::NFP) * sizeof(T);
+  auto kern = trace_kernel<T, ND, P, VISC>;
+  static size_t configured = 0;
+  ensure_smem(kern, smem, configured);
+  kern<<<nblocks(a.count, epb), epb * Shape<ND, P>::NSP, smem, s>>>(a, epb);
 }
 
 template <typename T, int ND, bool VISC>
-static void launch_trace(fr_ctx* c, const Bucket& b, const T* q, T* trace, cudaStream_t s) {
+static TraceArgs<T> trace_args(fr_ctx* c, const Bucket& b, const T* q, T* trace) {
   TraceArgs<T> a;
   a.q = q;
   a.trace = trace;
@@ -88,41 +142,73 @@ static void launch_trace(fr_ctx* c, const Bucket& b, const T* q, T* trace, cudaS
   a.count = b.count;
   a.slot_begin = b.slot_begin;
   a.nvt = c->nvt;
-  const int P = b.p + 1;
-  const double nb = (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
-  const double nfl = (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC);
-  FR_LAUNCH_BF(c, sizeof(T) == 8 ? "trace_f64" : "trace_f32", s, nb, nfl, {
-    switch (P) {
-      case 2: launch_trace_p<T, ND, 2, VISC>(a, s); break;
-      case 3: launch_trace_p<T, ND, 3, VISC>(a, s); break;
-      case 4: launch_trace_p<T, ND, 4, VISC>(a, s); break;
-      case 5: launch_trace_p<T, ND, 5, VISC>(a, s); break;
-      case 6: launch_trace_p<T, ND, 6, VISC>(a, s); break;
+  return a;
+}
+
+// traces of every bucket: one launch per bucket, or one multi-bucket launch
+template <typename T, int ND, bool VISC>
+static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  double nb = 0.0, nfl = 0.0;
+  for (const auto& b : c->buckets) {
+    const int P = b.p + 1;
+    nb += (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
+    nfl += (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC);
+  }
+  const char* name = sizeof(T) == 8 ? "trace_f64" : "trace_f32";
+  int n_items = 0;
+  const WorkItem* items = (c->multi_launch && c->buckets.size() > 1) ? work_items(c, prec, 0, &n_items) : nullptr;
+  if (items) {
+    TraceMulti<T> m;
+    size_t smem = 0;
+    for (size_t i = 0; i < c->buckets.size(); ++i) {
+      const Bucket& b = c->buckets[i];
+      const int P = b.p + 1, e = epb_for(c, prec, 0, P);
+      m.b[i] = trace_args<T, ND, VISC>(c, b, q, trace);
+      m.P[i] = P;
+      m.epb[i] = e;
+      smem = std::max(smem, (size_t)e * ((ND + 2) * nsp_of(ND, P) + 2 * ND * (ND + 2) * ipow(P, ND - 1)) * sizeof(T));
     }
-  });
+    m.items = items;
+    m.n_items = n_items;
+    auto kern = trace_multi_kernel<T, ND, VISC>;
+    static size_t configured = 0;
+    ensure_smem(kern, smem, configured);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    const unsigned grid = (unsigned)std::max(1, std::min(m.n_items, (int)(std::max(per_sm, 1) * sm_count(c))));
+    FR_LAUNCH_BF(c, name, s, nb, nfl, kern<<<grid, 256, smem, s>>>(m));
+    return;
+  }
+  for (const auto& b : c->buckets) {
+    const TraceArgs<T> a = trace_args<T, ND, VISC>(c, b, q, trace);
+    const int P = b.p + 1, e = epb_for(c, prec, 0, P);
+    const double nbb = (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
+    const double nfb = (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC);
+    FR_LAUNCH_BF(c, name, s, nbb, nfb, {
+      switch (P) {
+        case 2: launch_trace_p<T, ND, 2, VISC>(a, e, s); break;
+        case 3: launch_trace_p<T, ND, 3, VISC>(a, e, s); break;
+        case 4: launch_trace_p<T, ND, 4, VISC>(a, e, s); break;
+        case 5: launch_trace_p<T, ND, 5, VISC>(a, e, s); break;
+        case 6: launch_trace_p<T, ND, 6, VISC>(a, e, s); break;
+      }
+    });
+  }
 }
 
 template <typename T, int ND, int P, bool VISC, int MODE>
-static void launch_vol_p(fr_ctx* c, const VolArgs<T>& a, cudaStream_t s) {
-  using Cfg = VolCfg<ND, P>;
+static void launch_vol_p(const VolArgs<T>& a, int epb, cudaStream_t s) {
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
-  const size_t smem = (size_t)Cfg::EPB * (ND + 2) * (1 + ND) * Cfg::NSP * sizeof(S);
+  const size_t smem = (size_t)epb * (ND + 2) * (1 + ND) * Shape<ND, P>::NSP * sizeof(S);
   auto kern = vol_kernel<T, ND, P, VISC, MODE>;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = true;
-  }
-  const unsigned g = nblocks(a.count, Cfg::EPB);
-  const char* name = MODE == 1 ? (sizeof(T) == 8 ? "vol_jvp_f64" : "vol_jvp_f32")
-                               : (sizeof(T) == 8 ? "vol_res_f64" : "vol_res_f32");
-  const double nb = (double)a.count * (ND + 2) * Cfg::NSP * sizeof(T) * (MODE == 1 ? 3 : 2);
-  const double nfl = MODE == 1 ? 0.0 : (double)a.count * Cfg::NSP * flops_volume(ND, P, VISC);
-  FR_LAUNCH_BF(c, name, s, nb, nfl, kern<<<g, Cfg::THREADS, smem, s>>>(a));
+  static size_t configured = 0;
+  ensure_smem(kern, smem, configured);
+  kern<<<nblocks(a.count, epb), epb * Shape<ND, P>::NSP, smem, s>>>(a, epb);
 }
 
-template <typename T, int ND, bool VISC, int MODE>
-static void launch_vol(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* out, cudaStream_t s) {
+template <typename T>
+static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* out) {
   VolArgs<T> a;
   a.q = q;
   a.v = v;
@@ -138,12 +224,60 @@ static void launch_vol(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* ou
   a.out_base = b.out_base;
   a.count = b.count;
   a.slot_begin = b.slot_begin;
-  switch (b.p + 1) {
-    case 2: launch_vol_p<T, ND, 2, VISC, MODE>(c, a, s); break;
-    case 3: launch_vol_p<T, ND, 3, VISC, MODE>(c, a, s); break;
-    case 4: launch_vol_p<T, ND, 4, VISC, MODE>(c, a, s); break;
-    case 5: launch_vol_p<T, ND, 5, VISC, MODE>(c, a, s); break;
-    case 6: launch_vol_p<T, ND, 6, VISC, MODE>(c, a, s); break;
+  return a;
+}
+
+// volume kernel of every bucket: one launch per bucket, or one multi-bucket launch
+template <typename T, int ND, bool VISC, int MODE>
+static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t s) {
+  using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
+  const int prec = sizeof(T) == 8 ? 0 : 1, kind = MODE == 1 ? 2 : 1;
+  const char* name = MODE == 1 ? (sizeof(T) == 8 ? "vol_jvp_f64" : "vol_jvp_f32")
+                               : (sizeof(T) == 8 ? "vol_res_f64" : "vol_res_f32");
+  double nb = 0.0, nfl = 0.0;
+  for (const auto& b : c->buckets) {
+    const int P = b.p + 1;
+    nb += (double)b.count * (ND + 2) * nsp_of(ND, P) * sizeof(T) * (MODE == 1 ? 3 : 2);
+    nfl += MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC);
+  }
+  int n_items = 0;
+  const WorkItem* items = (c->multi_launch && c->buckets.size() > 1) ? work_items(c, prec, kind, &n_items) : nullptr;
+  if (items) {
+    VolMulti<T> m;
+    size_t smem = 0;
+    for (size_t i = 0; i < c->buckets.size(); ++i) {
+      const Bucket& b = c->buckets[i];
+      const int P = b.p + 1, e = epb_for(c, prec, kind, P);
+      m.b[i] = vol_args<T>(c, b, q, v, out);
+      m.P[i] = P;
+      m.epb[i] = e;
+      smem = std::max(smem, (size_t)e * (ND + 2) * (1 + ND) * nsp_of(ND, P) * sizeof(S));
+    }
+    m.items = items;
+    m.n_items = n_items;
+    auto kern = vol_multi_kernel<T, ND, VISC, MODE>;
+    static size_t configured = 0;
+    ensure_smem(kern, smem, configured);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    const unsigned grid = (unsigned)std::max(1, std::min(m.n_items, (int)(std::max(per_sm, 1) * sm_count(c))));
+    FR_LAUNCH_BF(c, name, s, nb, nfl, kern<<<grid, 256, smem, s>>>(m));
+    return;
+  }
+  for (const auto& b : c->buckets) {
+    const VolArgs<T> a = vol_args<T>(c, b, q, v, out);
+    const int P = b.p + 1, e = epb_for(c, prec, kind, P);
+    const double nbb = (double)b.count * (ND + 2) * nsp_of(ND, P) * sizeof(T) * (MODE == 1 ? 3 : 2);
+    const double nfb = MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC);
+    FR_LAUNCH_BF(c, name, s, nbb, nfb, {
+      switch (P) {
+        case 2: launch_vol_p<T, ND, 2, VISC, MODE>(a, e, s); break;
+        case 3: launch_vol_p<T, ND, 3, VISC, MODE>(a, e, s); break;
+        case 4: launch_vol_p<T, ND, 4, VISC, MODE>(a, e, s); break;
+        case 5: launch_vol_p<T, ND, 5, VISC, MODE>(a, e, s); break;
+        case 6: launch_vol_p<T, ND, 6, VISC, MODE>(a, e, s); break;
+      }
+    });
   }
 }
 
@@ -202,9 +336,9 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
 template <typename T, int ND, bool VISC>
 static void residual_impl(fr_ctx* c, const T* q, T* R, cudaStream_t s) {
   T* trq = (T*)c->d_trace_q;
-  for (const auto& b : c->buckets) launch_trace<T, ND, VISC>(c, b, q, trq, s);
+  launch_traces<T, ND, VISC>(c, q, trq, s);
   launch_faces<T, ND, VISC, 0>(c, trq, nullptr, s);
-  for (const auto& b : c->buckets) launch_vol<T, ND, VISC, 0>(c, b, q, nullptr, R, s);
+  launch_vols<T, ND, VISC, 0>(c, q, nullptr, R, s);
 }
 
 // JVP; with q_traces_ready the traces of q in d_trace_q are reused (q is
@@ -213,12 +347,10 @@ template <typename T, int ND, bool VISC>
 static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready = false) {
   T* trq = (T*)c->d_trace_q;
   T* trv = (T*)c->d_trace_v;
-  for (const auto& b : c->buckets) {
-    if (!q_traces_ready) launch_trace<T, ND, VISC>(c, b, q, trq, s);
-    launch_trace<T, ND, VISC>(c, b, v, trv, s);
-  }
+  if (!q_traces_ready) launch_traces<T, ND, VISC>(c, q, trq, s);
+  launch_traces<T, ND, VISC>(c, v, trv, s);
   launch_faces<T, ND, VISC, 1>(c, trq, trv, s);
-  for (const auto& b : c->buckets) launch_vol<T, ND, VISC, 1>(c, b, q, v, Jv, s);
+  launch_vols<T, ND, VISC, 1>(c, q, v, Jv, s);
 }
 
 
@@ -245,7 +377,7 @@ static void vjp_impl(fr_ctx* c, const T* q, const T* w, T* out, cudaStream_t s) 
   T* trq = (T*)c->d_trace_q;
   T* fbar = (T*)c->d_fbar;
   T* trbar = (T*)c->d_trbar;
-  for (const auto& b : c->buckets) launch_trace<T, ND, VISC>(c, b, q, trq, s);
+  launch_traces<T, ND, VISC>(c, q, trq, s);
   launch_faces<T, ND, VISC, 0>(c, trq, nullptr, s);
   for (const auto& b : c->buckets) {
     VolAdjArgs<T> a;
@@ -340,6 +472,108 @@ static void vjp_impl(fr_ctx* c, const T* q, const T* w, T* out, cudaStream_t s) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: elements per CTA of the trace and volume kernels for every
+// degree present, then one launch per bucket vs the multi-bucket launch.
+// Candidates are timed with CUDA events (best of `reps`) on the caller's state.
+// ---------------------------------------------------------------------------
+template <typename F>
+static float time_best(int reps, cudaStream_t s, F&& f) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  f();   // warm-up
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, s);
+    f();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+template <typename T, int ND, bool VISC>
+static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStream_t s) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  T* trq = (T*)c->d_trace_q;
+  T* trv = (T*)c->d_trace_v;
+  const bool multi_saved = c->multi_launch;
+  c->multi_launch = false;
+  for (int kind = 0; kind < 3; ++kind) {
+    // valid face data for the volume kernels
+    if (kind == 1) residual_impl<T, ND, VISC>(c, q, scratch, s);
+    if (kind == 2) jvp_impl<T, ND, VISC>(c, q, q, scratch, s);
+    for (const auto& b : c->buckets) {
+      const int P = b.p + 1, nsp = nsp_of(ND, P);
+      std::vector<int> cand;
+      for (int e = 1; e * nsp <= 256; e *= 2) cand.push_back(e);
+      const int dflt = nsp >= 256 ? 1 : 256 / nsp;
+      if (std::find(cand.begin(), cand.end(), dflt) == cand.end()) cand.push_back(dflt);
+      float best = 1e30f;
+      int best_e = dflt;
+      for (int e : cand) {
+        float ms = 1e30f;
+        if (kind == 0) {
+          const TraceArgs<T> a = trace_args<T, ND, VISC>(c, b, q, trq);
+          ms = time_best(reps, s, [&] {
+            switch (P) {
+              case 2: launch_trace_p<T, ND, 2, VISC>(a, e, s); break;
+              case 3: launch_trace_p<T, ND, 3, VISC>(a, e, s); break;
+              case 4: launch_trace_p<T, ND, 4, VISC>(a, e, s); break;
+              case 5: launch_trace_p<T, ND, 5, VISC>(a, e, s); break;
+              case 6: launch_trace_p<T, ND, 6, VISC>(a, e, s); break;
+            }
+          });
+        } else {
+          const VolArgs<T> a = vol_args<T>(c, b, q, kind == 2 ? q : nullptr, scratch);
+          ms = time_best(reps, s, [&] {
+            if (kind == 1) {
+              switch (P) {
+                case 2: launch_vol_p<T, ND, 2, VISC, 0>(a, e, s); break;
+                case 3: launch_vol_p<T, ND, 3, VISC, 0>(a, e, s); break;
+                case 4: launch_vol_p<T, ND, 4, VISC, 0>(a, e, s); break;
+                case 5: launch_vol_p<T, ND, 5, VISC, 0>(a, e, s); break;
+                case 6: launch_vol_p<T, ND, 6, VISC, 0>(a, e, s); break;
+              }
+            } else {
+              switch (P) {
+                case 2: launch_vol_p<T, ND, 2, VISC, 1>(a, e, s); break;
+                case 3: launch_vol_p<T, ND, 3, VISC, 1>(a, e, s); break;
+                case 4: launch_vol_p<T, ND, 4, VISC, 1>(a, e, s); break;
+                case 5: launch_vol_p<T, ND, 5, VISC, 1>(a, e, s); break;
+                case 6: launch_vol_p<T, ND, 6, VISC, 1>(a, e, s); break;
+              }
+            }
+          });
+        }
+        if (ms < best) {
+          best = ms;
+          best_e = e;
+        }
+      }
+      c->epb_tab[prec][kind][P] = best_e;
+    }
+  }
+  (void)trv;
+  clear_work_cache(c);
+  // one launch per bucket vs one multi-bucket launch, for the whole JVP
+  if (c->buckets.size() > 1) {
+    c->multi_launch = false;
+    const float t_sep = time_best(reps, s, [&] { jvp_impl<T, ND, VISC>(c, q, q, scratch, s); });
+    c->multi_launch = true;
+    const float t_multi = time_best(reps, s, [&] { jvp_impl<T, ND, VISC>(c, q, q, scratch, s); });
+    c->multi_launch = t_multi <= t_sep;
+  } else {
+    c->multi_launch = multi_saved;
+  }
+}
+
 template <typename T>
 static fr_status run_op(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s) {
   const T* qq = (const T*)q;
@@ -359,7 +593,8 @@ static fr_status run_op(fr_ctx* c, int op, const void* q, const void* v, void* o
   if (op == 0) residual_impl<T, ND, VISC>(c, qq, oo, s);                       \
   else if (op == 1) jvp_impl<T, ND, VISC>(c, qq, vv, oo, s);                   \
   else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);                   \
-  else if (op == 3) { for (const auto& b : c->buckets) launch_trace<T, ND, VISC>(c, b, qq, (T*)c->d_trace_q, s); } \
+  else if (op == 3) { launch_traces<T, ND, VISC>(c, qq, (T*)c->d_trace_q, s); } \
+  else if (op == 5) autotune_impl<T, ND, VISC>(c, qq, oo, 3, s);              \
   else jvp_impl<T, ND, VISC>(c, qq, vv, oo, s, true);
   if (c->nd == 2) {
     if (c->visc) { FR_OPS(2, true) } else { FR_OPS(2, false) }

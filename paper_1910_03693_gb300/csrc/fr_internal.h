@@ -145,6 +145,24 @@ struct fr_ctx {
   int64_t red_cap = 0;
   double* h_red = nullptr;               // pinned host mirror
   frgb::Timing timing;                   // launch counter and optional per-kernel events
+  // launch configuration: elements per CTA by [precision][kind][P] (kind 0
+  // trace, 1 volume residual, 2 volume JVP), 0 = default; cost-ordered work
+  // tables of the multi-bucket launch by (precision, kind)
+  int epb_tab[2][3][frgb::kPM + 1] = {};
+  bool multi_launch = true;
+  std::vector<std::pair<int, std::pair<void*, int>>> work_cache;
+  // CUDA graph of one Arnoldi matrix-vector product -J(q) V[j] (per precision),
+  // with the column index read from d_jidx; keyed by the pointers it captured
+  cudaGraphExec_t jvp_graph[2] = {nullptr, nullptr};
+  const void* jvp_graph_key[2][4] = {};
+  int jvp_graph_nodes[2] = {0, 0};
+  std::vector<frgb::TimerRec> graph_timers[2];  // event pairs inside each graph
+  bool graph_timers_live[2] = {false, false};   // a replay's timers are not yet accumulated
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
+  bool jvp_graph_ok = true;
+  int* d_jidx = nullptr;
+  int* h_jidx = nullptr;                        // pinned, h_jidx[j] = j
   // adaptation workspaces (lazily allocated)
   double* d_xfer = nullptr;              // prolongation / projection matrices [Po][Pn][6][6]
   int* d_adapt_i32 = nullptr;
@@ -158,6 +176,9 @@ struct fr_ctx {
 };
 
 namespace frgb {
+void clear_work_cache(fr_ctx* c);
+void clear_graphs(fr_ctx* c);
+void collect_graph_timers(fr_ctx* c);
 // launchers (kernels_*.cu)
 fr_status launch_residual(fr_ctx* c, const void* q, void* R, fr_prec prec, cudaStream_t s);
 fr_status launch_jvp_exact(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec,

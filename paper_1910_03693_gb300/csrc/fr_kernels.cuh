@@ -119,17 +119,17 @@ struct VolCfg {
 // derivative uses l'(+-1) (P terms), and the two tangential derivatives
 // differentiate the face trace (P terms each); the physical gradient follows
 // from the face metric terms.
+// Elements i0 .. i0+epb-1 of the bucket described by ``a``; every thread of the
+// block reaches the barriers (threads beyond epb*NSP only help to synchronise).
 template <typename T, int ND, int P, bool VISC>
-__global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) trace_kernel(TraceArgs<T> a) {
+__device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, int epb, unsigned char* smem_raw) {
   using Sh = Shape<ND, P>;
   constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
-  constexpr int EPB = VolCfg<ND, P>::EPB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int le = threadIdx.x / NSP;
   const int lt = threadIdx.x % NSP;
-  const int64_t i = (int64_t)blockIdx.x * EPB + le;
-  const bool valid = i < a.count;
+  const int64_t i = i0 + le;
+  const bool valid = le < epb && i < a.count;
   T* sq = sm + le * (NV * NSP + NF * NV * NFP);   // [NV][NSP]
   T* sqf = sq + NV * NSP;                           // [NF][NV][NFP]
   const BasisTab<T>& B = a.basis[P];
@@ -193,6 +193,48 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) trace_kernel(TraceArgs
         out[(f * a.nvt + NV + j * NV + v) * NFP + t] = g * Jinv;
       }
     }
+  }
+}
+
+template <typename T, int ND, int P, bool VISC>
+__global__ void __launch_bounds__(256) trace_kernel(TraceArgs<T> a, int epb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  trace_body<T, ND, P, VISC>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
+}
+
+// One tile of elements of one bucket: the unit of the multi-bucket launch.
+struct WorkItem {
+  int32_t bucket;   // index into the launch's bucket table
+  int32_t first;    // first element (bucket-local)
+};
+
+constexpr int kMaxBuckets = kMaxDeg + 1;
+
+template <typename T>
+struct TraceMulti {
+  TraceArgs<T> b[kMaxBuckets];
+  int P[kMaxBuckets];
+  int epb[kMaxBuckets];
+  const WorkItem* items;
+  int n_items;
+};
+
+// Every bucket in one persistent launch: CTAs walk the cost-ordered work
+// table with a grid stride and dispatch on the tile's degree.
+template <typename T, int ND, bool VISC>
+__global__ void __launch_bounds__(256) trace_multi_kernel(TraceMulti<T> m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
+    const WorkItem it = m.items[w];
+    const int b = it.bucket;
+    switch (m.P[b]) {
+      case 2: trace_body<T, ND, 2, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 3: trace_body<T, ND, 3, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 4: trace_body<T, ND, 4, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 5: trace_body<T, ND, 5, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 6: trace_body<T, ND, 6, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
+    }
+    __syncthreads();
   }
 }
 
@@ -529,18 +571,16 @@ struct VolArgs {
 
 
 template <typename T, int ND, int P, bool VISC, int MODE>
-__global__ void __launch_bounds__(VolCfg<ND, P>::THREADS, sizeof(T) == 4 ? 3 : 1) vol_kernel(VolArgs<T> a) {
+__device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int epb, unsigned char* smem_raw) {
   using Sh = Shape<ND, P>;
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
   constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
-  constexpr int EPB = VolCfg<ND, P>::EPB;
   constexpr int FOUT_STRIDE = 3 * NV * NFP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   S* sm = reinterpret_cast<S*>(smem_raw);
   const int le = threadIdx.x / NSP;
   const int sp = threadIdx.x % NSP;
-  const int64_t i = (int64_t)blockIdx.x * EPB + le;
-  const bool valid = i < a.count;
+  const int64_t i = i0 + le;
+  const bool valid = le < epb && i < a.count;
   S* sq = sm + le * (NV + ND * NV) * NSP;       // [NV][NSP]
   S* sF = sq + NV * NSP;                         // [ND][NV][NSP]
   const BasisTab<T>& B = a.basis[P];
@@ -656,6 +696,38 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS, sizeof(T) == 4 ? 3 : 1
   for (int v = 0; v < NV; ++v) {
     S r = (T(0) - div[v]) * Jinv;
     a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
+  }
+}
+
+template <typename T, int ND, int P, bool VISC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) vol_kernel(VolArgs<T> a, int epb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  vol_body<T, ND, P, VISC, MODE>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
+}
+
+template <typename T>
+struct VolMulti {
+  VolArgs<T> b[kMaxBuckets];
+  int P[kMaxBuckets];
+  int epb[kMaxBuckets];
+  const WorkItem* items;
+  int n_items;
+};
+
+template <typename T, int ND, bool VISC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) vol_multi_kernel(VolMulti<T> m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
+    const WorkItem it = m.items[w];
+    const int b = it.bucket;
+    switch (m.P[b]) {
+      case 2: vol_body<T, ND, 2, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 3: vol_body<T, ND, 3, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 4: vol_body<T, ND, 4, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 5: vol_body<T, ND, 5, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 6: vol_body<T, ND, 6, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
+    }
+    __syncthreads();
   }
 }
 

@@ -94,6 +94,7 @@ fr_status fr_timing(fr_ctx* c, int32_t enable) {
   if (!c) return FR_ERR_INVALID;
   cudaDeviceSynchronize();
   c->timing.collect();
+  collect_graph_timers(c);
   c->timing.acc.clear();
   c->timing.launches = 0;
   c->timing.on = enable != 0;
@@ -104,6 +105,7 @@ fr_status fr_timing_report(fr_ctx* c, char* buf, int64_t len, int64_t* launches)
   if (!c || !buf || len <= 0) return FR_ERR_INVALID;
   cudaDeviceSynchronize();
   c->timing.collect();
+  collect_graph_timers(c);
   std::string out;
   char line[256];
   for (const auto& kv : c->timing.acc) {
@@ -114,6 +116,55 @@ fr_status fr_timing_report(fr_ctx* c, char* buf, int64_t len, int64_t* launches)
   if ((int64_t)out.size() + 1 > len) return FR_ERR_INVALID;
   std::memcpy(buf, out.c_str(), out.size() + 1);
   if (launches) *launches = c->timing.launches;
+  return FR_OK;
+}
+
+fr_status fr_autotune(fr_ctx* c, const double* q64_dev, void* stream) {
+  if (!c || !q64_dev) {
+    set_error("fr_autotune: null argument");
+    return FR_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* scr64 = vec64(c, 11);
+  float* q32 = vec32(c, 0);
+  float* scr32 = vec32(c, 1);
+  if (!scr64 || !q32 || !scr32) return FR_ERR_NOMEM;
+  const bool timing = c->timing.on;
+  c->timing.on = false;
+  fr_status st = run_op_f64(c, 5, q64_dev, nullptr, scr64, s);
+  if (st == FR_OK) {
+    vcast_f64_f32(c, q64_dev, q32, c->n_dof, s);
+    st = run_op_f32(c, 5, q32, nullptr, scr32, s);
+  }
+  c->timing.on = timing;
+  if (st != FR_OK) return st;
+  return cuda_check(cudaStreamSynchronize(s), "fr_autotune");
+}
+
+fr_status fr_tuning_get(const fr_ctx* c, int32_t* table, int32_t* flags) {
+  if (!c || !table) return FR_ERR_INVALID;
+  std::memcpy(table, c->epb_tab, sizeof(c->epb_tab));
+  if (flags) *flags = (c->multi_launch ? FR_TUNE_MULTI_LAUNCH : 0) | (c->use_graphs ? FR_TUNE_GRAPHS : 0);
+  return FR_OK;
+}
+
+fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
+  if (!c) return FR_ERR_INVALID;
+  if (flags & ~(FR_TUNE_MULTI_LAUNCH | FR_TUNE_GRAPHS)) {
+    set_error("fr_tuning_set: unknown flag bits");
+    return FR_ERR_INVALID;
+  }
+  if (table) {
+    for (int i = 0; i < 2 * 3 * (kPM + 1); ++i)
+      if (table[i] < 0 || table[i] > 256) {
+        set_error("fr_tuning_set: elements per CTA must lie in [0, 256]");
+        return FR_ERR_INVALID;
+      }
+    std::memcpy(c->epb_tab, table, sizeof(c->epb_tab));
+  }
+  c->multi_launch = (flags & FR_TUNE_MULTI_LAUNCH) != 0;
+  c->use_graphs = (flags & FR_TUNE_GRAPHS) != 0;
+  clear_work_cache(c);
   return FR_OK;
 }
 

@@ -17,7 +17,8 @@ void vcast_f64_f32(fr_ctx* c, const double* x, float* y, int64_t n, cudaStream_t
 void vcast_f32_f64(fr_ctx* c, const float* x, double* y, int64_t n, cudaStream_t s);
 
 // op 0: out = R(q); op 1: out = J(q) v (exact); op 2: out = J(q)^T v;
-// op 3: traces of q only (prepares op 4); op 4: J(q) v reusing those traces.
+// op 3: traces of q only (prepares op 4); op 4: J(q) v reusing those traces;
+// op 5: autotune the launch configuration on q (out: scratch of n_dof).
 fr_status run_op_f64(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 fr_status run_op_f32(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 

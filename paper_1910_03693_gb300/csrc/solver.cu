@@ -192,6 +192,132 @@ static fr_status norm2(fr_ctx* c, const double* w, int64_t n, double* out, cudaS
   return st;
 }
 
+// x = (T) V[*jidx]
+template <typename T>
+__global__ void k_gather_col(const double* __restrict__ V, int64_t ld, const int* __restrict__ jidx,
+                             T* __restrict__ x, int64_t n) {
+  const double* src = V + (int64_t)(*jidx) * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (T)src[i];
+}
+
+// w = -J
+template <typename T>
+__global__ void k_negate(const T* __restrict__ J, double* __restrict__ w, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = -(double)J[i];
+}
+
+// One Arnoldi matrix-vector product w = -J(q) V[j] of the exact mode as a CUDA
+// graph: gather V[j] into a fixed buffer (j read from device memory), the JVP
+// kernels (q traces prepared beforehand), negate into w.  Captured on first
+// use and again whenever q, V, w or the timing state changed; the layout and
+// the launch tuning drop it.  Returns false when graphs are off or cannot be
+// used, and the caller then launches the same kernels directly.
+static void gather_col(fr_ctx* c, int pi, const double* V, int64_t ld, void* x, int64_t n, cudaStream_t s) {
+  const double nb = (double)n * (8 + (pi ? 4 : 8));
+  if (pi) FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<float><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, (float*)x, n));
+  else FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<double><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, (double*)x, n));
+}
+
+static void negate_into(fr_ctx* c, int pi, const void* J, double* w, int64_t n, cudaStream_t s) {
+  const double nb = (double)n * (8 + (pi ? 4 : 8));
+  if (pi) FR_LAUNCH_B(c, "vec", s, nb, k_negate<float><<<egrid(n), 256, 0, s>>>((const float*)J, w, n));
+  else FR_LAUNCH_B(c, "vec", s, nb, k_negate<double><<<egrid(n), 256, 0, s>>>((const double*)J, w, n));
+}
+
+static bool jvp_graph_apply(fr_ctx* c, const fr_shifted_op* op, const double* V, int j, double* w,
+                            cudaStream_t s) {
+  if (!c->use_graphs || !c->jvp_graph_ok || op->mode != FR_JV_EXACT || j < 0 || j >= kMaxK) return false;
+  const int pi = op->jv_prec == FR_F32 ? 1 : 0;
+  const fr_prec prec = pi ? FR_F32 : FR_F64;
+  const int64_t n = c->n_dof, ld = c->n_dof_cap;
+  if (!c->d_jidx) {
+    if (cudaMalloc(&c->d_jidx, sizeof(int)) != cudaSuccess) return false;
+    if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return false;
+    for (int k = 0; k < kMaxK; ++k) c->h_jidx[k] = k;
+  }
+  // the q the traces were prepared from: the FP32 copy for FP32 products
+  const void* qptr = pi ? (const void*)vec32(c, 0) : (const void*)op->q64_dev;
+  void* x = pi ? (void*)vec32(c, 1) : (void*)vec64(c, 10);
+  void* J = pi ? (void*)vec32(c, 2) : (void*)vec64(c, 3);
+  if (!qptr || !x || !J) return false;
+  const void* timed = c->timing.on ? (const void*)c : nullptr;
+  const void* key[4] = {qptr, V, w, timed};
+  const bool stale = !c->jvp_graph[pi] || !std::equal(key, key + 4, c->jvp_graph_key[pi]);
+  collect_graph_timers(c);
+  cudaMemcpyAsync(c->d_jidx, c->h_jidx + j, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (stale) {
+    if (c->jvp_graph[pi]) {
+      cudaStreamSynchronize(s);
+      cudaGraphExecDestroy(c->jvp_graph[pi]);
+      c->jvp_graph[pi] = nullptr;
+      for (auto& r : c->graph_timers[pi]) {
+        c->timing.pool.push_back(r.a);
+        c->timing.pool.push_back(r.b);
+      }
+      c->graph_timers[pi].clear();
+    }
+    // this product launched directly: every lazy allocation and kernel
+    // attribute is then in place before the capture
+    gather_col(c, pi, V, ld, x, n, s);
+    if (launch_jvp_prepared(c, qptr, x, J, prec, s) != FR_OK) return false;
+    negate_into(c, pi, J, w, n, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    // captured on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); replayed on the caller's stream
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->cap_stream = nullptr;
+      c->jvp_graph_ok = false;
+      return true;
+    }
+    cudaStream_t cs = c->cap_stream;
+    const long long l0 = c->timing.launches;
+    c->timing.capture = true;
+    c->timing.mark = (int64_t)c->timing.pending.size();
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    fr_status st = FR_OK;
+    if (ok) {
+      gather_col(c, pi, V, ld, x, n, cs);
+      st = launch_jvp_prepared(c, qptr, x, J, prec, cs);
+      negate_into(c, pi, J, w, n, cs);
+      const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+      ok = st == FR_OK && ee == cudaSuccess && g != nullptr &&
+           cudaGraphInstantiate(&c->jvp_graph[pi], g, 0) == cudaSuccess;
+    }
+    if (g) cudaGraphDestroy(g);
+    c->timing.capture = false;
+    // the timers recorded during the capture belong to the graph
+    auto& pend = c->timing.pending;
+    c->graph_timers[pi].assign(pend.begin() + c->timing.mark, pend.end());
+    pend.resize(c->timing.mark);
+    c->jvp_graph_nodes[pi] = (int)(c->timing.launches - l0);
+    c->timing.launches = l0;
+    if (!ok) {
+      cudaGetLastError();
+      for (auto& r : c->graph_timers[pi]) {
+        c->timing.pool.push_back(r.a);
+        c->timing.pool.push_back(r.b);
+      }
+      c->graph_timers[pi].clear();
+      c->jvp_graph[pi] = nullptr;
+      c->jvp_graph_ok = false;
+      return true;  // the direct launches above already produced w
+    }
+    std::copy(key, key + 4, c->jvp_graph_key[pi]);
+    return true;
+  }
+  if (cudaGraphLaunch(c->jvp_graph[pi], s) != cudaSuccess) {
+    cudaGetLastError();
+    c->jvp_graph_ok = false;
+    return false;
+  }
+  c->timing.launches += c->jvp_graph_nodes[pi];
+  c->graph_timers_live[pi] = c->timing.on && !c->graph_timers[pi].empty();
+  return true;
+}
+
 // y = A x = sigma x - J(q) x, or y = -J(q) x when shifted is false (Arnoldi
 // runs on -J: the Krylov space of sigma I - J is that of -J, and the shift is
 // added to the Hessenberg diagonal; this avoids the cancellation of w ~ sigma v)
@@ -242,6 +368,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       return FR_ERR_NOMEM;
     }
     c->krylov_m = m;
+    clear_graphs(c);
   }
   if (op->mode == FR_JV_EXACT && op->jv_prec == FR_F32) {
     float* q32 = vec32(c, 0);
@@ -294,7 +421,8 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     int k = 0;
     res = beta;
     for (int j = 0; j < m; ++j) {
-      if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s, false)) != FR_OK) return e;
+      if (!jvp_graph_apply(c, op, V, j, w, s))
+        if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s, false)) != FR_OK) return e;
       ++it;
       // classical Gram-Schmidt with the DGKS criterion: a second pass only when
       // the first removed more than 1 - 1/sqrt(2) of ||w|| (||w_new|| < 0.7 ||w||)
@@ -351,7 +479,8 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       g[j] = cs[j] * g[j];
       res = std::fabs(g[j + 1]);
       k = j + 1;
-      if (hn != 0.0) k_scale<<<egrid(n), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * ld, n);
+      if (hn != 0.0)
+        FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * ld, n));
       if (res <= o->rtol * beta0 || it >= o->max_it || hn == 0.0) break;
     }
     for (int i = k - 1; i >= 0; --i) {

@@ -28,6 +28,8 @@ struct TimerAcc {
 
 struct Timing {
   bool on = false;
+  bool capture = false;     // launches are being captured into a CUDA graph
+  int64_t mark = 0;         // pending.size() when the current capture began
   long long launches = 0;
   std::vector<cudaEvent_t> pool;
   std::vector<TimerRec> pending;
@@ -57,6 +59,19 @@ struct Timing {
     }
     pending.clear();
   }
+  // Accumulate the timers of one replay of a graph (the events belong to the graph).
+  void accumulate(const std::vector<TimerRec>& recs) {
+    for (const auto& r : recs) {
+      float ms = 0.f;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      auto& x = acc[r.name];
+      x.ms += ms;
+      x.count += 1;
+      x.bytes += r.bytes;
+      x.flops += r.flops;
+    }
+  }
   ~Timing() {
     for (auto& r : pending) {
       cudaEventDestroy(r.a);
@@ -80,13 +95,18 @@ struct LaunchScope {
     ++t.launches;
     if (t.on) {
       a = t.take();
-      cudaEventRecord(a, s);
+      record(a);
     }
+  }
+  // inside a stream capture the event becomes an event-record node of the graph
+  void record(cudaEvent_t e) {
+    if (t.capture) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
   }
   ~LaunchScope() {
     if (t.on) {
       cudaEvent_t b = t.take();
-      cudaEventRecord(b, s);
+      record(b);
       t.pending.push_back(TimerRec{name, a, b, bytes, flops});
     }
   }
