@@ -175,9 +175,13 @@ typedef struct {
 } fr_shifted_op;
 
 typedef struct {
-  int32_t m;               /* restart length (paper: 60; hot path: 30)      */
+  int32_t m;               /* restart length, 1..63 (paper: 60)             */
   double rtol;             /* relative tolerance (paper: 1e-1)              */
   int32_t max_it;          /* total iterations (paper: 100)                 */
+  int32_t reorth;          /* classical Gram-Schmidt passes: 0 one pass (the
+                              default of the paper's Krylov library), 1 a
+                              second pass when the first left less than
+                              1/sqrt(2) of ||w|| (DGKS), 2 always two passes */
 } fr_gmres_opts;
 
 typedef struct {
@@ -187,8 +191,9 @@ typedef struct {
   double rel_res;
 } fr_gmres_stats;
 
-/* Restarted GMRES(m) from x = 0 in FP64 (classical Gram-Schmidt with
- * re-orthogonalisation, Givens rotations).  b, x: device FP64, n_dof. */
+/* Restarted GMRES(m) from x = 0 in FP64 (classical Gram-Schmidt as
+ * opts->reorth says, Givens rotations on the host).  b, x: device FP64,
+ * n_dof.  One host synchronisation per Arnoldi iteration. */
 fr_status gmres_solve(fr_ctx* ctx, const fr_shifted_op* op, const double* b_dev, double* x_dev,
                       const fr_gmres_opts* opts, fr_gmres_stats* stats, void* stream);
 
@@ -208,6 +213,11 @@ typedef struct {
   fr_prec jv_prec;         /* precision of the exact JVP                      */
   double eps;
   fr_gmres_opts gmres;
+  double f32_above;        /* exact mode: F uses the FP32 residual while the
+                              last ||F|| / ||F(q^{0})|| is above this value,
+                              the FP64 residual below it (0: FP64 throughout).
+                              Convergence is only declared on an FP64 F, and
+                              the last F of the stage is always FP64.        */
 } fr_newton_opts;
 
 typedef struct {
@@ -216,6 +226,8 @@ typedef struct {
   int32_t halvings;
   int32_t converged;
   double norm0, norm_final;
+  int32_t f32_evaluations; /* stage residuals evaluated in FP32              */
+  int32_t f64_evaluations; /* stage residuals evaluated in FP64              */
 } fr_stage_stats;
 
 /* ESDIRK tableaus (Sec. 2.3; the paper cites them but prints no

@@ -47,7 +47,7 @@ class ShiftedOp(C.Structure):
 
 
 class GmresOpts(C.Structure):
-    _fields_ = [("m", C.c_int32), ("rtol", C.c_double), ("max_it", C.c_int32)]
+    _fields_ = [("m", C.c_int32), ("rtol", C.c_double), ("max_it", C.c_int32), ("reorth", C.c_int32)]
 
 
 class GmresStats(C.Structure):
@@ -62,13 +62,14 @@ class Tableau(C.Structure):
 class NewtonOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("dtau_init", C.c_double), ("dtau_max", C.c_double),
                 ("max_newton", C.c_int32), ("max_halvings", C.c_int32), ("mode", C.c_int),
-                ("jv_prec", C.c_int), ("eps", C.c_double), ("gmres", GmresOpts)]
+                ("jv_prec", C.c_int), ("eps", C.c_double), ("gmres", GmresOpts), ("f32_above", C.c_double)]
 
 
 class StageStats(C.Structure):
     _fields_ = [("newton_iterations", C.c_int32), ("gmres_iterations", C.c_int32),
                 ("halvings", C.c_int32), ("converged", C.c_int32),
-                ("norm0", C.c_double), ("norm_final", C.c_double)]
+                ("norm0", C.c_double), ("norm_final", C.c_double),
+                ("f32_evaluations", C.c_int32), ("f64_evaluations", C.c_int32)]
 
 
 class AdaptOpts(C.Structure):

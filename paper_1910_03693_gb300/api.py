@@ -200,15 +200,18 @@ class FRContext:
 
     # --------------------------------------------------------------- solvers
     def gmres(self, q64, b, sigma, mode="exact", jv_dtype=torch.float64, eps=1e-6, m=30, rtol=0.1,
-              max_it=100, out=None):
-        """Solve (sigma I - dR/dq(q64)) x = b from x = 0 (FP64 Arnoldi)."""
+              max_it=100, out=None, reorth=0):
+        """Solve (sigma I - dR/dq(q64)) x = b from x = 0 (FP64 Arnoldi).
+
+        ``reorth``: 0 one classical Gram-Schmidt pass (the default of the paper's
+        Krylov library), 1 a second pass when needed (DGKS), 2 always two."""
         q64, b = _dev(q64, "q64"), _dev(b, "b")
         assert q64.dtype == torch.float64 and b.dtype == torch.float64
         x = torch.empty_like(b) if out is None else _dev(out, "out")
         op = _lib.ShiftedOp(float(sigma), q64.data_ptr(),
                             _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
                             _lib.FR_F64 if jv_dtype == torch.float64 else _lib.FR_F32, float(eps))
-        opts = _lib.GmresOpts(int(m), float(rtol), int(max_it))
+        opts = _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth))
         st = _lib.GmresStats()
         _check(lib().gmres_solve(self.h, C.byref(op), _ptr(b), _ptr(x), C.byref(opts), C.byref(st), _stream()),
                "gmres_solve")
@@ -217,11 +220,13 @@ class FRContext:
 
     def esdirk_stage(self, A, stage, dt, qn, Rstages, qi, tol=1e-8, dtau_init=0.05, dtau_max=10.0,
                      mode="exact", jv_dtype=torch.float32, eps=1e-6, m=30, rtol=0.1, max_it=100,
-                     max_newton=200, max_halvings=20, b=None):
+                     max_newton=200, max_halvings=20, b=None, reorth=0, f32_above=0.0):
         """Solve ESDIRK stage ``stage`` (1-based, >= 2) in place in ``qi``.
 
         ``A`` is the s x s tableau (list of rows); ``Rstages[j]`` holds R(q^{j+1})
-        for j < stage-1 and receives R(q^stage) in slot stage-1 when not None."""
+        for j < stage-1 and receives R(q^stage) in slot stage-1 when not None.
+        ``f32_above`` > 0 (exact mode): F from the FP32 residual while
+        ||F||/||F0|| is above it, FP64 below; convergence is judged in FP64."""
         S = len(A)
         tab = _lib.Tableau()
         tab.s = S
@@ -235,14 +240,15 @@ class FRContext:
         o = _lib.NewtonOpts(float(tol), float(dtau_init), float(dtau_max), int(max_newton), int(max_halvings),
                             _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
                             _lib.FR_F64 if jv_dtype == torch.float64 else _lib.FR_F32, float(eps),
-                            _lib.GmresOpts(int(m), float(rtol), int(max_it)))
+                            _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(f32_above))
         st = _lib.StageStats()
         rc = lib().esdirk_stage(self.h, C.byref(tab), int(stage), float(dt), _ptr(qn), ptrs, _ptr(qi),
                                 C.byref(o), C.byref(st), _stream())
         if rc not in (0, -4):
             raise FRError("esdirk_stage", rc)
         return dict(newton=st.newton_iterations, gmres=st.gmres_iterations, halvings=st.halvings,
-                    converged=bool(st.converged), norm0=st.norm0, norm_final=st.norm_final)
+                    converged=bool(st.converged), norm0=st.norm0, norm_final=st.norm_final,
+                    f32_evaluations=st.f32_evaluations, f64_evaluations=st.f64_evaluations)
 
 
     # ------------------------------------------------------------ adaptation

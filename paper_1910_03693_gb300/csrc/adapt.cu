@@ -97,13 +97,13 @@ template <typename T, int ND>
 static void launch_indicator(fr_ctx* c, const T* q, int var, double* eta, cudaStream_t s) {
   for (const auto& b : c->buckets) {
     GeoView<double> g{};
-    const int P = b.p + 1, NK = c->nd * c->nd + 1;
+    const int P = b.p + 1, NKV = geo_nk_vol(c->nd), NKF = geo_nk_face(c->nd);
     int NSP = 1;
     for (int d = 0; d < ND; ++d) NSP *= P;
     if (c->affine) {
-      g.vol = c->d_gaff64; g.ves = NK; g.vks = 1; g.vps = 0;
+      g.vol = c->d_gaff64; g.ves = NKF; g.vks = 1; g.vps = 0;
     } else {
-      g.vol = c->d_gvol64[b.p]; g.ves = (int64_t)NK * NSP; g.vks = NSP; g.vps = 1;
+      g.vol = c->d_gvol64[b.p]; g.ves = (int64_t)NKV * NSP; g.vks = NSP; g.vps = 1;
     }
     const unsigned grid = (unsigned)((b.count + 127) / 128);
     const double nb = (double)b.count * NSP * sizeof(T);

@@ -408,25 +408,46 @@ static fr_status create_impl(const fr_mesh_desc* m, const fr_physics* ph, const 
   // geometry
   c->affine = true;
   for (int e = 0; e < E && c->affine; ++e) c->affine = element_is_affine(c, e);
-  const int NK = nd * nd + 1;
+  const int NK = nd * nd + 1, NKV = geo_nk_vol(nd), NKF = geo_nk_face(nd);
+  // the derived components of one point: src holds S and |J| with stride `ss`
+  auto derive = [nd, NK](const double* src, int64_t ss, double* dst, int64_t ds, bool face_terms) {
+    for (int k = 0; k < NK; ++k) dst[k * ds] = src[k * ss];
+    dst[NK * ds] = 1.0 / src[(NK - 1) * ss];
+    if (!face_terms) return;
+    for (int d = 0; d < nd; ++d) {
+      double a2 = 0.0;
+      for (int j = 0; j < nd; ++j) a2 += src[(d * nd + j) * ss] * src[(d * nd + j) * ss];
+      const double a = std::sqrt(a2);
+      dst[(NK + 1 + d) * ds] = a;
+      dst[(NK + 1 + nd + d) * ds] = 1.0 / a;
+    }
+  };
   if (c->affine) {
-    std::vector<double> g((size_t)E * NK);
-    std::vector<double> vol(NK * 1), face((size_t)nf * NK * 1);
+    // one set of constants per element serves both views (vol uses the first NKV)
+    std::vector<double> g((size_t)E * NKF);
     for (int e = 0; e < E; ++e) {
       // constant metrics: evaluate at degree 0 would be degenerate; use p = 1, first point
       std::vector<double> v1((size_t)NK * ipow(2, nd)), f1((size_t)nf * NK * ipow(2, nd - 1));
       element_metrics(c, e, 1, v1.data(), f1.data());
-      for (int k = 0; k < NK; ++k) g[(size_t)e * NK + k] = v1[(size_t)k * ipow(2, nd)];
+      derive(v1.data(), ipow(2, nd), g.data() + (size_t)e * NKF, 1, true);
     }
     FR_TRY(upload_cast(g, &c->d_gaff64));
     FR_TRY(upload_cast(g, &c->d_gaff32));
   } else {
     for (int p = c->p_min; p <= c->p_max; ++p) {
       const int P = p + 1, NSP = ipow(P, nd), NFP = ipow(P, nd - 1);
-      std::vector<double> vol((size_t)E * NK * NSP), face((size_t)E * nf * NK * NFP);
+      std::vector<double> vol((size_t)E * NKV * NSP), face((size_t)E * nf * NKF * NFP);
 #pragma omp parallel for schedule(static)
-      for (int e = 0; e < E; ++e)
-        element_metrics(c, e, p, vol.data() + (size_t)e * NK * NSP, face.data() + (size_t)e * nf * NK * NFP);
+      for (int e = 0; e < E; ++e) {
+        std::vector<double> v0((size_t)NK * NSP), f0((size_t)nf * NK * NFP);
+        element_metrics(c, e, p, v0.data(), f0.data());
+        double* ve = vol.data() + (size_t)e * NKV * NSP;
+        double* fe = face.data() + (size_t)e * nf * NKF * NFP;
+        for (int sp = 0; sp < NSP; ++sp) derive(v0.data() + sp, NSP, ve + sp, NSP, false);
+        for (int f = 0; f < nf; ++f)
+          for (int t = 0; t < NFP; ++t)
+            derive(f0.data() + (size_t)f * NK * NFP + t, NFP, fe + (size_t)f * NKF * NFP + t, NFP, true);
+      }
       FR_TRY(upload_cast(vol, &c->d_gvol64[p]));
       FR_TRY(upload_cast(vol, &c->d_gvol32[p]));
       FR_TRY(upload_cast(face, &c->d_gface64[p]));

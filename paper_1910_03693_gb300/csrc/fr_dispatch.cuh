@@ -31,27 +31,27 @@ inline MortarTab<T>* mortar_ptr(fr_ctx* c, int Pm, int Ps) {
 template <typename T>
 inline GeoView<T> geo_view(fr_ctx* c, int p) {
   GeoView<T> g{};
-  const int nd = c->nd, NK = nd * nd + 1, P = p + 1;
+  const int nd = c->nd, NKV = geo_nk_vol(nd), NKF = geo_nk_face(nd), P = p + 1;
   const int NSP = ipow(P, nd), NFP = ipow(P, nd - 1);
   const T* aff = std::is_same<T, double>::value ? (const T*)c->d_gaff64 : (const T*)c->d_gaff32;
   if (c->affine) {
     g.vol = aff;
-    g.ves = NK;
+    g.ves = NKF;
     g.vks = 1;
     g.vps = 0;
     g.face = aff;
-    g.fes = NK;
+    g.fes = NKF;
     g.ffs = 0;
     g.fks = 1;
     g.fps = 0;
   } else {
     g.vol = std::is_same<T, double>::value ? (const T*)c->d_gvol64[p] : (const T*)c->d_gvol32[p];
-    g.ves = (int64_t)NK * NSP;
+    g.ves = (int64_t)NKV * NSP;
     g.vks = NSP;
     g.vps = 1;
     g.face = std::is_same<T, double>::value ? (const T*)c->d_gface64[p] : (const T*)c->d_gface32[p];
-    g.fes = (int64_t)c->nf * NK * NFP;
-    g.ffs = NK * NFP;
+    g.fes = (int64_t)c->nf * NKF * NFP;
+    g.ffs = NKF * NFP;
     g.fks = NFP;
     g.fps = 1;
   }

@@ -58,7 +58,14 @@ struct BndRec {
   int32_t me, mf;
 };
 
-// Strided view of metric terms S[d][j] (k = d*nd + j) and |J| (k = nd*nd).
+// Strided view of the geometry: metric terms S[d][j] (k = d*nd + j), |J|
+// (k = nd*nd) and 1/|J| (k = nd*nd + 1) at solution and face points; at face
+// points also |S_d| (k = nd*nd + 2 + d) and 1/|S_d| (k = nd*nd + 2 + nd + d),
+// S_d the row d of S (the face area vector of a face normal to axis d).
+// Everything that does not depend on the state is computed once on the host
+// in FP64: the FP64 divides and square roots it saves are expensive on GB300.
+inline int geo_nk_vol(int nd) { return nd * nd + 2; }
+inline int geo_nk_face(int nd) { return nd * nd + 2 + 2 * nd; }
 template <typename T>
 struct GeoView {
   const T* vol;         // value(e, k, sp) = vol[e*ves + k*vks + sp*vps]

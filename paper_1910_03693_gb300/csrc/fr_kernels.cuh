@@ -166,7 +166,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
     for (int dd = 0; dd < ND; ++dd)
 #pragma unroll
       for (int j = 0; j < ND; ++j) Sf[dd][j] = geo_face(a.geo, e, f, dd * ND + j, t);
-    const T Jinv = T(1) / geo_face(a.geo, e, f, ND * ND, t);
+    const T Jinv = geo_face(a.geo, e, f, ND * ND + 1, t);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T dq[ND];
@@ -304,8 +304,8 @@ __device__ __forceinline__ void slave_coef_at_mortar(const FaceArgs<T>& a, const
   const T g = a.basis[Ps].dgf[ss];
   for (int j = 0; j < ND; ++j) cS[j] = T(0);
   if (Pm == Ps) {
-    const T J = geo_face(a.geo_s, r.se, r.sf, ND * ND, u);
-    for (int j = 0; j < ND; ++j) cS[j] = g * geo_face(a.geo_s, r.se, r.sf, ds * ND + j, u) / J;
+    const T gJ = g * geo_face(a.geo_s, r.se, r.sf, ND * ND + 1, u);
+    for (int j = 0; j < ND; ++j) cS[j] = gJ * geo_face(a.geo_s, r.se, r.sf, ds * ND + j, u);
     return;
   }
   const int ua = u % Pm, ub = ND == 2 ? 0 : u / Pm;
@@ -314,8 +314,8 @@ __device__ __forceinline__ void slave_coef_at_mortar(const FaceArgs<T>& a, const
     for (int aa = 0; aa < Ps; ++aa) {
       const T w = a.mortar->I[ua][aa] * wb;
       const int pt = aa + Ps * bb;
-      const T J = geo_face(a.geo_s, r.se, r.sf, ND * ND, pt);
-      for (int j = 0; j < ND; ++j) cS[j] += w * (g * geo_face(a.geo_s, r.se, r.sf, ds * ND + j, pt) / J);
+      const T gJ = g * geo_face(a.geo_s, r.se, r.sf, ND * ND + 1, pt);
+      for (int j = 0; j < ND; ++j) cS[j] += w * (gJ * geo_face(a.geo_s, r.se, r.sf, ds * ND + j, pt));
     }
   }
 }
@@ -343,16 +343,14 @@ __global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
     slave_at_mortar<ND>(b, r.st, 0, NV, u, qS);
   }
   T A[ND], n[ND];
-  T absA2 = T(0);
   const T sgm = sm ? T(1) : T(-1);
+  const T absA = geo_face(a.geo_m, r.me, r.mf, ND * ND + 2 + dm, t);
+  const T inv_absA = geo_face(a.geo_m, r.me, r.mf, ND * ND + 2 + ND + dm, t);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     A[j] = sgm * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t);
-    absA2 += A[j] * A[j];
+    n[j] = A[j] * inv_absA;
   }
-  const T absA = sqrt(absA2);
-#pragma unroll
-  for (int j = 0; j < ND; ++j) n[j] = A[j] / absA;
   S Fn[NV];
   rusanov<ND>(qM, qS, n, absA, a.gamma, Fn);
   S qc[NV];
@@ -360,10 +358,9 @@ __global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qS[v]);
     T cM[ND], cS[ND];
-    const T gM = a.basis[Pm].dgf[sm];
-    const T JM = geo_face(a.geo_m, r.me, r.mf, ND * ND, t);
+    const T gJ = a.basis[Pm].dgf[sm] * geo_face(a.geo_m, r.me, r.mf, ND * ND + 1, t);
 #pragma unroll
-    for (int j = 0; j < ND; ++j) cM[j] = gM * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t) / JM;
+    for (int j = 0; j < ND; ++j) cM[j] = gJ * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t);
     slave_coef_at_mortar<ND>(a, r, u, cS);
     S GM[ND][NV], GS[ND][NV], Gc[ND][NV];
     load_trace_pt<ND>(a.trq, trv, r.mt, NV, ND * NV, NFPm, t, &GM[0][0]);
@@ -500,16 +497,14 @@ __global__ void __launch_bounds__(128) bnd_kernel(BndArgs<T> a) {
   load_trace_pt<ND>(a.trq, trv, r.mt, 0, NV, NFP, t, qM);
   ghost_state<ND>(qM, a.kind, a.qinf, qG);
   T A[ND], n[ND];
-  T absA2 = T(0);
   const T sg = s ? T(1) : T(-1);
+  const T absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + d, t);
+  const T inv_absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + ND + d, t);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     A[j] = sg * geo_face(a.geo, r.me, r.mf, d * ND + j, t);
-    absA2 += A[j] * A[j];
+    n[j] = A[j] * inv_absA;
   }
-  const T absA = sqrt(absA2);
-#pragma unroll
-  for (int j = 0; j < ND; ++j) n[j] = A[j] / absA;
   S Fn[NV];
   rusanov<ND>(qM, qG, n, absA, a.gamma, Fn);
   S qc[NV];
@@ -517,10 +512,9 @@ __global__ void __launch_bounds__(128) bnd_kernel(BndArgs<T> a) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qG[v]);
     T cM[ND];
-    const T g = a.basis[P].dgf[s];
-    const T J = geo_face(a.geo, r.me, r.mf, ND * ND, t);
+    const T gJ = a.basis[P].dgf[s] * geo_face(a.geo, r.me, r.mf, ND * ND + 1, t);
 #pragma unroll
-    for (int j = 0; j < ND; ++j) cM[j] = g * geo_face(a.geo, r.me, r.mf, d * ND + j, t) / J;
+    for (int j = 0; j < ND; ++j) cM[j] = gJ * geo_face(a.geo, r.me, r.mf, d * ND + j, t);
     S GM[ND][NV], Gc[ND][NV];
     load_trace_pt<ND>(a.trq, trv, r.mt, NV, ND * NV, NFP, t, &GM[0][0]);
 #pragma unroll
@@ -610,7 +604,7 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
     for (int d = 0; d < ND; ++d)
 #pragma unroll
       for (int j = 0; j < ND; ++j) Sm[d][j] = geo_vol(a.geo, e, d * ND + j, sp);
-    Jinv = T(1) / geo_vol(a.geo, e, ND * ND, sp);
+    Jinv = geo_vol(a.geo, e, ND * ND + 1, sp);
 
     S f[ND][NV];
     flux_inviscid<ND>(q, a.gamma, f);

@@ -1,10 +1,10 @@
 // Matrix-free Newton-Krylov of Sec. 2.3: restarted GMRES(m) on
-// (sigma I - dR/dq) dq = F with FP64 Arnoldi (classical Gram-Schmidt applied
-// twice, Givens rotations), and one ESDIRK stage by pseudo-transient
+// (sigma I - dR/dq) dq = F with FP64 Arnoldi (classical Gram-Schmidt, once or
+// with re-orthogonalisation; Givens rotations), and one ESDIRK stage by pseudo-transient
 // continuation with the SER pseudo-time step and dtau back-off.
 //
 // Reductions are deterministic: every block writes its partial sums to a
-// fixed slot and one block adds the partials in slot order.
+// fixed slot and the last block to finish adds the slots in a fixed order.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -14,34 +14,51 @@
 
 namespace frgb {
 
-constexpr int kRedBlocks = 1216;    // 8 blocks per SM on 152 SMs (grid-stride)
+constexpr int kRedBlocks = 1216;    // most blocks of a reduction: 8 per SM on 152 SMs (grid-stride)
 constexpr int kRedThreads = 256;
 constexpr int kMaxK = 64;           // most vectors in one multi-dot (restart length + 1)
 
-// reduction scratch: per-block partials [kRedBlocks][kMaxK], then the reduced
-// values H1 (first Gram-Schmidt pass), H2 (second pass) and ||w||^2
+// reduction scratch (doubles): per-block partials [kRedBlocks][kMaxK], then the
+// reduced values H1 (first Gram-Schmidt pass, ||w||^2 after the dots), H2
+// (second pass), N (||w||^2 after an update), Y (the GMRES coefficients) and
+// one slot holding the arrival counter of the grid reductions
 constexpr int64_t kOutH1 = (int64_t)kRedBlocks * kMaxK;
 constexpr int64_t kOutH2 = kOutH1 + kMaxK;
 constexpr int64_t kOutN = kOutH2 + kMaxK;
 constexpr int64_t kOutY = kOutN + kMaxK;
+constexpr int64_t kTicket = kOutY + kMaxK;
 
 static fr_status ensure_red(fr_ctx* c) {
   if (c->d_red) return FR_OK;
-  c->red_cap = kOutY + kMaxK;
+  c->red_cap = kTicket + 1;
   if (cudaMalloc(&c->d_red, sizeof(double) * c->red_cap) != cudaSuccess) return FR_ERR_NOMEM;
+  if (cudaMemset(c->d_red, 0, sizeof(double) * c->red_cap) != cudaSuccess) return FR_ERR_CUDA;
   if (cudaMallocHost(&c->h_red, sizeof(double) * 4 * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
   return FR_OK;
 }
 
-// block reduction of KC accumulators (kk < k) into partial[block][kk]
+static unsigned* ticket_of(fr_ctx* c) { return reinterpret_cast<unsigned*>(c->d_red + kTicket); }
+
+// Blocks of a reduction over n values: enough to fill every SM, no more than
+// one pair of values per thread.
+static unsigned red_blocks(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + 2 * kRedThreads - 1) / (2 * kRedThreads)));
+}
+
+// Sum vals[0..k) over the grid into out[0..k), deterministically: every block
+// writes its sums (warp-shuffle then shared-memory tree, fixed order) to its
+// own slot of `partial`; the last block to arrive (arrival counter) adds the
+// slots in a fixed order, writes out[] and re-arms the counter.
 template <int KC>
-__device__ __forceinline__ void block_partials(const double (&acc)[KC], int k, double* __restrict__ partial) {
+__device__ __forceinline__ void grid_sum(const double (&vals)[KC], int k, double* __restrict__ partial,
+                                         double* __restrict__ out, unsigned* __restrict__ ticket) {
   __shared__ double red[kRedThreads / 32][KC];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int kk = 0; kk < KC; ++kk) {
     if (kk < k) {
-      double v = acc[kk];
+      double v = vals[kk];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) red[warp][kk] = v;
@@ -49,90 +66,239 @@ __device__ __forceinline__ void block_partials(const double (&acc)[KC], int k, d
   }
   __syncthreads();
   if (threadIdx.x < k) {
-    double s = 0.0;
+    double t = 0.0;
 #pragma unroll
-    for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) s += red[wgi][threadIdx.x];
-    partial[(int64_t)blockIdx.x * kMaxK + threadIdx.x] = s;
+    for (int wi = 0; wi < kRedThreads / 32; ++wi) t += red[wi][threadIdx.x];
+    partial[(int64_t)blockIdx.x * kMaxK + threadIdx.x] = t;
+    __threadfence();
   }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // the last block: thread t adds the slots t, t + blockDim, ... (all loads of
+  // a thread issued together), then the same warp/shared-memory tree as above
+  constexpr int kSlots = (kRedBlocks + kRedThreads - 1) / kRedThreads;
+  double tot[KC];
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) tot[kk] = 0.0;
+#pragma unroll
+  for (int r = 0; r < kSlots; ++r) {
+    const int bl = threadIdx.x + r * kRedThreads;
+    if (bl < (int)gridDim.x) {
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk)
+        if (kk < k) tot[kk] += __ldcg(partial + (int64_t)bl * kMaxK + kk);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) {
+    if (kk < k) {
+      double v = tot[kk];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][kk] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double t = 0.0;
+#pragma unroll
+    for (int wi = 0; wi < kRedThreads / 32; ++wi) t += red[wi][threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// partial[block][kk] = sum_i V[kk][i] w[i] (kk < k); with V == nullptr, ||w||^2
-// partial[block][kk] = sum_i V[kk][i] w[i] for kk < k, and, when with_norm,
-// partial[block][k] = ||w||^2.  V == nullptr gives ||w||^2 alone in slot 0.
+// Slot q of a vector seen as pairs (VEC: 16-byte loads of two values) or
+// single values: slot nw = n / W is the odd tail (one value) when VEC and n is
+// odd; slots beyond the vector read as zero.
+template <bool VEC>
+struct Slots {
+  static constexpr int W = VEC ? 2 : 1;
+  // streaming load (the Krylov columns: read once per pass)
+  __device__ static void load_stream(const double* __restrict__ p, int64_t q, int64_t nw, int64_t n, double (&x)[2]) {
+    if (q < nw) {
+      if (VEC) {
+        const double2 t = __ldcs(reinterpret_cast<const double2*>(p + 2 * q));
+        x[0] = t.x;
+        x[1] = t.y;
+      } else {
+        x[0] = __ldcs(p + q);
+        x[1] = 0.0;
+      }
+    } else {
+      x[0] = (VEC && q == nw && (n & 1)) ? p[2 * nw] : 0.0;
+      x[1] = 0.0;
+    }
+  }
+  // ordinary load (w: read again by the update that follows)
+  __device__ static void load(const double* __restrict__ p, int64_t q, int64_t nw, int64_t n, double (&x)[2]) {
+    if (q < nw) {
+      if (VEC) {
+        const double2 t = *reinterpret_cast<const double2*>(p + 2 * q);
+        x[0] = t.x;
+        x[1] = t.y;
+      } else {
+        x[0] = p[q];
+        x[1] = 0.0;
+      }
+    } else {
+      x[0] = (VEC && q == nw && (n & 1)) ? p[2 * nw] : 0.0;
+      x[1] = 0.0;
+    }
+  }
+  __device__ static void store(double* __restrict__ p, int64_t q, int64_t nw, int64_t n, const double (&x)[2]) {
+    if (q < nw) {
+      if (VEC) *reinterpret_cast<double2*>(p + 2 * q) = make_double2(x[0], x[1]);
+      else p[q] = x[0];
+    } else if (VEC && q == nw && (n & 1)) {
+      p[2 * nw] = x[0];
+    }
+  }
+};
+
+// Slots handled per thread and loop step: U slots spaced one grid apart, all
+// their loads issued before any arithmetic (bytes in flight per thread scale
+// with U), fewer for many columns to bound the registers.
 template <int KC>
+struct Unroll {
+  static constexpr int U = KC <= 2 ? 4 : (KC <= 8 ? 2 : 1);
+  static constexpr int CH = KC < 8 ? KC : 8;   // columns per load batch
+};
+
+// out[kk] = V[kk]^T w for kk < k, and, when with_norm, out[k] = ||w||^2.
+// V == nullptr: out[0] = ||w||^2 alone.
+template <int KC, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int k,
                                                            const double* __restrict__ w, int64_t n,
-                                                           double* __restrict__ partial, int with_norm) {
+                                                           double* __restrict__ partial, double* __restrict__ out,
+                                                           unsigned* __restrict__ ticket, int with_norm) {
+  constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
+  using L = Slots<VEC>;
   double acc[KC + 1];
 #pragma unroll
   for (int kk = 0; kk <= KC; ++kk) acc[kk] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = w[i];
-    if (V) {   // V == nullptr: norm only
+  const int64_t nw = n / L::W, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t last = nw + ((VEC && (n & 1)) ? 0 : -1);   // highest slot holding data
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 <= last; q0 += U * stride) {
+    double wv[U][2];
 #pragma unroll
-      for (int kk = 0; kk < KC; ++kk)
-        if (kk < k) acc[kk] += V[kk * ldv + i] * wi;
+    for (int u = 0; u < U; ++u) L::load(w, q0 + u * stride, nw, n, wv[u]);
+    if (V) {
+#pragma unroll
+      for (int c0 = 0; c0 < KC; c0 += CH) {
+        if (c0 < k) {
+          double vv[U][CH][2];
+#pragma unroll
+          for (int t = 0; t < CH; ++t)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (c0 + t < k) L::load_stream(V + (c0 + t) * ldv, q0 + u * stride, nw, n, vv[u][t]);
+#pragma unroll
+          for (int t = 0; t < CH; ++t)
+            if (c0 + t < k) {
+#pragma unroll
+              for (int u = 0; u < U; ++u) acc[c0 + t] += vv[u][t][0] * wv[u][0] + vv[u][t][1] * wv[u][1];
+            }
+        }
+      }
     }
-    acc[KC] += wi * wi;
+    // ||w||^2 only when asked for: on GB300 every FP64 FMA here costs about as
+    // much time as the 8 bytes it is paired with
+    if (!V || with_norm) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[KC] += wv[u][0] * wv[u][0] + wv[u][1] * wv[u][1];
+    }
   }
   if (!V) {
     const double one[1] = {acc[KC]};
-    block_partials<1>(one, 1, partial);
+    grid_sum<1>(one, 1, partial, out, ticket);
     return;
   }
   // slots 0..k-1: the dots; slot k: ||w||^2 (selects only, no runtime indexing)
-  double out[KC + 1];
+  double o[KC + 1];
 #pragma unroll
-  for (int kk = 0; kk < KC; ++kk) out[kk] = kk < k ? acc[kk] : acc[KC];
-  out[KC] = acc[KC];
-  block_partials<KC + 1>(out, with_norm ? k + 1 : k, partial);
+  for (int kk = 0; kk < KC; ++kk) o[kk] = kk < k ? acc[kk] : acc[KC];
+  o[KC] = acc[KC];
+  grid_sum<KC + 1>(o, with_norm ? k + 1 : k, partial, out, ticket);
 }
 
-// out[kk] = sum over blocks of partial[b][kk]: one block per coefficient,
-// fixed-order tree (deterministic)
-__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partial, int nb, int k,
-                                                          double* __restrict__ out) {
-  __shared__ double red[256];
-  const int kk = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(int64_t)b * kMaxK + kk];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[kk] = red[0];
-}
-
-// second pass update: w <- w - sum_kk h[kk] V[kk]; partial[block][0] = ||w_new||^2
-template <int KC>
+// w <- w - sum_kk h[kk] V[kk]; out[0] = ||w_new||^2
+template <int KC, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __restrict__ V, int64_t ldv, int k,
                                                               const double* __restrict__ h, double* __restrict__ w,
-                                                              int64_t n, double* __restrict__ partial) {
+                                                              int64_t n, double* __restrict__ partial,
+                                                              double* __restrict__ out, unsigned* __restrict__ ticket) {
+  constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
+  using L = Slots<VEC>;
   __shared__ double hs[KC];
   if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < k ? h[threadIdx.x] : 0.0;
   __syncthreads();
   double acc[1] = {0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double x = w[i];
+  const int64_t nw = n / L::W, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t last = nw + ((VEC && (n & 1)) ? 0 : -1);
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 <= last; q0 += U * stride) {
+    double x[U][2];
 #pragma unroll
-    for (int kk = 0; kk < KC; ++kk)
-      if (kk < k) x -= hs[kk] * V[kk * ldv + i];
-    w[i] = x;
-    acc[0] += x * x;
+    for (int u = 0; u < U; ++u) L::load(w, q0 + u * stride, nw, n, x[u]);
+#pragma unroll
+    for (int c0 = 0; c0 < KC; c0 += CH) {
+      if (c0 < k) {
+        double vv[U][CH][2];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (c0 + t < k) L::load_stream(V + (c0 + t) * ldv, q0 + u * stride, nw, n, vv[u][t]);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+          if (c0 + t < k) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              x[u][0] -= hs[c0 + t] * vv[u][t][0];
+              x[u][1] -= hs[c0 + t] * vv[u][t][1];
+            }
+          }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      L::store(w, q0 + u * stride, nw, n, x[u]);
+      acc[0] += x[u][0] * x[u][0] + x[u][1] * x[u][1];
+    }
   }
-  block_partials<1>(acc, 1, partial);
+  grid_sum<1>(acc, 1, partial, out, ticket);
 }
 
-#define FR_KC_DISPATCH(k, KERNEL, ...)                                   \
-  do {                                                                   \
-    if ((k) <= 4) KERNEL<4><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);        \
-    else if ((k) <= 8) KERNEL<8><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);   \
-    else if ((k) <= 16) KERNEL<16><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__); \
-    else if ((k) <= 32) KERNEL<32><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__); \
-    else KERNEL<64><<<kRedBlocks, kRedThreads, 0, s>>>(__VA_ARGS__);                \
+// launch KERNEL<KC, VEC> with the smallest KC >= k; VEC when every vector
+// starts on a 16-byte boundary and the column stride is even
+#define FR_KC_DISPATCH(k, vec, grid, KERNEL, ...)                                                   \
+  do {                                                                                              \
+    if (vec) {                                                                                      \
+      if ((k) <= 1) KERNEL<1, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                      \
+      else if ((k) <= 2) KERNEL<2, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                 \
+      else if ((k) <= 4) KERNEL<4, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                 \
+      else if ((k) <= 8) KERNEL<8, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                 \
+      else if ((k) <= 16) KERNEL<16, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);               \
+      else if ((k) <= 32) KERNEL<32, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);               \
+      else KERNEL<64, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                              \
+    } else {                                                                                        \
+      if ((k) <= 4) KERNEL<4, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                     \
+      else if ((k) <= 8) KERNEL<8, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
+      else if ((k) <= 16) KERNEL<16, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
+      else if ((k) <= 32) KERNEL<32, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
+      else KERNEL<64, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                             \
+    }                                                                                               \
   } while (0)
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// column stride of the Krylov basis: n_dof_capacity rounded up to 32 values,
+// so that every column starts on a 256-byte boundary
+static int64_t krylov_ld(const fr_ctx* c) { return (c->n_dof_cap + 31) & ~(int64_t)31; }
 
 __global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -160,11 +326,12 @@ __global__ void k_shift(double sigma, const double* __restrict__ v, const T* __r
     out[i] = sigma * v[i] - (double)J[i];
 }
 
-// F = -q / (w dt) + R + rhs
-__global__ void k_stage_F(const double* __restrict__ q, const double* __restrict__ R,
+// F = -q / (w dt) + R + rhs   (R in FP64 or FP32)
+template <typename T>
+__global__ void k_stage_F(const double* __restrict__ q, const T* __restrict__ R,
                           const double* __restrict__ rhs, double inv_wdt, double* __restrict__ F, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    F[i] = -q[i] * inv_wdt + R[i] + rhs[i];
+    F[i] = -q[i] * inv_wdt + (double)R[i] + rhs[i];
 }
 
 static unsigned egrid(int64_t n) {
@@ -177,8 +344,10 @@ static fr_status multidot(fr_ctx* c, const double* V, int64_t ldv, int k, const 
   double* part = c->d_red;
   double* dout = c->d_red + kOutH1;
   const int kk = V ? k : 1;
-  FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1), FR_KC_DISPATCH(kk, k_multidot, V, ldv, kk, w, n, part, 0));
-  FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<kk, 256, 0, s>>>(part, kRedBlocks, kk, dout));
+  const bool vec = aligned16(w) && (!V || (aligned16(V) && ldv % 2 == 0));
+  const unsigned g = red_blocks(n);
+  FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1),
+              FR_KC_DISPATCH(kk, vec, g, k_multidot, V, ldv, kk, w, n, part, dout, ticket_of(c), 0));
   cudaMemcpyAsync(c->h_red, dout, sizeof(double) * (V ? k : 1), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "multidot");
   std::memcpy(out_host, c->h_red, sizeof(double) * (V ? k : 1));
@@ -231,7 +400,7 @@ static bool jvp_graph_apply(fr_ctx* c, const fr_shifted_op* op, const double* V,
   if (!c->use_graphs || !c->jvp_graph_ok || op->mode != FR_JV_EXACT || j < 0 || j >= kMaxK) return false;
   const int pi = op->jv_prec == FR_F32 ? 1 : 0;
   const fr_prec prec = pi ? FR_F32 : FR_F64;
-  const int64_t n = c->n_dof, ld = c->n_dof_cap;
+  const int64_t n = c->n_dof, ld = krylov_ld(c);
   if (!c->d_jidx) {
     if (cudaMalloc(&c->d_jidx, sizeof(int)) != cudaSuccess) return false;
     if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return false;
@@ -351,12 +520,13 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
 }
 
 // GMRES(m) with x0 = 0.  R0 (optional) = R(q) for the finite-difference mode.
+// b_norm: ||b|| when the caller already has it, else negative.
 static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0, const double* b, double* x,
-                            const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s) {
+                            const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s, double b_norm = -1.0) {
   const int m = o->m;
-  const int64_t n = c->n_dof, ld = c->n_dof_cap;
-  if (m < 1 || m + 1 > kMaxK || o->max_it < 1 || !(o->rtol > 0.0)) {
-    set_error("gmres_solve: need 1 <= m <= 63, max_it >= 1, rtol > 0");
+  const int64_t n = c->n_dof, ld = krylov_ld(c);
+  if (m < 1 || m + 1 > kMaxK || o->max_it < 1 || !(o->rtol > 0.0) || o->reorth < 0 || o->reorth > 2) {
+    set_error("gmres_solve: need 1 <= m <= 63, max_it >= 1, rtol > 0, reorth in {0, 1, 2}");
     return FR_ERR_INVALID;
   }
   if (ensure_red(c) != FR_OK) return FR_ERR_NOMEM;
@@ -387,9 +557,9 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   if (!w || !r) return FR_ERR_NOMEM;
   std::memset(st, 0, sizeof(*st));
   cudaMemsetAsync(x, 0, sizeof(double) * n, s);
-  double beta0;
-  fr_status e = norm2(c, b, n, &beta0, s);
-  if (e != FR_OK) return e;
+  double beta0 = b_norm;
+  fr_status e = FR_OK;
+  if (!(beta0 >= 0.0) && (e = norm2(c, b, n, &beta0, s)) != FR_OK) return e;
   if (!std::isfinite(beta0)) {
     set_error("gmres_solve: non-finite right-hand side");
     return FR_ERR_NONFINITE;
@@ -402,9 +572,15 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   int it = 0;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(kMaxK), h2(kMaxK);
   double res = beta0;
+  const bool vec = aligned16(w) && aligned16(V) && ld % 2 == 0;
+  const unsigned grid = red_blocks(n);
+  unsigned* ticket = ticket_of(c);
+  double* part = c->d_red;
+  bool first = true;
   while (true) {
-    double beta;
-    if ((e = norm2(c, r, n, &beta, s)) != FR_OK) return e;
+    double beta = beta0;   // r = b on the first cycle
+    if (!first && (e = norm2(c, r, n, &beta, s)) != FR_OK) return e;
+    first = false;
     if (beta <= o->rtol * beta0) {
       st->converged = 1;
       res = beta;
@@ -424,29 +600,38 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       if (!jvp_graph_apply(c, op, V, j, w, s))
         if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s, false)) != FR_OK) return e;
       ++it;
-      // classical Gram-Schmidt with the DGKS criterion: a second pass only when
-      // the first removed more than 1 - 1/sqrt(2) of ||w|| (||w_new|| < 0.7 ||w||)
+      // classical Gram-Schmidt: one pass (reorth 0), a second pass when the
+      // first removed more than half of ||w||^2, ||w_new|| < 0.7 ||w|| (DGKS,
+      // reorth 1), or always two passes (reorth 2).  Each pass is one multi-dot
+      // and one update; both end in a grid reduction, no separate launch.
       {
         const int kk = j + 1;
-        double* part = c->d_red;
-        FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1), FR_KC_DISPATCH(kk, k_multidot, V, ld, kk, w, n, part, 1));
-        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<kk + 1, 256, 0, s>>>(part, kRedBlocks, kk + 1, c->d_red + kOutH1));
+        const int ro = o->reorth;
+        FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
+                    FR_KC_DISPATCH(kk, vec, grid, k_multidot, V, ld, kk, w, n, part, c->d_red + kOutH1, ticket,
+                                   ro == 1 ? 1 : 0));
         FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
-                    FR_KC_DISPATCH(kk, k_orth_update, V, ld, kk, c->d_red + kOutH1, w, n, part));
-        FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, 256, 0, s>>>(part, kRedBlocks, 1, c->d_red + kOutN));
+                    FR_KC_DISPATCH(kk, vec, grid, k_orth_update, V, ld, kk, c->d_red + kOutH1, w, n, part,
+                                   c->d_red + kOutN, ticket));
+        if (ro == 2) {
+          FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
+                      FR_KC_DISPATCH(kk, vec, grid, k_multidot, V, ld, kk, w, n, part, c->d_red + kOutH2, ticket, 0));
+          FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
+                      FR_KC_DISPATCH(kk, vec, grid, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part,
+                                     c->d_red + kOutN, ticket));
+        }
         cudaMemcpyAsync(c->h_red, c->d_red + kOutH1, sizeof(double) * 3 * kMaxK, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
-        const double w_old = std::sqrt(c->h_red[kk]);
         for (int i = 0; i <= j; ++i) {
           h[i] = c->h_red[i];
-          h2[i] = 0.0;
+          h2[i] = ro == 2 ? c->h_red[kMaxK + i] : 0.0;
         }
-        if (std::sqrt(c->h_red[2 * kMaxK]) < 0.7 * w_old) {
-          FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1), FR_KC_DISPATCH(kk, k_multidot, V, ld, kk, w, n, part, 0));
-          FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<kk, 256, 0, s>>>(part, kRedBlocks, kk, c->d_red + kOutH2));
+        if (ro == 1 && std::sqrt(c->h_red[2 * kMaxK]) < 0.7 * std::sqrt(c->h_red[kk])) {
+          FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
+                      FR_KC_DISPATCH(kk, vec, grid, k_multidot, V, ld, kk, w, n, part, c->d_red + kOutH2, ticket, 0));
           FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
-                      FR_KC_DISPATCH(kk, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part));
-          FR_LAUNCH(c, "arnoldi_reduce", s, k_reduce_partials<<<1, 256, 0, s>>>(part, kRedBlocks, 1, c->d_red + kOutN));
+                      FR_KC_DISPATCH(kk, vec, grid, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part,
+                                     c->d_red + kOutN, ticket));
           cudaMemcpyAsync(c->h_red + kMaxK, c->d_red + kOutH2, sizeof(double) * 2 * kMaxK, cudaMemcpyDeviceToHost, s);
           if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
           for (int i = 0; i <= j; ++i) h2[i] = c->h_red[kMaxK + i];
@@ -538,7 +723,8 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
                        double* const* Rstages_dev, double* qi_dev, const fr_newton_opts* o,
                        fr_stage_stats* st, void* stream) {
   if (!c || !tab || !qn_dev || !qi_dev || !o || !st || tab->s < 2 || tab->s > 6 || stage < 2 ||
-      stage > tab->s || !(dt > 0.0) || !(o->tol > 0.0) || !(o->dtau_init > 0.0) || !(o->dtau_max > 0.0)) {
+      stage > tab->s || !(dt > 0.0) || !(o->tol > 0.0) || !(o->dtau_init > 0.0) || !(o->dtau_max > 0.0) ||
+      !(o->f32_above >= 0.0)) {
     set_error("esdirk_stage: bad argument");
     return FR_ERR_INVALID;
   }
@@ -569,18 +755,35 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
   for (int j = 0; j < i; ++j)
     if (tab->A[i * S + j] != 0.0) vaxpby(c, dt * tab->A[i * S + j] * inv_wdt, Rstages_dev[j], 1.0, rhs, n, s);
   std::memset(st, 0, sizeof(*st));
+  // F from the FP64 residual, or (mixed mode, while ||F|| is large) from the
+  // FP32 residual of the FP32-rounded state; the FP32 buffers are the GMRES
+  // product scratch, idle between solves
+  const bool mixedF = o->mode == FR_JV_EXACT && o->f32_above > 0.0;
+  float* q32 = mixedF ? vec32(c, 1) : nullptr;
+  float* R32 = mixedF ? vec32(c, 2) : nullptr;
+  if (mixedF && (!q32 || !R32)) return FR_ERR_NOMEM;
+  bool f32 = mixedF;
   auto evalF = [&](double* norm) -> fr_status {
-    fr_status ee = launch_residual(c, qi_dev, R, FR_F64, s);
-    if (ee != FR_OK) return ee;
-    FR_LAUNCH_B(c, "vec", s, 32.0 * n, k_stage_F<<<egrid(n), 256, 0, s>>>(qi_dev, R, rhs, inv_wdt, F, n));
-    return norm2(c, F, n, norm, s);
+    fr_status ee;
+    if (f32) {
+      vcast_f64_f32(c, qi_dev, q32, n, s);
+      if ((ee = launch_residual(c, q32, R32, FR_F32, s)) != FR_OK) return ee;
+      FR_LAUNCH_B(c, "vec", s, 28.0 * n, k_stage_F<float><<<egrid(n), 256, 0, s>>>(qi_dev, R32, rhs, inv_wdt, F, n));
+      st->f32_evaluations += 1;
+    } else {
+      if ((ee = launch_residual(c, qi_dev, R, FR_F64, s)) != FR_OK) return ee;
+      FR_LAUNCH_B(c, "vec", s, 32.0 * n, k_stage_F<double><<<egrid(n), 256, 0, s>>>(qi_dev, R, rhs, inv_wdt, F, n));
+      st->f64_evaluations += 1;
+    }
+    if ((ee = norm2(c, F, n, norm, s)) != FR_OK) return ee;
+    if (!std::isfinite(*norm)) {
+      set_error("esdirk_stage: non-finite stage residual");
+      return FR_ERR_NONFINITE;
+    }
+    return FR_OK;
   };
   double norm;
   if ((e = evalF(&norm)) != FR_OK) return e;
-  if (!std::isfinite(norm)) {
-    set_error("esdirk_stage: non-finite stage residual");
-    return FR_ERR_NONFINITE;
-  }
   st->norm0 = norm;
   double dtau = o->dtau_init, norm_prev = -1.0;
   fr_shifted_op op;
@@ -589,7 +792,12 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
   op.jv_prec = o->mode == FR_JV_FD ? FR_F64 : o->jv_prec;
   op.eps = o->eps;
   for (int m = 0; m < o->max_newton; ++m) {
-    if (norm <= o->tol * st->norm0) {
+    if (f32 && norm <= o->f32_above * st->norm0) {
+      // close enough to the FP32 noise: FP64 from here on, starting with this F
+      f32 = false;
+      if ((e = evalF(&norm)) != FR_OK) return e;
+    }
+    if (!f32 && norm <= o->tol * st->norm0) {
       st->converged = 1;
       break;
     }
@@ -597,7 +805,7 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
     fr_gmres_stats gs;
     for (int h = 0; h <= o->max_halvings; ++h) {
       op.sigma = inv_wdt + 1.0 / dtau;
-      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s)) != FR_OK) return e;
+      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s, norm)) != FR_OK) return e;
       st->gmres_iterations += gs.iterations;
       if (gs.converged) break;
       dtau *= 0.5;
@@ -606,11 +814,11 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
     vaxpby(c, 1.0, dq, 1.0, qi_dev, n, s);
     norm_prev = norm;
     if ((e = evalF(&norm)) != FR_OK) return e;
-    if (!std::isfinite(norm)) {
-      set_error("esdirk_stage: non-finite stage residual");
-      return FR_ERR_NONFINITE;
-    }
     st->newton_iterations += 1;
+  }
+  if (f32) {   // iteration limit reached in the FP32 phase: the stage ends on an FP64 F
+    f32 = false;
+    if ((e = evalF(&norm)) != FR_OK) return e;
   }
   if (norm <= o->tol * st->norm0) st->converged = 1;
   st->norm_final = norm;

@@ -162,18 +162,18 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_adj_kernel(VolAdjA
 
   T q[NV];
   T Sm[ND][ND];
-  T J = T(1);
+  T Jinv = T(1);
   if (valid) {
 #pragma unroll
     for (int d = 0; d < ND; ++d)
 #pragma unroll
       for (int j = 0; j < ND; ++j) Sm[d][j] = geo_vol(a.geo, e, d * ND + j, sp);
-    J = geo_vol(a.geo, e, ND * ND, sp);
+    Jinv = geo_vol(a.geo, e, ND * ND + 1, sp);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       q[v] = a.q[a.state_base + (i * NV + v) * NSP + sp];
       sq[v * NSP + sp] = q[v];
-      sdb[v * NSP + sp] = -a.w[a.state_base + (i * NV + v) * NSP + sp] / J;
+      sdb[v * NSP + sp] = -a.w[a.state_base + (i * NV + v) * NSP + sp] * Jinv;
     }
   }
   __syncthreads();
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_adj_kernel(VolAdjA
           T acc = T(0);
 #pragma unroll
           for (int d = 0; d < ND; ++d) acc += Sm[d][j] * gref[d][v];
-          G[j][v] = acc / J;
+          G[j][v] = acc * Jinv;
         }
     }
     flux_adjoint_q<ND>(q, G, fbar, a.gamma, a.mu, a.kappa, true, VISC, qb);
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(VolCfg<ND, P>::THREADS) vol_adj_kernel(VolAdjA
           T acc = T(0);
 #pragma unroll
           for (int j = 0; j < ND; ++j) acc += Sm[d][j] * Gb[j][v];
-          sgb[(d * NV + v) * NSP + sp] = acc / J;
+          sgb[(d * NV + v) * NSP + sp] = acc * Jinv;
         }
     }
   }
@@ -319,7 +319,7 @@ template <int ND, typename T>
 __device__ __forceinline__ void gradient_to_ref_adjoint(const GeoView<T>& g, int64_t e, int f, int t,
                                                         const T (*Gb)[ND + 2], T (*dqb)[ND + 2]) {
   constexpr int NV = ND + 2;
-  const T J = geo_face(g, e, f, ND * ND, t);
+  const T Jinv = geo_face(g, e, f, ND * ND + 1, t);
 #pragma unroll
   for (int d = 0; d < ND; ++d)
 #pragma unroll
@@ -327,7 +327,7 @@ __device__ __forceinline__ void gradient_to_ref_adjoint(const GeoView<T>& g, int
       T acc = T(0);
 #pragma unroll
       for (int j = 0; j < ND; ++j) acc += geo_face(g, e, f, d * ND + j, t) * Gb[j][v];
-      dqb[d][v] = acc / J;
+      dqb[d][v] = acc * Jinv;
     }
 }
 
@@ -356,16 +356,15 @@ __global__ void __launch_bounds__(128) face_adj_kernel(FaceAdjArgs<T> a) {
   fa.mortar = a.mortar;
   load_trace_pt<ND>(a.trq, (const T*)nullptr, r.mt, 0, NV, NFPm, t, qM);
   slave_at_mortar<ND>(fa, r.st, 0, NV, u, qS);
-  T A[ND], n[ND], absA2 = T(0);
+  T A[ND], n[ND];
   const T sgm = sm ? T(1) : T(-1), sgs = ss ? T(1) : T(-1);
+  const T absA = geo_face(a.geo_m, r.me, r.mf, ND * ND + 2 + dm, t);
+  const T inv_absA = geo_face(a.geo_m, r.me, r.mf, ND * ND + 2 + ND + dm, t);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     A[j] = sgm * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t);
-    absA2 += A[j] * A[j];
+    n[j] = A[j] * inv_absA;
   }
-  const T absA = sqrt(absA2);
-#pragma unroll
-  for (int j = 0; j < ND; ++j) n[j] = A[j] / absA;
 
   // adjoint seeds
   T Fnb[NV], qcb[NV], qMb[NV], qSb[NV];
@@ -407,10 +406,9 @@ __global__ void __launch_bounds__(128) face_adj_kernel(FaceAdjArgs<T> a) {
     T qc[NV], cM[ND], cS[ND];
 #pragma unroll
     for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qS[v]);
-    const T gM = a.basis[Pm].dgf[sm];
-    const T JM = geo_face(a.geo_m, r.me, r.mf, ND * ND, t);
+    const T gJ = a.basis[Pm].dgf[sm] * geo_face(a.geo_m, r.me, r.mf, ND * ND + 1, t);
 #pragma unroll
-    for (int j = 0; j < ND; ++j) cM[j] = gM * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t) / JM;
+    for (int j = 0; j < ND; ++j) cM[j] = gJ * geo_face(a.geo_m, r.me, r.mf, dm * ND + j, t);
     {
       FaceArgs<T> fb2 = fa;
       fb2.basis = a.basis;
@@ -567,16 +565,15 @@ __global__ void __launch_bounds__(128) bnd_adj_kernel(BndAdjArgs<T> a) {
   T qM[NV], qG[NV];
   load_trace_pt<ND>(a.trq, (const T*)nullptr, r.mt, 0, NV, NFP, t, qM);
   ghost_state<ND>(qM, a.kind, a.qinf, qG);
-  T A[ND], n[ND], absA2 = T(0);
+  T A[ND], n[ND];
   const T sg = s ? T(1) : T(-1);
+  const T absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + d, t);
+  const T inv_absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + ND + d, t);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     A[j] = sg * geo_face(a.geo, r.me, r.mf, d * ND + j, t);
-    absA2 += A[j] * A[j];
+    n[j] = A[j] * inv_absA;
   }
-  const T absA = sqrt(absA2);
-#pragma unroll
-  for (int j = 0; j < ND; ++j) n[j] = A[j] / absA;
   T Fnb[NV], qcb[NV], qMb[NV], qGb[NV];
   const T* fbm = a.fbar + r.mo;
 #pragma unroll
@@ -592,10 +589,9 @@ __global__ void __launch_bounds__(128) bnd_adj_kernel(BndAdjArgs<T> a) {
     T qc[NV], cM[ND];
 #pragma unroll
     for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qG[v]);
-    const T g = a.basis[P].dgf[s];
-    const T J = geo_face(a.geo, r.me, r.mf, ND * ND, t);
+    const T gJ = a.basis[P].dgf[s] * geo_face(a.geo, r.me, r.mf, ND * ND + 1, t);
 #pragma unroll
-    for (int j = 0; j < ND; ++j) cM[j] = g * geo_face(a.geo, r.me, r.mf, d * ND + j, t) / J;
+    for (int j = 0; j < ND; ++j) cM[j] = gJ * geo_face(a.geo, r.me, r.mf, d * ND + j, t);
     T GM[ND][NV], Gc[ND][NV];
     load_trace_pt<ND>(a.trq, (const T*)nullptr, r.mt, NV, ND * NV, NFP, t, &GM[0][0]);
 #pragma unroll

@@ -58,7 +58,8 @@ def _small_system():
     return m, cases.random_state(m, 2), ph
 
 
-def test_gmres_matches_dense_solve(built):
+@pytest.mark.parametrize("reorth", [1, 2])
+def test_gmres_matches_dense_solve(built, reorth):
     from oracle import linearize as L
     m, q, ph = _small_system()
     fr, ctx = oracle_fr(m, ph), gpu_ctx(m, ph)
@@ -70,15 +71,17 @@ def test_gmres_matches_dense_solve(built):
     xref = torch.linalg.solve(A, b).numpy()
     qs = ctx.pack(qt.cuda())
     bs = ctx.pack(b.cuda())
-    x, st = ctx.gmres(qs, bs, sigma, mode="exact", rtol=1e-13, m=30, max_it=3000)
+    x, st = ctx.gmres(qs, bs, sigma, mode="exact", rtol=1e-13, m=30, max_it=3000, reorth=reorth)
     assert st["converged"] and st["restarts"] >= 1
     xg = ctx.unpack(x).cpu().numpy()
     assert np.abs(xg - xref).max() <= 1e-10 * np.abs(xref).max()
 
 
-def test_gmres_iterates_match_oracle(built):
-    """At the paper's tolerance (1e-1) the GPU (classical GS twice) and the oracle
-    (modified GS) build the same Krylov space: same iteration count, same x."""
+@pytest.mark.parametrize("reorth", [0, 1, 2])
+def test_gmres_iterates_match_oracle(built, reorth):
+    """At the paper's tolerance (1e-1) the GPU (classical Gram-Schmidt once, with
+    the DGKS second pass, or twice) and the oracle (modified Gram-Schmidt) build
+    the same Krylov space: same iteration count, same x."""
     from oracle import krylov
     from oracle import linearize as L
     m, q, ph = cases.workload_vortex2d(6, 2)
@@ -88,17 +91,19 @@ def test_gmres_iterates_match_oracle(built):
     sigma = 1.0 / (0.4358665215 * 0.05) + 1.0 / 0.05
     xo, so = krylov.gmres(lambda v: sigma * v - L.jvp(fr, qt, v), b, m=30, rtol=1e-1, max_it=100)
     qs = ctx.pack(qt.cuda())
-    x, st = ctx.gmres(qs, ctx.pack(b.cuda()), sigma, mode="exact", rtol=1e-1, m=30, max_it=100)
+    x, st = ctx.gmres(qs, ctx.pack(b.cuda()), sigma, mode="exact", rtol=1e-1, m=30, max_it=100, reorth=reorth)
     assert st["iterations"] == so["iterations"]
     xg = ctx.unpack(x).cpu().numpy()
     assert np.abs(xg - xo.numpy()).max() <= 1e-9 * np.abs(xo.numpy()).max()
 
 
-@pytest.mark.parametrize("mode,jv_dtype", [("fd", torch.float64), ("exact", torch.float64),
-                                           ("exact", torch.float32)])
-def test_esdirk3_stage_matches_oracle(built, mode, jv_dtype):
+@pytest.mark.parametrize("mode,jv_dtype,f32_above", [("fd", torch.float64, 0.0), ("exact", torch.float64, 0.0),
+                                                     ("exact", torch.float32, 0.0), ("exact", torch.float32, 1e-3)])
+def test_esdirk3_stage_matches_oracle(built, mode, jv_dtype, f32_above):
     """Stage 2 of ESDIRK3 on the 2D vortex to ||F|| <= 1e-8 ||F0|| (the oracle
-    with the paper's FD Jv); the converged stage values agree to the tolerance."""
+    with the paper's FD Jv); the converged stage values agree to the tolerance.
+    With f32_above the early Newton iterations use the FP32 residual and the
+    later ones, including the final check, the FP64 residual."""
     from oracle import esdirk
     from oracle import linearize as L
     m, q, ph = cases.workload_vortex2d(8, 2)
@@ -114,8 +119,10 @@ def test_esdirk3_stage_matches_oracle(built, mode, jv_dtype):
     qi = qns.clone()
     R2 = torch.empty_like(qns)
     st = ctx.esdirk_stage(tab.A, 2, 0.05, qns, [R1, R2, None, None], qi, tol=1e-8, dtau_init=0.05,
-                          dtau_max=10.0, mode=mode, jv_dtype=jv_dtype)
+                          dtau_max=10.0, mode=mode, jv_dtype=jv_dtype, f32_above=f32_above)
     assert st["converged"] and st["norm_final"] <= 1e-8 * st["norm0"]
+    assert st["f64_evaluations"] >= 1
+    assert (st["f32_evaluations"] > 0) == (f32_above > 0)
     qg = ctx.unpack(qi).cpu().numpy()
     dq = np.abs(qo.numpy() - q).max()
     assert np.abs(qg - qo.numpy()).max() <= 1e-6 * dq
