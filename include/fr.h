@@ -290,6 +290,8 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
  * flags; entries outside [0, 256] or unknown flag bits give FR_ERR_INVALID. */
 #define FR_TUNE_MULTI_LAUNCH 1  /* one persistent launch over all degree buckets */
 #define FR_TUNE_GRAPHS 2        /* Arnoldi products replayed from a CUDA graph */
+#define FR_TUNE_DIAG_METRICS 4  /* 3D meshes of axis-aligned affine elements:
+                                   kernels that skip the zero metric terms   */
 fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
 fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
 fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);

@@ -425,12 +425,31 @@ static fr_status create_impl(const fr_mesh_desc* m, const fr_physics* ph, const 
   if (c->affine) {
     // one set of constants per element serves both views (vol uses the first NKV)
     std::vector<double> g((size_t)E * NKF);
+    bool diag = nd == 3;
     for (int e = 0; e < E; ++e) {
       // constant metrics: evaluate at degree 0 would be degenerate; use p = 1, first point
       std::vector<double> v1((size_t)NK * ipow(2, nd)), f1((size_t)nf * NK * ipow(2, nd - 1));
       element_metrics(c, e, 1, v1.data(), f1.data());
+      // axis-aligned box: the off-diagonal metric terms are rounding noise of
+      // the metric evaluation; they are set to exact zeros
+      double smax = 0.0, offmax = 0.0;
+      for (int d = 0; d < nd; ++d)
+        for (int j = 0; j < nd; ++j) {
+          const double x = std::fabs(v1[(size_t)(d * nd + j) * ipow(2, nd)]);
+          smax = std::max(smax, x);
+          if (d != j) offmax = std::max(offmax, x);
+        }
+      if (offmax <= 1e-13 * smax) {
+        for (int d = 0; d < nd; ++d)
+          for (int j = 0; j < nd; ++j)
+            if (d != j) v1[(size_t)(d * nd + j) * ipow(2, nd)] = 0.0;
+      } else {
+        diag = false;
+      }
       derive(v1.data(), ipow(2, nd), g.data() + (size_t)e * NKF, 1, true);
     }
+    c->diag_mesh = diag;
+    c->diag = c->diag_mesh && c->use_diag;
     FR_TRY(upload_cast(g, &c->d_gaff64));
     FR_TRY(upload_cast(g, &c->d_gaff32));
   } else {

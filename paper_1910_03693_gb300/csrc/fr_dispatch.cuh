@@ -119,11 +119,11 @@ static void ensure_smem(KernelT kern, size_t smem, size_t& configured) {
   }
 }
 
-template <typename T, int ND, int P, bool VISC>
+template <typename T, int ND, int P, bool VISC, bool DIAG = false>
 static void launch_trace_p(const TraceArgs<T>& a, int epb, cudaStream_t s) {
   constexpr int NV = ND + 2, NF = 2 * ND;
   const size_t smem = (size_t)epb * (NV * Shape<ND, P>::NSP + NF * NV * Shape<ND, P>::NFP) * sizeof(T);
-  auto kern = trace_kernel<T, ND, P, VISC>;
+  auto kern = trace_kernel<T, ND, P, VISC, DIAG>;
   static size_t configured = 0;
   ensure_smem(kern, smem, configured);
   kern<<<nblocks(a.count, epb), epb * Shape<ND, P>::NSP, smem, s>>>(a, epb);
@@ -146,14 +146,14 @@ static TraceArgs<T> trace_args(fr_ctx* c, const Bucket& b, const T* q, T* trace)
 }
 
 // traces of every bucket: one launch per bucket, or one multi-bucket launch
-template <typename T, int ND, bool VISC>
+template <typename T, int ND, bool VISC, bool DIAG = false>
 static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
   double nb = 0.0, nfl = 0.0;
   for (const auto& b : c->buckets) {
     const int P = b.p + 1;
     nb += (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
-    nfl += (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC);
+    nfl += (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC, DIAG);
   }
   const char* name = sizeof(T) == 8 ? "trace_f64" : "trace_f32";
   int n_items = 0;
@@ -171,7 +171,7 @@ static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
     }
     m.items = items;
     m.n_items = n_items;
-    auto kern = trace_multi_kernel<T, ND, VISC>;
+    auto kern = trace_multi_kernel<T, ND, VISC, DIAG>;
     static size_t configured = 0;
     ensure_smem(kern, smem, configured);
     int per_sm = 1;
@@ -184,24 +184,24 @@ static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
     const TraceArgs<T> a = trace_args<T, ND, VISC>(c, b, q, trace);
     const int P = b.p + 1, e = epb_for(c, prec, 0, P);
     const double nbb = (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
-    const double nfb = (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC);
+    const double nfb = (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC, DIAG);
     FR_LAUNCH_BF(c, name, s, nbb, nfb, {
       switch (P) {
-        case 2: launch_trace_p<T, ND, 2, VISC>(a, e, s); break;
-        case 3: launch_trace_p<T, ND, 3, VISC>(a, e, s); break;
-        case 4: launch_trace_p<T, ND, 4, VISC>(a, e, s); break;
-        case 5: launch_trace_p<T, ND, 5, VISC>(a, e, s); break;
-        case 6: launch_trace_p<T, ND, 6, VISC>(a, e, s); break;
+        case 2: launch_trace_p<T, ND, 2, VISC, DIAG>(a, e, s); break;
+        case 3: launch_trace_p<T, ND, 3, VISC, DIAG>(a, e, s); break;
+        case 4: launch_trace_p<T, ND, 4, VISC, DIAG>(a, e, s); break;
+        case 5: launch_trace_p<T, ND, 5, VISC, DIAG>(a, e, s); break;
+        case 6: launch_trace_p<T, ND, 6, VISC, DIAG>(a, e, s); break;
       }
     });
   }
 }
 
-template <typename T, int ND, int P, bool VISC, int MODE>
+template <typename T, int ND, int P, bool VISC, int MODE, bool DIAG = false>
 static void launch_vol_p(const VolArgs<T>& a, int epb, cudaStream_t s) {
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
   const size_t smem = (size_t)epb * (ND + 2) * (1 + ND) * Shape<ND, P>::NSP * sizeof(S);
-  auto kern = vol_kernel<T, ND, P, VISC, MODE>;
+  auto kern = vol_kernel<T, ND, P, VISC, MODE, DIAG>;
   static size_t configured = 0;
   ensure_smem(kern, smem, configured);
   kern<<<nblocks(a.count, epb), epb * Shape<ND, P>::NSP, smem, s>>>(a, epb);
@@ -228,7 +228,7 @@ static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T
 }
 
 // volume kernel of every bucket: one launch per bucket, or one multi-bucket launch
-template <typename T, int ND, bool VISC, int MODE>
+template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
 static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t s) {
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
   const int prec = sizeof(T) == 8 ? 0 : 1, kind = MODE == 1 ? 2 : 1;
@@ -238,7 +238,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
   for (const auto& b : c->buckets) {
     const int P = b.p + 1;
     nb += (double)b.count * (ND + 2) * nsp_of(ND, P) * sizeof(T) * (MODE == 1 ? 3 : 2);
-    nfl += MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC);
+    nfl += MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC, DIAG);
   }
   int n_items = 0;
   const WorkItem* items = (c->multi_launch && c->buckets.size() > 1) ? work_items(c, prec, kind, &n_items) : nullptr;
@@ -255,7 +255,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     }
     m.items = items;
     m.n_items = n_items;
-    auto kern = vol_multi_kernel<T, ND, VISC, MODE>;
+    auto kern = vol_multi_kernel<T, ND, VISC, MODE, DIAG>;
     static size_t configured = 0;
     ensure_smem(kern, smem, configured);
     int per_sm = 1;
@@ -268,14 +268,14 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     const VolArgs<T> a = vol_args<T>(c, b, q, v, out);
     const int P = b.p + 1, e = epb_for(c, prec, kind, P);
     const double nbb = (double)b.count * (ND + 2) * nsp_of(ND, P) * sizeof(T) * (MODE == 1 ? 3 : 2);
-    const double nfb = MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC);
+    const double nfb = MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC, DIAG);
     FR_LAUNCH_BF(c, name, s, nbb, nfb, {
       switch (P) {
-        case 2: launch_vol_p<T, ND, 2, VISC, MODE>(a, e, s); break;
-        case 3: launch_vol_p<T, ND, 3, VISC, MODE>(a, e, s); break;
-        case 4: launch_vol_p<T, ND, 4, VISC, MODE>(a, e, s); break;
-        case 5: launch_vol_p<T, ND, 5, VISC, MODE>(a, e, s); break;
-        case 6: launch_vol_p<T, ND, 6, VISC, MODE>(a, e, s); break;
+        case 2: launch_vol_p<T, ND, 2, VISC, MODE, DIAG>(a, e, s); break;
+        case 3: launch_vol_p<T, ND, 3, VISC, MODE, DIAG>(a, e, s); break;
+        case 4: launch_vol_p<T, ND, 4, VISC, MODE, DIAG>(a, e, s); break;
+        case 5: launch_vol_p<T, ND, 5, VISC, MODE, DIAG>(a, e, s); break;
+        case 6: launch_vol_p<T, ND, 6, VISC, MODE, DIAG>(a, e, s); break;
       }
     });
   }
@@ -333,24 +333,24 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
   }
 }
 
-template <typename T, int ND, bool VISC>
+template <typename T, int ND, bool VISC, bool DIAG = false>
 static void residual_impl(fr_ctx* c, const T* q, T* R, cudaStream_t s) {
   T* trq = (T*)c->d_trace_q;
-  launch_traces<T, ND, VISC>(c, q, trq, s);
+  launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
   launch_faces<T, ND, VISC, 0>(c, trq, nullptr, s);
-  launch_vols<T, ND, VISC, 0>(c, q, nullptr, R, s);
+  launch_vols<T, ND, VISC, 0, DIAG>(c, q, nullptr, R, s);
 }
 
 // JVP; with q_traces_ready the traces of q in d_trace_q are reused (q is
 // fixed during one GMRES solve)
-template <typename T, int ND, bool VISC>
+template <typename T, int ND, bool VISC, bool DIAG = false>
 static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready = false) {
   T* trq = (T*)c->d_trace_q;
   T* trv = (T*)c->d_trace_v;
-  if (!q_traces_ready) launch_traces<T, ND, VISC>(c, q, trq, s);
-  launch_traces<T, ND, VISC>(c, v, trv, s);
+  if (!q_traces_ready) launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
+  launch_traces<T, ND, VISC, DIAG>(c, v, trv, s);
   launch_faces<T, ND, VISC, 1>(c, trq, trv, s);
-  launch_vols<T, ND, VISC, 1>(c, q, v, Jv, s);
+  launch_vols<T, ND, VISC, 1, DIAG>(c, q, v, Jv, s);
 }
 
 
@@ -498,7 +498,7 @@ static float time_best(int reps, cudaStream_t s, F&& f) {
   return best;
 }
 
-template <typename T, int ND, bool VISC>
+template <typename T, int ND, bool VISC, bool DIAG = false>
 static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStream_t s) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
   T* trq = (T*)c->d_trace_q;
@@ -507,8 +507,8 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
   c->multi_launch = false;
   for (int kind = 0; kind < 3; ++kind) {
     // valid face data for the volume kernels
-    if (kind == 1) residual_impl<T, ND, VISC>(c, q, scratch, s);
-    if (kind == 2) jvp_impl<T, ND, VISC>(c, q, q, scratch, s);
+    if (kind == 1) residual_impl<T, ND, VISC, DIAG>(c, q, scratch, s);
+    if (kind == 2) jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s);
     for (const auto& b : c->buckets) {
       const int P = b.p + 1, nsp = nsp_of(ND, P);
       std::vector<int> cand;
@@ -523,11 +523,11 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
           const TraceArgs<T> a = trace_args<T, ND, VISC>(c, b, q, trq);
           ms = time_best(reps, s, [&] {
             switch (P) {
-              case 2: launch_trace_p<T, ND, 2, VISC>(a, e, s); break;
-              case 3: launch_trace_p<T, ND, 3, VISC>(a, e, s); break;
-              case 4: launch_trace_p<T, ND, 4, VISC>(a, e, s); break;
-              case 5: launch_trace_p<T, ND, 5, VISC>(a, e, s); break;
-              case 6: launch_trace_p<T, ND, 6, VISC>(a, e, s); break;
+              case 2: launch_trace_p<T, ND, 2, VISC, DIAG>(a, e, s); break;
+              case 3: launch_trace_p<T, ND, 3, VISC, DIAG>(a, e, s); break;
+              case 4: launch_trace_p<T, ND, 4, VISC, DIAG>(a, e, s); break;
+              case 5: launch_trace_p<T, ND, 5, VISC, DIAG>(a, e, s); break;
+              case 6: launch_trace_p<T, ND, 6, VISC, DIAG>(a, e, s); break;
             }
           });
         } else {
@@ -535,19 +535,19 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
           ms = time_best(reps, s, [&] {
             if (kind == 1) {
               switch (P) {
-                case 2: launch_vol_p<T, ND, 2, VISC, 0>(a, e, s); break;
-                case 3: launch_vol_p<T, ND, 3, VISC, 0>(a, e, s); break;
-                case 4: launch_vol_p<T, ND, 4, VISC, 0>(a, e, s); break;
-                case 5: launch_vol_p<T, ND, 5, VISC, 0>(a, e, s); break;
-                case 6: launch_vol_p<T, ND, 6, VISC, 0>(a, e, s); break;
+                case 2: launch_vol_p<T, ND, 2, VISC, 0, DIAG>(a, e, s); break;
+                case 3: launch_vol_p<T, ND, 3, VISC, 0, DIAG>(a, e, s); break;
+                case 4: launch_vol_p<T, ND, 4, VISC, 0, DIAG>(a, e, s); break;
+                case 5: launch_vol_p<T, ND, 5, VISC, 0, DIAG>(a, e, s); break;
+                case 6: launch_vol_p<T, ND, 6, VISC, 0, DIAG>(a, e, s); break;
               }
             } else {
               switch (P) {
-                case 2: launch_vol_p<T, ND, 2, VISC, 1>(a, e, s); break;
-                case 3: launch_vol_p<T, ND, 3, VISC, 1>(a, e, s); break;
-                case 4: launch_vol_p<T, ND, 4, VISC, 1>(a, e, s); break;
-                case 5: launch_vol_p<T, ND, 5, VISC, 1>(a, e, s); break;
-                case 6: launch_vol_p<T, ND, 6, VISC, 1>(a, e, s); break;
+                case 2: launch_vol_p<T, ND, 2, VISC, 1, DIAG>(a, e, s); break;
+                case 3: launch_vol_p<T, ND, 3, VISC, 1, DIAG>(a, e, s); break;
+                case 4: launch_vol_p<T, ND, 4, VISC, 1, DIAG>(a, e, s); break;
+                case 5: launch_vol_p<T, ND, 5, VISC, 1, DIAG>(a, e, s); break;
+                case 6: launch_vol_p<T, ND, 6, VISC, 1, DIAG>(a, e, s); break;
               }
             }
           });
@@ -565,44 +565,35 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
   // one launch per bucket vs one multi-bucket launch, for the whole JVP
   if (c->buckets.size() > 1) {
     c->multi_launch = false;
-    const float t_sep = time_best(reps, s, [&] { jvp_impl<T, ND, VISC>(c, q, q, scratch, s); });
+    const float t_sep = time_best(reps, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });
     c->multi_launch = true;
-    const float t_multi = time_best(reps, s, [&] { jvp_impl<T, ND, VISC>(c, q, q, scratch, s); });
+    const float t_multi = time_best(reps, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });
     c->multi_launch = t_multi <= t_sep;
   } else {
     c->multi_launch = multi_saved;
   }
 }
 
-template <typename T>
-static fr_status run_op(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s) {
+// One operation for one (dimension, viscosity, metric) configuration.
+template <typename T, int ND, bool VISC, bool DIAG>
+static void run_op_cfg(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s) {
   const T* qq = (const T*)q;
   const T* vv = (const T*)v;
   T* oo = (T*)out;
-  if (op == 2 && (!c->d_fbar || !c->d_trbar)) {
-    if (!c->d_fbar && cudaMalloc(&c->d_fbar, sizeof(double) * c->fout_cap) != cudaSuccess) {
-      set_error("fr_vjp: workspace allocation failed");
-      return FR_ERR_NOMEM;
-    }
-    if (!c->d_trbar && cudaMalloc(&c->d_trbar, sizeof(double) * c->trace_cap) != cudaSuccess) {
-      set_error("fr_vjp: workspace allocation failed");
-      return FR_ERR_NOMEM;
-    }
-  }
-#define FR_OPS(ND, VISC)                                                       \
-  if (op == 0) residual_impl<T, ND, VISC>(c, qq, oo, s);                       \
-  else if (op == 1) jvp_impl<T, ND, VISC>(c, qq, vv, oo, s);                   \
-  else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);                   \
-  else if (op == 3) { launch_traces<T, ND, VISC>(c, qq, (T*)c->d_trace_q, s); } \
-  else if (op == 5) autotune_impl<T, ND, VISC>(c, qq, oo, 3, s);              \
-  else jvp_impl<T, ND, VISC>(c, qq, vv, oo, s, true);
-  if (c->nd == 2) {
-    if (c->visc) { FR_OPS(2, true) } else { FR_OPS(2, false) }
-  } else {
-    if (c->visc) { FR_OPS(3, true) } else { FR_OPS(3, false) }
-  }
-#undef FR_OPS
-  return cuda_check(cudaGetLastError(), "FR kernel launch");
+  if (op == 0) residual_impl<T, ND, VISC, DIAG>(c, qq, oo, s);
+  else if (op == 1) jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, oo, s);
+  else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);
+  else if (op == 3) launch_traces<T, ND, VISC, DIAG>(c, qq, (T*)c->d_trace_q, s);
+  else if (op == 5) autotune_impl<T, ND, VISC, DIAG>(c, qq, oo, 3, s);
+  else jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, oo, s, true);
 }
+
+// The instantiations live in one translation unit per (precision, dimension,
+// metric) so that they compile in parallel.
+#define FR_RUN_CFG(NAME, T, ND, DIAG)                                                             \
+  void NAME(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s) {        \
+    if (c->visc) run_op_cfg<T, ND, true, DIAG>(c, op, q, v, out, s);                           \
+    else run_op_cfg<T, ND, false, DIAG>(c, op, q, v, out, s);                                  \
+  }
 
 }  // namespace frgb

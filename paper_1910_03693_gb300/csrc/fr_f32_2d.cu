@@ -1,0 +1,6 @@
+// F32 kernels of the residual, JVP and VJP: 2D.
+#include "fr_dispatch.cuh"
+
+namespace frgb {
+FR_RUN_CFG(run_f32_2d, float, 2, false)
+}  // namespace frgb

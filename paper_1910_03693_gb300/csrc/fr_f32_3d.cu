@@ -1,0 +1,6 @@
+// F32 kernels of the residual, JVP and VJP: 3D.
+#include "fr_dispatch.cuh"
+
+namespace frgb {
+FR_RUN_CFG(run_f32_3d, float, 3, false)
+}  // namespace frgb

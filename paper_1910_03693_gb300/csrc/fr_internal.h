@@ -103,6 +103,8 @@ struct PhysParams {
 struct fr_ctx {
   int nd = 0, nv = 0, nf = 0, E = 0, geom_order = 1, p_min = 1, p_max = 1;
   bool affine = false, visc = false;
+  bool diag_mesh = false;   // 3D, affine, every metric diagonal (axis-aligned boxes)
+  bool diag = false;        // diag_mesh and the diagonal-metric kernels enabled
   frgb::PhysParams phys{};
   int device = 0;
   // host mesh
@@ -166,6 +168,7 @@ struct fr_ctx {
   std::vector<frgb::TimerRec> graph_timers[2];  // event pairs inside each graph
   bool graph_timers_live[2] = {false, false};   // a replay's timers are not yet accumulated
   bool use_graphs = true;
+  bool use_diag = true;
   cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
   bool jvp_graph_ok = true;
   int* d_jidx = nullptr;

@@ -121,7 +121,9 @@ struct VolCfg {
 // from the face metric terms.
 // Elements i0 .. i0+epb-1 of the bucket described by ``a``; every thread of the
 // block reaches the barriers (threads beyond epb*NSP only help to synchronise).
-template <typename T, int ND, int P, bool VISC>
+// DIAG: every metric S is diagonal (axis-aligned affine elements): only S[d][d]
+// is read and the metric products reduce to one multiply per component.
+template <typename T, int ND, int P, bool VISC, bool DIAG = false>
 __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, int epb, unsigned char* smem_raw) {
   using Sh = Shape<ND, P>;
   constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
@@ -165,7 +167,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
 #pragma unroll
     for (int dd = 0; dd < ND; ++dd)
 #pragma unroll
-      for (int j = 0; j < ND; ++j) Sf[dd][j] = geo_face(a.geo, e, f, dd * ND + j, t);
+      for (int j = 0; j < ND; ++j) Sf[dd][j] = (DIAG && dd != j) ? T(0) : geo_face(a.geo, e, f, dd * ND + j, t);
     const T Jinv = geo_face(a.geo, e, f, ND * ND + 1, t);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -188,18 +190,22 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
         T g = T(0);
+        if (DIAG) {
+          g = Sf[j][j] * dq[j];
+        } else {
 #pragma unroll
-        for (int dd = 0; dd < ND; ++dd) g += Sf[dd][j] * dq[dd];
+          for (int dd = 0; dd < ND; ++dd) g += Sf[dd][j] * dq[dd];
+        }
         out[(f * a.nvt + NV + j * NV + v) * NFP + t] = g * Jinv;
       }
     }
   }
 }
 
-template <typename T, int ND, int P, bool VISC>
+template <typename T, int ND, int P, bool VISC, bool DIAG>
 __global__ void __launch_bounds__(256) trace_kernel(TraceArgs<T> a, int epb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  trace_body<T, ND, P, VISC>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
+  trace_body<T, ND, P, VISC, DIAG>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
 }
 
 // One tile of elements of one bucket: the unit of the multi-bucket launch.
@@ -221,18 +227,18 @@ struct TraceMulti {
 
 // Every bucket in one persistent launch: CTAs walk the cost-ordered work
 // table with a grid stride and dispatch on the tile's degree.
-template <typename T, int ND, bool VISC>
+template <typename T, int ND, bool VISC, bool DIAG>
 __global__ void __launch_bounds__(256) trace_multi_kernel(TraceMulti<T> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
     const WorkItem it = m.items[w];
     const int b = it.bucket;
     switch (m.P[b]) {
-      case 2: trace_body<T, ND, 2, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 3: trace_body<T, ND, 3, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 4: trace_body<T, ND, 4, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 5: trace_body<T, ND, 5, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 6: trace_body<T, ND, 6, VISC>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 2: trace_body<T, ND, 2, VISC, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 3: trace_body<T, ND, 3, VISC, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 4: trace_body<T, ND, 4, VISC, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 5: trace_body<T, ND, 5, VISC, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 6: trace_body<T, ND, 6, VISC, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
     }
     __syncthreads();
   }
@@ -564,7 +570,7 @@ struct VolArgs {
 };
 
 
-template <typename T, int ND, int P, bool VISC, int MODE>
+template <typename T, int ND, int P, bool VISC, int MODE, bool DIAG = false>
 __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int epb, unsigned char* smem_raw) {
   using Sh = Shape<ND, P>;
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
@@ -603,7 +609,7 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
 #pragma unroll
     for (int d = 0; d < ND; ++d)
 #pragma unroll
-      for (int j = 0; j < ND; ++j) Sm[d][j] = geo_vol(a.geo, e, d * ND + j, sp);
+      for (int j = 0; j < ND; ++j) Sm[d][j] = (DIAG && d != j) ? T(0) : geo_vol(a.geo, e, d * ND + j, sp);
     Jinv = geo_vol(a.geo, e, ND * ND + 1, sp);
 
     S f[ND][NV];
@@ -635,10 +641,14 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
       for (int j = 0; j < ND; ++j)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          S acc = szero<S>();
+          if (DIAG) {
+            G[j][v] = (Sm[j][j] * Jinv) * gref[j][v];
+          } else {
+            S acc = szero<S>();
 #pragma unroll
-          for (int d = 0; d < ND; ++d) acc = acc + Sm[d][j] * gref[d][v];
-          G[j][v] = acc * Jinv;
+            for (int d = 0; d < ND; ++d) acc = acc + Sm[d][j] * gref[d][v];
+            G[j][v] = acc * Jinv;
+          }
         }
       S fv[ND][NV];
       flux_viscous<ND>(q, G, a.gamma, a.mu, a.kappa, fv);
@@ -652,10 +662,14 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
     for (int d = 0; d < ND; ++d)
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        S acc = szero<S>();
+        if (DIAG) {
+          sF[(d * NV + v) * NSP + sp] = Sm[d][d] * f[d][v];
+        } else {
+          S acc = szero<S>();
 #pragma unroll
-        for (int j = 0; j < ND; ++j) acc = acc + Sm[d][j] * f[j][v];
-        sF[(d * NV + v) * NSP + sp] = acc;
+          for (int j = 0; j < ND; ++j) acc = acc + Sm[d][j] * f[j][v];
+          sF[(d * NV + v) * NSP + sp] = acc;
+        }
       }
   }
   __syncthreads();
@@ -693,10 +707,10 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
   }
 }
 
-template <typename T, int ND, int P, bool VISC, int MODE>
+template <typename T, int ND, int P, bool VISC, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) vol_kernel(VolArgs<T> a, int epb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  vol_body<T, ND, P, VISC, MODE>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
+  vol_body<T, ND, P, VISC, MODE, DIAG>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
 }
 
 template <typename T>
@@ -708,18 +722,18 @@ struct VolMulti {
   int n_items;
 };
 
-template <typename T, int ND, bool VISC, int MODE>
+template <typename T, int ND, bool VISC, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) vol_multi_kernel(VolMulti<T> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
     const WorkItem it = m.items[w];
     const int b = it.bucket;
     switch (m.P[b]) {
-      case 2: vol_body<T, ND, 2, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 3: vol_body<T, ND, 3, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 4: vol_body<T, ND, 4, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 5: vol_body<T, ND, 5, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
-      case 6: vol_body<T, ND, 6, VISC, MODE>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 2: vol_body<T, ND, 2, VISC, MODE, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 3: vol_body<T, ND, 3, VISC, MODE, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 4: vol_body<T, ND, 4, VISC, MODE, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 5: vol_body<T, ND, 5, VISC, MODE, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
+      case 6: vol_body<T, ND, 6, VISC, MODE, DIAG>(m.b[b], it.first, m.epb[b], smem_raw); break;
     }
     __syncthreads();
   }

@@ -138,24 +138,26 @@ namespace frgb {
 // Algorithmic operation counts of the FR operators as formulated (FMA = 2):
 // per solution point of the volume residual, per face point of the traces,
 // per mortar point of the common flux.
-inline double flops_volume(int nd, int P, bool visc) {
+// diag: axis-aligned affine elements, whose metric products are one multiply
+// per component.
+inline double flops_volume(int nd, int P, bool visc, bool diag = false) {
   const int nv = nd + 2;
   double f = 1 + nd + 2 * nd + 3 + nd * (nd + 3);                  // inviscid flux
-  f += nd * nv * 2 * nd;                                             // transformed flux
+  f += diag ? nd * nv : nd * nv * 2 * nd;                            // transformed flux
   f += nd * nv * (2 * P + 4);                                        // divergence + correction
   f += 2 * nv;                                                       // -div / |J|
   if (visc) {
     f += nd * nv * (2 * P + 4);                                      // corrected gradient
-    f += nd * nv * (2 * nd + 1);                                     // physical gradient
+    f += diag ? nd + nd * nv : nd * nv * (2 * nd + 1);               // physical gradient
     f += 2 + nd + 3 * nd * nd + 3 * nd + 2 * nd * nd + 2 * nd + (nd - 1) + 3 * nd * nd + 2 * nd * nd + 2 * nd;
     f += nd * nv;                                                    // f_inv - f_v
   }
   return f;
 }
-inline double flops_trace(int nd, int P, bool visc) {
+inline double flops_trace(int nd, int P, bool visc, bool diag = false) {
   const int nv = nd + 2;
   double f = nv * 2 * P;
-  if (visc) f += nv * 2 * P * nd + nd * nv * (2 * nd + 1) + 1;
+  if (visc) f += nv * 2 * P * nd + (diag ? 2 * nd * nv : nd * nv * (2 * nd + 1));
   return f;
 }
 inline double flops_face(int nd, bool visc) {
