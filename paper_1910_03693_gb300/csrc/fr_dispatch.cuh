@@ -208,11 +208,12 @@ static void launch_vol_p(const VolArgs<T>& a, int epb, cudaStream_t s) {
 }
 
 template <typename T>
-static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* out) {
+static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* out, double* out_neg64 = nullptr) {
   VolArgs<T> a;
   a.q = q;
   a.v = v;
   a.out = out;
+  a.out_neg64 = out_neg64;
   a.fout = (const T*)c->d_fout;
   a.slot_elem = c->d_slot_elem;
   a.basis = basis_ptr<T>(c);
@@ -229,7 +230,7 @@ static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T
 
 // volume kernel of every bucket: one launch per bucket, or one multi-bucket launch
 template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
-static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t s) {
+static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t s, double* out_neg64 = nullptr) {
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
   const int prec = sizeof(T) == 8 ? 0 : 1, kind = MODE == 1 ? 2 : 1;
   const char* name = MODE == 1 ? (sizeof(T) == 8 ? "vol_jvp_f64" : "vol_jvp_f32")
@@ -248,7 +249,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     for (size_t i = 0; i < c->buckets.size(); ++i) {
       const Bucket& b = c->buckets[i];
       const int P = b.p + 1, e = epb_for(c, prec, kind, P);
-      m.b[i] = vol_args<T>(c, b, q, v, out);
+      m.b[i] = vol_args<T>(c, b, q, v, out, out_neg64);
       m.P[i] = P;
       m.epb[i] = e;
       smem = std::max(smem, (size_t)e * (ND + 2) * (1 + ND) * nsp_of(ND, P) * sizeof(S));
@@ -265,7 +266,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     return;
   }
   for (const auto& b : c->buckets) {
-    const VolArgs<T> a = vol_args<T>(c, b, q, v, out);
+    const VolArgs<T> a = vol_args<T>(c, b, q, v, out, out_neg64);
     const int P = b.p + 1, e = epb_for(c, prec, kind, P);
     const double nbb = (double)b.count * (ND + 2) * nsp_of(ND, P) * sizeof(T) * (MODE == 1 ? 3 : 2);
     const double nfb = MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC, DIAG);
@@ -344,13 +345,14 @@ static void residual_impl(fr_ctx* c, const T* q, T* R, cudaStream_t s) {
 // JVP; with q_traces_ready the traces of q in d_trace_q are reused (q is
 // fixed during one GMRES solve)
 template <typename T, int ND, bool VISC, bool DIAG = false>
-static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready = false) {
+static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready = false,
+                     double* neg64 = nullptr) {
   T* trq = (T*)c->d_trace_q;
   T* trv = (T*)c->d_trace_v;
   if (!q_traces_ready) launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
   launch_traces<T, ND, VISC, DIAG>(c, v, trv, s);
   launch_faces<T, ND, VISC, 1>(c, trq, trv, s);
-  launch_vols<T, ND, VISC, 1, DIAG>(c, q, v, Jv, s);
+  launch_vols<T, ND, VISC, 1, DIAG>(c, q, v, Jv, s, neg64);
 }
 
 
@@ -585,6 +587,7 @@ static void run_op_cfg(fr_ctx* c, int op, const void* q, const void* v, void* ou
   else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);
   else if (op == 3) launch_traces<T, ND, VISC, DIAG>(c, qq, (T*)c->d_trace_q, s);
   else if (op == 5) autotune_impl<T, ND, VISC, DIAG>(c, qq, oo, 3, s);
+  else if (op == 6) jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, nullptr, s, true, (double*)out);
   else jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, oo, s, true);
 }
 

@@ -560,6 +560,7 @@ struct VolArgs {
   const T* q;
   const T* v;          // tangent (JVP)
   T* out;
+  double* out_neg64;   // JVP only, optional: -J v written in FP64 instead of out
   const T* fout;
   const int32_t* slot_elem;
   const BasisTab<T>* basis;
@@ -703,7 +704,10 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     S r = (T(0) - div[v]) * Jinv;
-    a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
+    if (MODE == 1 && a.out_neg64)
+      a.out_neg64[a.state_base + (i * NV + v) * NSP + sp] = -(double)tangent(r);
+    else
+      a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
   }
 }
 

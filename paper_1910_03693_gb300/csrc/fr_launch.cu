@@ -29,6 +29,11 @@ fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv,
   return prec == FR_F64 ? run_op_f64(c, 4, q, v, Jv, s) : run_op_f32(c, 4, q, v, Jv, s);
 }
 
+fr_status launch_jvp_prepared_neg64(fr_ctx* c, const void* q, const void* v, double* w, fr_prec prec,
+                                    cudaStream_t s) {
+  return prec == FR_F64 ? run_op_f64(c, 6, q, v, w, s) : run_op_f32(c, 6, q, v, w, s);
+}
+
 fr_status launch_vjp(fr_ctx* c, const void* q, const void* w, void* JTw, fr_prec prec, cudaStream_t s) {
   return prec == FR_F64 ? run_op_f64(c, 2, q, w, JTw, s) : run_op_f32(c, 2, q, w, JTw, s);
 }

@@ -18,7 +18,8 @@ void vcast_f32_f64(fr_ctx* c, const float* x, double* y, int64_t n, cudaStream_t
 
 // op 0: out = R(q); op 1: out = J(q) v (exact); op 2: out = J(q)^T v;
 // op 3: traces of q only (prepares op 4); op 4: J(q) v reusing those traces;
-// op 5: autotune the launch configuration on q (out: scratch of n_dof).
+// op 5: autotune the launch configuration on q (out: scratch of n_dof);
+// op 6: as op 4, writing -J(q) v in FP64 into out.
 fr_status run_op_f64(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 fr_status run_op_f32(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 
@@ -33,6 +34,9 @@ void run_f32_3d_diag(fr_ctx* c, int op, const void* q, const void* v, void* out,
 
 fr_status launch_jvp_prepare(fr_ctx* c, const void* q, fr_prec prec, cudaStream_t s);
 fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec, cudaStream_t s);
+// Same, writing w = -J(q) v in FP64 (the Arnoldi vector), in either precision.
+fr_status launch_jvp_prepared_neg64(fr_ctx* c, const void* q, const void* v, double* w, fr_prec prec,
+                                    cudaStream_t s);
 
 // Jv = (R(q + eps v) - R0) / eps in FP64; R0 = R(q) is computed when null.
 fr_status launch_fd_jv(fr_ctx* c, const double* q, const double* v, double* Jv, double eps,

@@ -20,19 +20,22 @@ constexpr int kMaxK = 64;           // most vectors in one multi-dot (restart le
 
 // reduction scratch (doubles): per-block partials [kRedBlocks][kMaxK], then the
 // reduced values H1 (first Gram-Schmidt pass, ||w||^2 after the dots), H2
-// (second pass), N (||w||^2 after an update), Y (the GMRES coefficients) and
-// one slot holding the arrival counter of the grid reductions
+// (second pass), N (||w||^2 after an update), Y (the GMRES coefficients), S
+// (the scales of the stored Krylov columns) and one slot holding the arrival
+// counter of the grid reductions
 constexpr int64_t kOutH1 = (int64_t)kRedBlocks * kMaxK;
 constexpr int64_t kOutH2 = kOutH1 + kMaxK;
 constexpr int64_t kOutN = kOutH2 + kMaxK;
 constexpr int64_t kOutY = kOutN + kMaxK;
-constexpr int64_t kTicket = kOutY + kMaxK;
+constexpr int64_t kOutS = kOutY + kMaxK;    // scales of the stored Krylov columns
+constexpr int64_t kTicket = kOutS + kMaxK;
 
 static fr_status ensure_red(fr_ctx* c) {
   if (c->d_red) return FR_OK;
   c->red_cap = kTicket + 1;
   if (cudaMalloc(&c->d_red, sizeof(double) * c->red_cap) != cudaSuccess) return FR_ERR_NOMEM;
   if (cudaMemset(c->d_red, 0, sizeof(double) * c->red_cap) != cudaSuccess) return FR_ERR_CUDA;
+  // host mirror: H1, H2, N (read back), then the column scales (uploaded)
   if (cudaMallocHost(&c->h_red, sizeof(double) * 4 * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
   return FR_OK;
 }
@@ -169,15 +172,48 @@ struct Unroll {
   static constexpr int CH = KC < 8 ? KC : 8;   // columns per load batch
 };
 
+// Slot q of the vector w as FP64 values: w is FP64, or the FP32 output of the
+// JVP (converted); NEG negates it (w = -J v), which costs nothing in the FMAs.
+template <bool VEC, typename WT, bool NEG>
+struct WSlots {
+  __device__ static void load(const WT* p, int64_t q, int64_t nw, int64_t n, double (&x)[2]) {
+    if (q < nw) {
+      if (VEC) {
+        if constexpr (sizeof(WT) == 8) {
+          const double2 t = *reinterpret_cast<const double2*>(p + 2 * q);
+          x[0] = t.x;
+          x[1] = t.y;
+        } else {
+          const float2 t = *reinterpret_cast<const float2*>(p + 2 * q);
+          x[0] = (double)t.x;
+          x[1] = (double)t.y;
+        }
+      } else {
+        x[0] = (double)p[q];
+        x[1] = 0.0;
+      }
+    } else {
+      x[0] = (VEC && q == nw && (n & 1)) ? (double)p[2 * nw] : 0.0;
+      x[1] = 0.0;
+    }
+    if (NEG) {
+      x[0] = -x[0];
+      x[1] = -x[1];
+    }
+  }
+};
+
 // out[kk] = V[kk]^T w for kk < k, and, when with_norm, out[k] = ||w||^2.
-// V == nullptr: out[0] = ||w||^2 alone.
-template <int KC, bool VEC>
+// V == nullptr: out[0] = ||w||^2 alone.  V holds the stored (unscaled)
+// Krylov columns; the caller applies their scales to the dots.
+template <int KC, bool VEC, typename WT, bool NEG>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int k,
-                                                           const double* __restrict__ w, int64_t n,
+                                                           const WT* __restrict__ w, int64_t n,
                                                            double* __restrict__ partial, double* __restrict__ out,
                                                            unsigned* __restrict__ ticket, int with_norm) {
   constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
   using L = Slots<VEC>;
+  using LW = WSlots<VEC, WT, NEG>;
   double acc[KC + 1];
 #pragma unroll
   for (int kk = 0; kk <= KC; ++kk) acc[kk] = 0.0;
@@ -186,7 +222,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
   for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 <= last; q0 += U * stride) {
     double wv[U][2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) L::load(w, q0 + u * stride, nw, n, wv[u]);
+    for (int u = 0; u < U; ++u) LW::load(w, q0 + u * stride, nw, n, wv[u]);
     if (V) {
 #pragma unroll
       for (int c0 = 0; c0 < KC; c0 += CH) {
@@ -226,16 +262,20 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
   grid_sum<KC + 1>(o, with_norm ? k + 1 : k, partial, out, ticket);
 }
 
-// w <- w - sum_kk h[kk] V[kk]; out[0] = ||w_new||^2
-template <int KC, bool VEC>
+// w_out = w_in - sum_kk s_kk^2 raw[kk] V[kk] (the stored columns V[kk] scaled
+// by s_kk are the orthonormal basis, raw[kk] = V[kk]^T w_in); out[0] =
+// ||w_out||^2.  w_out may be w_in (in place, FP64).
+template <int KC, bool VEC, typename WT, bool NEG>
 __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __restrict__ V, int64_t ldv, int k,
-                                                              const double* __restrict__ h, double* __restrict__ w,
-                                                              int64_t n, double* __restrict__ partial,
+                                                              const double* __restrict__ raw,
+                                                              const double* __restrict__ scale, const WT* w_in,
+                                                              double* w_out, int64_t n, double* __restrict__ partial,
                                                               double* __restrict__ out, unsigned* __restrict__ ticket) {
   constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
   using L = Slots<VEC>;
+  using LW = WSlots<VEC, WT, NEG>;
   __shared__ double hs[KC];
-  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < k ? h[threadIdx.x] : 0.0;
+  if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < k ? scale[threadIdx.x] * scale[threadIdx.x] * raw[threadIdx.x] : 0.0;
   __syncthreads();
   double acc[1] = {0.0};
   const int64_t nw = n / L::W, stride = (int64_t)gridDim.x * blockDim.x;
@@ -243,7 +283,7 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
   for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 <= last; q0 += U * stride) {
     double x[U][2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) L::load(w, q0 + u * stride, nw, n, x[u]);
+    for (int u = 0; u < U; ++u) LW::load(w_in, q0 + u * stride, nw, n, x[u]);
 #pragma unroll
     for (int c0 = 0; c0 < KC; c0 += CH) {
       if (c0 < k) {
@@ -266,32 +306,29 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      L::store(w, q0 + u * stride, nw, n, x[u]);
+      L::store(w_out, q0 + u * stride, nw, n, x[u]);
       acc[0] += x[u][0] * x[u][0] + x[u][1] * x[u][1];
     }
   }
   grid_sum<1>(acc, 1, partial, out, ticket);
 }
 
-// launch KERNEL<KC, VEC> with the smallest KC >= k; VEC when every vector
-// starts on a 16-byte boundary and the column stride is even
-#define FR_KC_DISPATCH(k, vec, grid, KERNEL, ...)                                                   \
-  do {                                                                                              \
-    if (vec) {                                                                                      \
-      if ((k) <= 1) KERNEL<1, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                      \
-      else if ((k) <= 2) KERNEL<2, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                 \
-      else if ((k) <= 4) KERNEL<4, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                 \
-      else if ((k) <= 8) KERNEL<8, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                 \
-      else if ((k) <= 16) KERNEL<16, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);               \
-      else if ((k) <= 32) KERNEL<32, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);               \
-      else KERNEL<64, true><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                              \
-    } else {                                                                                        \
-      if ((k) <= 4) KERNEL<4, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                     \
-      else if ((k) <= 8) KERNEL<8, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
-      else if ((k) <= 16) KERNEL<16, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
-      else if ((k) <= 32) KERNEL<32, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
-      else KERNEL<64, false><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                             \
-    }                                                                                               \
+// launch KERNEL<KC, VEC, WT, NEG> with the smallest KC >= k; VEC when every
+// vector starts on a 16-byte boundary and the column stride is even
+#define FR_KC_CASES(k, V_, grid, KERNEL, WT, NEG, ...)                                                   \
+  do {                                                                                                  \
+    if ((k) <= 1) KERNEL<1, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                     \
+    else if ((k) <= 2) KERNEL<2, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
+    else if ((k) <= 4) KERNEL<4, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
+    else if ((k) <= 8) KERNEL<8, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
+    else if ((k) <= 16) KERNEL<16, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
+    else if ((k) <= 32) KERNEL<32, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
+    else KERNEL<64, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                             \
+  } while (0)
+#define FR_KC_DISPATCH(k, vec, grid, KERNEL, WT, NEG, ...)                                              \
+  do {                                                                                                  \
+    if (vec) FR_KC_CASES(k, true, grid, KERNEL, WT, NEG, __VA_ARGS__);                                  \
+    else FR_KC_CASES(k, false, grid, KERNEL, WT, NEG, __VA_ARGS__);                                     \
   } while (0)
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -347,7 +384,7 @@ static fr_status multidot(fr_ctx* c, const double* V, int64_t ldv, int k, const 
   const bool vec = aligned16(w) && (!V || (aligned16(V) && ldv % 2 == 0));
   const unsigned g = red_blocks(n);
   FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1),
-              FR_KC_DISPATCH(kk, vec, g, k_multidot, V, ldv, kk, w, n, part, dout, ticket_of(c), 0));
+              FR_KC_DISPATCH(kk, vec, g, k_multidot, double, false, V, ldv, kk, w, n, part, dout, ticket_of(c), 0));
   cudaMemcpyAsync(c->h_red, dout, sizeof(double) * (V ? k : 1), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "multidot");
   std::memcpy(out_host, c->h_red, sizeof(double) * (V ? k : 1));
@@ -361,130 +398,119 @@ static fr_status norm2(fr_ctx* c, const double* w, int64_t n, double* out, cudaS
   return st;
 }
 
-// x = (T) V[*jidx]
+// x = (T)(s_j V[j]) with j = *jidx and s_j = scale[j]: the orthonormal Krylov
+// vector from its stored column (FP32: the scale applied after the rounding)
 template <typename T>
 __global__ void k_gather_col(const double* __restrict__ V, int64_t ld, const int* __restrict__ jidx,
-                             T* __restrict__ x, int64_t n) {
-  const double* src = V + (int64_t)(*jidx) * ld;
+                             const double* __restrict__ scale, T* __restrict__ x, int64_t n) {
+  const int j = *jidx;
+  const double* src = V + (int64_t)j * ld;
+  const T sc = (T)scale[j];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = (T)src[i];
+    x[i] = (T)src[i] * sc;
 }
 
-// w = -J
-template <typename T>
-__global__ void k_negate(const T* __restrict__ J, double* __restrict__ w, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    w[i] = -(double)J[i];
-}
-
-// One Arnoldi matrix-vector product w = -J(q) V[j] of the exact mode as a CUDA
-// graph: gather V[j] into a fixed buffer (j read from device memory), the JVP
-// kernels (q traces prepared beforehand), negate into w.  Captured on first
-// use and again whenever q, V, w or the timing state changed; the layout and
-// the launch tuning drop it.  Returns false when graphs are off or cannot be
-// used, and the caller then launches the same kernels directly.
+// One Arnoldi product w = -J(q) v_j of the exact mode, v_j = s_j V[j]: gather
+// into a fixed buffer (j read from device memory), then the JVP kernels (q
+// traces prepared beforehand), whose volume kernel writes -J v_j in FP64
+// straight into w.  Replayed from a CUDA graph captured on first use and again
+// whenever q, V, w or the timing state changed (the layout and the launch
+// tuning drop it); launched directly when graphs are off or cannot be used.
 static void gather_col(fr_ctx* c, int pi, const double* V, int64_t ld, void* x, int64_t n, cudaStream_t s) {
   const double nb = (double)n * (8 + (pi ? 4 : 8));
-  if (pi) FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<float><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, (float*)x, n));
-  else FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<double><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, (double*)x, n));
+  const double* sc = c->d_red + kOutS;
+  if (pi) FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<float><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, sc, (float*)x, n));
+  else FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<double><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, sc, (double*)x, n));
 }
 
-static void negate_into(fr_ctx* c, int pi, const void* J, double* w, int64_t n, cudaStream_t s) {
-  const double nb = (double)n * (8 + (pi ? 4 : 8));
-  if (pi) FR_LAUNCH_B(c, "vec", s, nb, k_negate<float><<<egrid(n), 256, 0, s>>>((const float*)J, w, n));
-  else FR_LAUNCH_B(c, "vec", s, nb, k_negate<double><<<egrid(n), 256, 0, s>>>((const double*)J, w, n));
+static void release_graph_timers(fr_ctx* c, int pi) {
+  for (auto& r : c->graph_timers[pi]) {
+    c->timing.pool.push_back(r.a);
+    c->timing.pool.push_back(r.b);
+  }
+  c->graph_timers[pi].clear();
 }
 
-static bool jvp_graph_apply(fr_ctx* c, const fr_shifted_op* op, const double* V, int j, double* w,
-                            cudaStream_t s) {
-  if (!c->use_graphs || !c->jvp_graph_ok || op->mode != FR_JV_EXACT || j < 0 || j >= kMaxK) return false;
+static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double* V, int j, double* w,
+                               cudaStream_t s) {
   const int pi = op->jv_prec == FR_F32 ? 1 : 0;
   const fr_prec prec = pi ? FR_F32 : FR_F64;
   const int64_t n = c->n_dof, ld = krylov_ld(c);
   if (!c->d_jidx) {
-    if (cudaMalloc(&c->d_jidx, sizeof(int)) != cudaSuccess) return false;
-    if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return false;
+    if (cudaMalloc(&c->d_jidx, sizeof(int)) != cudaSuccess) return FR_ERR_NOMEM;
+    if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
     for (int k = 0; k < kMaxK; ++k) c->h_jidx[k] = k;
   }
   // the q the traces were prepared from: the FP32 copy for FP32 products
   const void* qptr = pi ? (const void*)vec32(c, 0) : (const void*)op->q64_dev;
   void* x = pi ? (void*)vec32(c, 1) : (void*)vec64(c, 10);
-  void* J = pi ? (void*)vec32(c, 2) : (void*)vec64(c, 3);
-  if (!qptr || !x || !J) return false;
-  const void* timed = c->timing.on ? (const void*)c : nullptr;
-  const void* key[4] = {qptr, V, w, timed};
-  const bool stale = !c->jvp_graph[pi] || !std::equal(key, key + 4, c->jvp_graph_key[pi]);
+  if (!qptr || !x) return FR_ERR_NOMEM;
   collect_graph_timers(c);
   cudaMemcpyAsync(c->d_jidx, c->h_jidx + j, sizeof(int), cudaMemcpyHostToDevice, s);
-  if (stale) {
-    if (c->jvp_graph[pi]) {
-      cudaStreamSynchronize(s);
-      cudaGraphExecDestroy(c->jvp_graph[pi]);
-      c->jvp_graph[pi] = nullptr;
-      for (auto& r : c->graph_timers[pi]) {
-        c->timing.pool.push_back(r.a);
-        c->timing.pool.push_back(r.b);
-      }
-      c->graph_timers[pi].clear();
-    }
-    // this product launched directly: every lazy allocation and kernel
-    // attribute is then in place before the capture
-    gather_col(c, pi, V, ld, x, n, s);
-    if (launch_jvp_prepared(c, qptr, x, J, prec, s) != FR_OK) return false;
-    negate_into(c, pi, J, w, n, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-    // captured on a private stream (the caller's may be the legacy default
-    // stream, which cannot be captured); replayed on the caller's stream
-    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-      c->cap_stream = nullptr;
-      c->jvp_graph_ok = false;
-      return true;
-    }
-    cudaStream_t cs = c->cap_stream;
-    const long long l0 = c->timing.launches;
-    c->timing.capture = true;
-    c->timing.mark = (int64_t)c->timing.pending.size();
-    cudaGraph_t g = nullptr;
-    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess;
-    fr_status st = FR_OK;
-    if (ok) {
-      gather_col(c, pi, V, ld, x, n, cs);
-      st = launch_jvp_prepared(c, qptr, x, J, prec, cs);
-      negate_into(c, pi, J, w, n, cs);
-      const cudaError_t ee = cudaStreamEndCapture(cs, &g);
-      ok = st == FR_OK && ee == cudaSuccess && g != nullptr &&
-           cudaGraphInstantiate(&c->jvp_graph[pi], g, 0) == cudaSuccess;
-    }
-    if (g) cudaGraphDestroy(g);
-    c->timing.capture = false;
-    // the timers recorded during the capture belong to the graph
-    auto& pend = c->timing.pending;
-    c->graph_timers[pi].assign(pend.begin() + c->timing.mark, pend.end());
-    pend.resize(c->timing.mark);
-    c->jvp_graph_nodes[pi] = (int)(c->timing.launches - l0);
-    c->timing.launches = l0;
-    if (!ok) {
+  auto direct = [&](cudaStream_t st) -> fr_status {
+    gather_col(c, pi, V, ld, x, n, st);
+    return launch_jvp_prepared_neg64(c, qptr, x, w, prec, st);
+  };
+  if (!c->use_graphs || !c->jvp_graph_ok) return direct(s);
+  const void* timed = c->timing.on ? (const void*)c : nullptr;
+  const void* key[4] = {qptr, V, w, timed};
+  if (c->jvp_graph[pi] && std::equal(key, key + 4, c->jvp_graph_key[pi])) {
+    if (cudaGraphLaunch(c->jvp_graph[pi], s) != cudaSuccess) {
       cudaGetLastError();
-      for (auto& r : c->graph_timers[pi]) {
-        c->timing.pool.push_back(r.a);
-        c->timing.pool.push_back(r.b);
-      }
-      c->graph_timers[pi].clear();
-      c->jvp_graph[pi] = nullptr;
       c->jvp_graph_ok = false;
-      return true;  // the direct launches above already produced w
+      return direct(s);
     }
-    std::copy(key, key + 4, c->jvp_graph_key[pi]);
-    return true;
+    c->timing.launches += c->jvp_graph_nodes[pi];
+    c->graph_timers_live[pi] = c->timing.on && !c->graph_timers[pi].empty();
+    return FR_OK;
   }
-  if (cudaGraphLaunch(c->jvp_graph[pi], s) != cudaSuccess) {
+  if (c->jvp_graph[pi]) {
+    cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(c->jvp_graph[pi]);
+    c->jvp_graph[pi] = nullptr;
+    release_graph_timers(c, pi);
+  }
+  // this product launched directly: every lazy allocation and kernel attribute
+  // is then in place before the capture
+  fr_status e = direct(s);
+  if (e != FR_OK) return e;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres product");
+  // captured on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured); replayed on the caller's stream
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
+    c->cap_stream = nullptr;
     c->jvp_graph_ok = false;
-    return false;
+    return FR_OK;
   }
-  c->timing.launches += c->jvp_graph_nodes[pi];
-  c->graph_timers_live[pi] = c->timing.on && !c->graph_timers[pi].empty();
-  return true;
+  cudaStream_t cs = c->cap_stream;
+  const long long l0 = c->timing.launches;
+  c->timing.capture = true;
+  c->timing.mark = (int64_t)c->timing.pending.size();
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+  if (ok) {
+    const fr_status st = direct(cs);
+    const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    ok = st == FR_OK && ee == cudaSuccess && g != nullptr && cudaGraphInstantiate(&c->jvp_graph[pi], g, 0) == cudaSuccess;
+  }
+  if (g) cudaGraphDestroy(g);
+  c->timing.capture = false;
+  // the timers recorded during the capture belong to the graph
+  auto& pend = c->timing.pending;
+  c->graph_timers[pi].assign(pend.begin() + c->timing.mark, pend.end());
+  pend.resize(c->timing.mark);
+  c->jvp_graph_nodes[pi] = (int)(c->timing.launches - l0);
+  c->timing.launches = l0;
+  if (!ok) {
+    cudaGetLastError();
+    release_graph_timers(c, pi);
+    c->jvp_graph[pi] = nullptr;
+    c->jvp_graph_ok = false;
+    return FR_OK;   // the direct launches above already produced w
+  }
+  std::copy(key, key + 4, c->jvp_graph_key[pi]);
+  return FR_OK;
 }
 
 // y = A x = sigma x - J(q) x, or y = -J(q) x when shifted is false (Arnoldi
@@ -550,11 +576,21 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     fr_status ps = launch_jvp_prepare(c, op->q64_dev, FR_F64, s);
     if (ps != FR_OK) return ps;
   }
+  // The Krylov basis is stored unnormalised: column j holds u_j and the
+  // orthonormal vector is v_j = s_j u_j, with the scales s_j kept on the host
+  // and on the device.  The normalisation pass of every iteration then
+  // disappears: the update writes the new column directly, the dots are
+  // scaled on the host, the update applies s_i^2 to its coefficients, and the
+  // gather in front of the JVP applies s_j.  In the exact modes the JVP's
+  // volume kernel writes w = -J v_j in FP64 directly.
   double* V = c->d_krylov;
   double* w = vec64(c, 4);
   double* r = vec64(c, 5);
+  double* xs = vec64(c, 10);   // s_j u_j for the finite-difference product
   double* ydev = c->d_red + kOutY;
-  if (!w || !r) return FR_ERR_NOMEM;
+  double* sdev = c->d_red + kOutS;
+  double* sh = c->h_red + 3 * kMaxK;   // pinned host copy of the scales
+  if (!w || !r || !xs) return FR_ERR_NOMEM;
   std::memset(st, 0, sizeof(*st));
   cudaMemsetAsync(x, 0, sizeof(double) * n, s);
   double beta0 = b_norm;
@@ -572,10 +608,25 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   int it = 0;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(kMaxK), h2(kMaxK);
   double res = beta0;
+  const bool exact = op->mode == FR_JV_EXACT;
   const bool vec = aligned16(w) && aligned16(V) && ld % 2 == 0;
   const unsigned grid = red_blocks(n);
   unsigned* ticket = ticket_of(c);
   double* part = c->d_red;
+  auto set_scale = [&](int j, double v) {
+    sh[j] = v;
+    cudaMemcpyAsync(sdev + j, sh + j, sizeof(double), cudaMemcpyHostToDevice, s);
+  };
+  // one Gram-Schmidt pass against columns 0..kk-1: dots of w_in into `raw`,
+  // then w_out = w_in - sum s_i^2 raw_i u_i with ||w_out||^2 into N
+  auto gs_pass = [&](int kk, const double* w_in, double* w_out, double* raw, int with_norm) {
+    FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
+                FR_KC_DISPATCH(kk, vec, grid, k_multidot, double, false, V, ld, kk, w_in, n, part, raw, ticket,
+                               with_norm));
+    FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
+                FR_KC_DISPATCH(kk, vec, grid, k_orth_update, double, false, V, ld, kk, raw, sdev, w_in, w_out, n,
+                               part, c->d_red + kOutN, ticket));
+  };
   bool first = true;
   while (true) {
     double beta = beta0;   // r = b on the first cycle
@@ -591,51 +642,42 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       break;
     }
     FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(r, 1.0 / beta, V, n));
+    set_scale(0, 1.0);
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
     res = beta;
     for (int j = 0; j < m; ++j) {
-      if (!jvp_graph_apply(c, op, V, j, w, s))
-        if ((e = apply_op(c, op, R0, V + (int64_t)j * ld, w, s, false)) != FR_OK) return e;
+      // product w = -J v_j
+      if (exact) {
+        if ((e = exact_product(c, op, V, j, w, s)) != FR_OK) return e;
+      } else {
+        FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(V + (int64_t)j * ld, sh[j], xs, n));
+        if ((e = apply_op(c, op, R0, xs, w, s, false)) != FR_OK) return e;
+      }
       ++it;
       // classical Gram-Schmidt: one pass (reorth 0), a second pass when the
       // first removed more than half of ||w||^2, ||w_new|| < 0.7 ||w|| (DGKS,
       // reorth 1), or always two passes (reorth 2).  Each pass is one multi-dot
-      // and one update; both end in a grid reduction, no separate launch.
-      {
-        const int kk = j + 1;
-        const int ro = o->reorth;
-        FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
-                    FR_KC_DISPATCH(kk, vec, grid, k_multidot, V, ld, kk, w, n, part, c->d_red + kOutH1, ticket,
-                                   ro == 1 ? 1 : 0));
-        FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
-                    FR_KC_DISPATCH(kk, vec, grid, k_orth_update, V, ld, kk, c->d_red + kOutH1, w, n, part,
-                                   c->d_red + kOutN, ticket));
-        if (ro == 2) {
-          FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
-                      FR_KC_DISPATCH(kk, vec, grid, k_multidot, V, ld, kk, w, n, part, c->d_red + kOutH2, ticket, 0));
-          FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
-                      FR_KC_DISPATCH(kk, vec, grid, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part,
-                                     c->d_red + kOutN, ticket));
-        }
-        cudaMemcpyAsync(c->h_red, c->d_red + kOutH1, sizeof(double) * 3 * kMaxK, cudaMemcpyDeviceToHost, s);
+      // and one update, both ending in a grid reduction; the first writes the
+      // new column u_{j+1}, the second works on it in place.
+      const int kk = j + 1;
+      const int ro = o->reorth;
+      double* unew = V + (int64_t)(j + 1) * ld;
+      gs_pass(kk, w, unew, c->d_red + kOutH1, ro == 1 ? 1 : 0);
+      if (ro == 2) gs_pass(kk, unew, unew, c->d_red + kOutH2, 0);
+      cudaMemcpyAsync(c->h_red, c->d_red + kOutH1, sizeof(double) * 3 * kMaxK, cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
+      for (int i = 0; i <= j; ++i) {
+        h[i] = sh[i] * c->h_red[i];
+        h2[i] = ro == 2 ? sh[i] * c->h_red[kMaxK + i] : 0.0;
+      }
+      if (ro == 1 && std::sqrt(c->h_red[2 * kMaxK]) < 0.7 * std::sqrt(c->h_red[kk])) {
+        gs_pass(kk, unew, unew, c->d_red + kOutH2, 0);
+        cudaMemcpyAsync(c->h_red + kMaxK, c->d_red + kOutH2, sizeof(double) * 2 * kMaxK, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
-        for (int i = 0; i <= j; ++i) {
-          h[i] = c->h_red[i];
-          h2[i] = ro == 2 ? c->h_red[kMaxK + i] : 0.0;
-        }
-        if (ro == 1 && std::sqrt(c->h_red[2 * kMaxK]) < 0.7 * std::sqrt(c->h_red[kk])) {
-          FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
-                      FR_KC_DISPATCH(kk, vec, grid, k_multidot, V, ld, kk, w, n, part, c->d_red + kOutH2, ticket, 0));
-          FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
-                      FR_KC_DISPATCH(kk, vec, grid, k_orth_update, V, ld, kk, c->d_red + kOutH2, w, n, part,
-                                     c->d_red + kOutN, ticket));
-          cudaMemcpyAsync(c->h_red + kMaxK, c->d_red + kOutH2, sizeof(double) * 2 * kMaxK, cudaMemcpyDeviceToHost, s);
-          if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
-          for (int i = 0; i <= j; ++i) h2[i] = c->h_red[kMaxK + i];
-        }
+        for (int i = 0; i <= j; ++i) h2[i] = sh[i] * c->h_red[kMaxK + i];
       }
       const double hn = std::sqrt(c->h_red[2 * kMaxK]);
       for (int i = 0; i <= j; ++i) H[i * m + j] = h[i] + h2[i];
@@ -664,8 +706,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       g[j] = cs[j] * g[j];
       res = std::fabs(g[j + 1]);
       k = j + 1;
-      if (hn != 0.0)
-        FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * ld, n));
+      if (hn != 0.0) set_scale(j + 1, 1.0 / hn);
       if (res <= o->rtol * beta0 || it >= o->max_it || hn == 0.0) break;
     }
     for (int i = k - 1; i >= 0; --i) {
@@ -673,6 +714,8 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       for (int l = i + 1; l < k; ++l) t -= H[i * m + l] * y[l];
       y[i] = t / H[i * m + i];
     }
+    // x += sum_i y_i v_i = sum_i (y_i s_i) u_i
+    for (int i = 0; i < k; ++i) y[i] *= sh[i];
     cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
     FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (k + 2), k_combine<<<egrid(n), 256, 0, s>>>(V, ld, k, ydev, x, n));
     st->restarts += 1;
