@@ -355,9 +355,12 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # NVTX range: lets a profiler select the timed steps (ncu --nvtx --nvtx-include bench_timed/)
+        torch.cuda.nvtx.range_push("bench_timed")
         e0.record(stream)
         stats.append(step(qn))
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
     if world > 1:

@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
           for (int t = 0; t < CH; ++t)
             if (c0 + t < k) {
 #pragma unroll
-              for (int u = 0; u < U; ++u) acc[c0 + t] += vv[u][t][0] * wv[u][0] + vv[u][t][1] * wv[u][1];
+              for (int u = 0; u < U; ++u)   // explicit FMA chain: one FP64 op per product
+                acc[c0 + t] = fma(vv[u][t][1], wv[u][1], fma(vv[u][t][0], wv[u][0], acc[c0 + t]));
             }
         }
       }
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
     // much time as the 8 bytes it is paired with
     if (!V || with_norm) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) acc[KC] += wv[u][0] * wv[u][0] + wv[u][1] * wv[u][1];
+      for (int u = 0; u < U; ++u) acc[KC] = fma(wv[u][1], wv[u][1], fma(wv[u][0], wv[u][0], acc[KC]));
     }
   }
   if (!V) {
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       L::store(w_out, q0 + u * stride, nw, n, x[u]);
-      acc[0] += x[u][0] * x[u][0] + x[u][1] * x[u][1];
+      acc[0] = fma(x[u][1], x[u][1], fma(x[u][0], x[u][0], acc[0]));
     }
   }
   grid_sum<1>(acc, 1, partial, out, ticket);
