@@ -226,6 +226,8 @@ def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5):
         "jvp_fd_f64": (lambda: ctx.jvp(q64, v64, out=outs[torch.float64], mode="fd"), 8, 4),
         "vjp_f64": (lambda: ctx.vjp(q64, v64, out=outs[torch.float64]), 8, 3),
         "vjp_f32": (lambda: ctx.vjp(q32, v32, out=outs[torch.float32]), 4, 3),
+        "residual_bf16op": (lambda: ctx.residual(q32, out=outs[torch.float32], bf16_operators=True), 4, 2),
+        "jvp_exact_bf16op": (lambda: ctx.jvp(q32, v32, out=outs[torch.float32], bf16_operators=True), 4, 3),
     }
     res = {}
     side = torch.cuda.Stream()
@@ -256,14 +258,24 @@ def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5):
         res[name] = {"gdof_s": round(N / (ms / 1e3) / 1e9, 3), "ms": round(ms, 4),
                      "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4)}
         del g
+    # accuracy of the reduced-precision operators against FP64 on the same
+    # input (relative 2-norm): FP32 and the bfloat16-operator trial
+    R64 = ctx.residual(q64)
+    J64 = ctx.jvp(q64, v64)
+    for tag, bf in (("f32", False), ("bf16op", True)):
+        Rx = ctx.residual(q32, bf16_operators=bf).double()
+        Jx = ctx.jvp(q32, v32, bf16_operators=bf).double()
+        res["residual_" + tag]["rel_err_vs_f64"] = float((Rx - R64).norm() / R64.norm())
+        res["jvp_exact_" + tag]["rel_err_vs_f64"] = float((Jx - J64).norm() / J64.norm())
     return res
 
 
-def stage_fd64(ctx, tab, qn, N, R1, opts):
-    """Mode (A): the same ESDIRK3 stage with FP64 finite-difference Jv, timed once
-    after one untimed solve."""
+def stage_fd64(ctx, tab, qn, N, R1, opts, **over):
+    """The same ESDIRK3 stage in another product mode, timed once after one
+    untimed solve: by default mode (A), FP64 finite-difference Jv."""
     import torch
     o = dict(opts, mode="fd", jv_dtype=torch.float64, f32_above=0.0)
+    o.update(over)
     qi = torch.empty(N, dtype=torch.float64, device="cuda")
     R2 = torch.empty_like(qi)
     st = None
@@ -410,6 +422,7 @@ def main():
     # per-operator throughput (graph-replayed) and the FP64 finite-difference stage
     ops = op_throughput(ctx, qn[:N], N, peak)
     fd = stage_fd64(ctx, tab, qn, N, R1, opts)
+    bf = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype="bf16op")
 
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
@@ -432,7 +445,7 @@ def main():
         "ops": ops,
         "stage_modes": {"exact_f32_jvp_ms": round(total_ms / args.steps, 3),
                         "exact_f32_jvp_final_abs": stats[-1]["norm_final"],
-                        "fd_f64": fd},
+                        "fd_f64": fd, "exact_bf16op_jvp": bf},
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clocks,

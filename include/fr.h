@@ -31,6 +31,12 @@
  *    n_sp(p_e) = (p_e+1)^nd points (xi fastest) times nv variables (variable
  *    fastest), FP64.  nv = nd + 2: (rho, rho u_i, rho E).
  *  - Precision: FR_F64 buffers are double, FR_F32 buffers are float.
+ *    FR_BF16OP (residual, JVP, VJP, GMRES products): float buffers and FP32
+ *    arithmetic with every operator matrix of the discretisation (Lagrange
+ *    interpolation and differentiation, correction-function derivatives,
+ *    mortar interpolation and projection) rounded to bfloat16, 8 significant
+ *    bits: the trial of BF16 operators.  Pack, unpack and the indicator
+ *    treat it as FR_F32.
  */
 #ifndef FR_H
 #define FR_H
@@ -52,7 +58,7 @@ typedef enum {
   FR_ERR_TIMEOUT = -6         /* a bounded device-side wait gave up               */
 } fr_status;
 
-typedef enum { FR_F64 = 0, FR_F32 = 1 } fr_prec;
+typedef enum { FR_F64 = 0, FR_F32 = 1, FR_BF16OP = 2 } fr_prec;
 typedef enum { FR_JV_FD = 0, FR_JV_EXACT = 1 } fr_jv_mode;
 
 /* Boundary kinds used in fr_mesh_desc.nbr (negative values). */

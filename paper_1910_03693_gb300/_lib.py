@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfrgb.so")
 
 FR_OK = 0
-FR_F64, FR_F32 = 0, 1
+FR_F64, FR_F32, FR_BF16OP = 0, 1, 2
 FR_JV_FD, FR_JV_EXACT = 0, 1
 STATUS = {0: "FR_OK", -1: "FR_ERR_INVALID", -2: "FR_ERR_CUDA", -3: "FR_ERR_NOMEM",
           -4: "FR_ERR_NOT_CONVERGED", -5: "FR_ERR_NONFINITE", -6: "FR_ERR_TIMEOUT"}

@@ -42,12 +42,21 @@ def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _prec(t):
-    if t.dtype == torch.float64:
+def _prec(t, bf16_operators=False):
+    if t.dtype == torch.float64 and not bf16_operators:
         return _lib.FR_F64
     if t.dtype == torch.float32:
-        return _lib.FR_F32
-    raise TypeError(f"unsupported dtype {t.dtype}")
+        return _lib.FR_BF16OP if bf16_operators else _lib.FR_F32
+    raise TypeError(f"unsupported dtype {t.dtype}" + (" (bfloat16 operators need FP32 buffers)" if bf16_operators else ""))
+
+
+def _jv_prec(jv_dtype):
+    """torch.float64 / torch.float32, or "bf16op" for FP32 products with bfloat16 operators."""
+    if isinstance(jv_dtype, str):
+        if jv_dtype == "bf16op":
+            return _lib.FR_BF16OP
+        raise ValueError(f"unknown product precision {jv_dtype!r}")
+    return _lib.FR_F64 if jv_dtype == torch.float64 else _lib.FR_F32
 
 
 def _dev(t, name):
@@ -141,24 +150,26 @@ class FRContext:
         return out
 
     # ---------------------------------------------------------------- operators
-    def residual(self, q, out=None):
+    def residual(self, q, out=None, bf16_operators=False):
+        """R(q) in the precision of q; ``bf16_operators`` (FP32 q): the operator
+        matrices rounded to bfloat16 (the BF16-operator trial)."""
         q = _dev(q, "q")
         out = torch.empty_like(q) if out is None else _dev(out, "out")
-        _check(lib().fr_residual(self.h, _ptr(q), _ptr(out), _prec(q), _stream()), "fr_residual")
+        _check(lib().fr_residual(self.h, _ptr(q), _ptr(out), _prec(q, bf16_operators), _stream()), "fr_residual")
         return out
 
-    def jvp(self, q, v, out=None, mode="exact", eps=1e-6):
+    def jvp(self, q, v, out=None, mode="exact", eps=1e-6, bf16_operators=False):
         q, v = _dev(q, "q"), _dev(v, "v")
         out = torch.empty_like(q) if out is None else _dev(out, "out")
         m = _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD
-        _check(lib().fr_jvp(self.h, _ptr(q), _ptr(v), _ptr(out), _prec(q), m, float(eps), _stream()),
-               "fr_jvp")
+        _check(lib().fr_jvp(self.h, _ptr(q), _ptr(v), _ptr(out), _prec(q, bf16_operators), m, float(eps),
+                            _stream()), "fr_jvp")
         return out
 
-    def vjp(self, q, w, out=None):
+    def vjp(self, q, w, out=None, bf16_operators=False):
         q, w = _dev(q, "q"), _dev(w, "w")
         out = torch.empty_like(q) if out is None else _dev(out, "out")
-        _check(lib().fr_vjp(self.h, _ptr(q), _ptr(w), _ptr(out), _prec(q), _stream()), "fr_vjp")
+        _check(lib().fr_vjp(self.h, _ptr(q), _ptr(w), _ptr(out), _prec(q, bf16_operators), _stream()), "fr_vjp")
         return out
 
 
@@ -212,7 +223,7 @@ class FRContext:
         x = torch.empty_like(b) if out is None else _dev(out, "out")
         op = _lib.ShiftedOp(float(sigma), q64.data_ptr(),
                             _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
-                            _lib.FR_F64 if jv_dtype == torch.float64 else _lib.FR_F32, float(eps))
+                            _jv_prec(jv_dtype), float(eps))
         opts = _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth))
         st = _lib.GmresStats()
         _check(lib().gmres_solve(self.h, C.byref(op), _ptr(b), _ptr(x), C.byref(opts), C.byref(st), _stream()),
@@ -241,7 +252,7 @@ class FRContext:
         ptrs = (C.c_void_p * S)(*[(r.data_ptr() if r is not None else 0) for r in Rstages])
         o = _lib.NewtonOpts(float(tol), float(dtau_init), float(dtau_max), int(max_newton), int(max_halvings),
                             _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
-                            _lib.FR_F64 if jv_dtype == torch.float64 else _lib.FR_F32, float(eps),
+                            _jv_prec(jv_dtype), float(eps),
                             _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(f32_above))
         st = _lib.StageStats()
         rc = lib().esdirk_stage(self.h, C.byref(tab), int(stage), float(dt), _ptr(qn), ptrs, _ptr(qi),

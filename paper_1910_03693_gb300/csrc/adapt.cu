@@ -319,7 +319,7 @@ extern "C" {
 
 fr_status spectral_decay_indicator(fr_ctx* c, const void* q_dev, fr_prec prec, int32_t var, double* eta_dev,
                                    double* eta_max_dev, void* stream) {
-  if (!c || !q_dev || !eta_dev || (prec != FR_F64 && prec != FR_F32) || var < 0 || var >= c->nv) {
+  if (!c || !q_dev || !eta_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP) || var < 0 || var >= c->nv) {
     set_error("spectral_decay_indicator: bad argument");
     return FR_ERR_INVALID;
   }
@@ -342,7 +342,7 @@ fr_status spectral_decay_indicator(fr_ctx* c, const void* q_dev, fr_prec prec, i
 
 fr_status p_rebucket(fr_ctx* c, const double* eta_dev, const double* eta_max_dev, const fr_adapt_opts* o,
                      void* q_dev, fr_prec prec, int32_t* perm_out_dev, void* stream) {
-  if (!c || !eta_dev || !eta_max_dev || !o || !q_dev || (prec != FR_F64 && prec != FR_F32) ||
+  if (!c || !eta_dev || !eta_max_dev || !o || !q_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP) ||
       o->p_min < c->p_min || o->p_max > c->p_max || o->p_min > o->p_max) {
     set_error("p_rebucket: bad argument (degrees must lie within the context's limits)");
     return FR_ERR_INVALID;

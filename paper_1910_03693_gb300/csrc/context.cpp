@@ -396,6 +396,29 @@ static fr_status create_impl(const fr_mesh_desc* m, const fr_physics* ph, const 
       float* dst = reinterpret_cast<float*>(&m32[Pm * (kPM + 1) + Ps]);
       for (size_t k = 0; k < sizeof(MortarTab<double>) / sizeof(double); ++k) dst[k] = (float)src[k];
     }
+  // the same tables rounded to bfloat16 (nearest, ties to even), kept in float
+  auto bf16 = [](float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+  };
+  std::vector<BasisTab<float>> b16(b32);
+  std::vector<MortarTab<float>> m16(m32);
+  for (auto& t : b16) {
+    float* f = reinterpret_cast<float*>(&t);
+    for (size_t k = 0; k < sizeof(BasisTab<float>) / sizeof(float); ++k) f[k] = bf16(f[k]);
+  }
+  for (auto& t : m16) {
+    float* f = reinterpret_cast<float*>(&t);
+    for (size_t k = 0; k < sizeof(MortarTab<float>) / sizeof(float); ++k) f[k] = bf16(f[k]);
+  }
+  FR_CUDA(cudaMalloc(&c->d_basis16, sizeof(BasisTab<float>) * b16.size()));
+  FR_CUDA(cudaMemcpy(c->d_basis16, b16.data(), sizeof(BasisTab<float>) * b16.size(), cudaMemcpyHostToDevice));
+  FR_CUDA(cudaMalloc(&c->d_mortar16, sizeof(MortarTab<float>) * m16.size()));
+  FR_CUDA(cudaMemcpy(c->d_mortar16, m16.data(), sizeof(MortarTab<float>) * m16.size(), cudaMemcpyHostToDevice));
   FR_CUDA(cudaMalloc(&c->d_basis64, sizeof(BasisTab<double>) * b64.size()));
   FR_CUDA(cudaMalloc(&c->d_basis32, sizeof(BasisTab<float>) * b32.size()));
   FR_CUDA(cudaMemcpy(c->d_basis64, b64.data(), sizeof(BasisTab<double>) * b64.size(), cudaMemcpyHostToDevice));
@@ -499,6 +522,8 @@ static fr_status create_impl(const fr_mesh_desc* m, const fr_physics* ph, const 
 static void destroy_impl(fr_ctx* c) {
   cudaFree(c->d_basis64);
   cudaFree(c->d_basis32);
+  cudaFree(c->d_basis16);
+  cudaFree(c->d_mortar16);
   cudaFree(c->d_mortar64);
   cudaFree(c->d_mortar32);
   cudaFree(c->d_gaff64);

@@ -20,12 +20,13 @@ static inline int ipow(int b, int e) {
 
 template <typename T>
 inline BasisTab<T>* basis_ptr(fr_ctx* c) {
-  return std::is_same<T, double>::value ? (BasisTab<T>*)c->d_basis64 : (BasisTab<T>*)c->d_basis32;
+  return std::is_same<T, double>::value ? (BasisTab<T>*)c->d_basis64
+                                        : (BasisTab<T>*)(c->bf16op ? c->d_basis16 : c->d_basis32);
 }
 template <typename T>
 inline MortarTab<T>* mortar_ptr(fr_ctx* c, int Pm, int Ps) {
   return std::is_same<T, double>::value ? (MortarTab<T>*)(c->d_mortar64 + Pm * (kPM + 1) + Ps)
-                                        : (MortarTab<T>*)(c->d_mortar32 + Pm * (kPM + 1) + Ps);
+                                        : (MortarTab<T>*)((c->bf16op ? c->d_mortar16 : c->d_mortar32) + Pm * (kPM + 1) + Ps);
 }
 
 template <typename T>

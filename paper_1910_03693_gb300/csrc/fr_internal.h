@@ -114,8 +114,11 @@ struct fr_ctx {
   // tables (device)
   frgb::BasisTab<double>* d_basis64 = nullptr;   // [kPM + 1], indexed by P
   frgb::BasisTab<float>* d_basis32 = nullptr;
+  frgb::BasisTab<float>* d_basis16 = nullptr;    // operators rounded to bfloat16 (FR_BF16OP)
   frgb::MortarTab<double>* d_mortar64 = nullptr; // [(kPM+1)*(kPM+1)], index Pm*(kPM+1)+Ps
   frgb::MortarTab<float>* d_mortar32 = nullptr;
+  frgb::MortarTab<float>* d_mortar16 = nullptr;
+  bool bf16op = false;      // FP32 kernels read the bfloat16-rounded operators
   // geometry (device): affine -> per element constants; else per degree
   double* d_gaff64 = nullptr;
   float* d_gaff32 = nullptr;
@@ -163,7 +166,7 @@ struct fr_ctx {
   // CUDA graph of one Arnoldi matrix-vector product -J(q) V[j] (per precision),
   // with the column index read from d_jidx; keyed by the pointers it captured
   cudaGraphExec_t jvp_graph[2] = {nullptr, nullptr};
-  const void* jvp_graph_key[2][4] = {};
+  const void* jvp_graph_key[2][5] = {};
   int jvp_graph_nodes[2] = {0, 0};
   std::vector<frgb::TimerRec> graph_timers[2];  // event pairs inside each graph
   bool graph_timers_live[2] = {false, false};   // a replay's timers are not yet accumulated

@@ -12,30 +12,42 @@ namespace frgb {
 
 Timing& timing_of(fr_ctx* c);
 
+// FR_F64 -> FP64 kernels; FR_F32 -> FP32 kernels; FR_BF16OP -> FP32 kernels
+// reading the bfloat16-rounded operator tables (the kernel arguments point at
+// them, so a captured graph keeps the tables it was captured with)
+static fr_status run_op_prec(fr_ctx* c, int op, const void* q, const void* v, void* out, fr_prec prec,
+                             cudaStream_t s) {
+  if (prec == FR_F64) return run_op_f64(c, op, q, v, out, s);
+  c->bf16op = prec == FR_BF16OP;
+  const fr_status st = run_op_f32(c, op, q, v, out, s);
+  c->bf16op = false;
+  return st;
+}
+
 fr_status launch_residual(fr_ctx* c, const void* q, void* R, fr_prec prec, cudaStream_t s) {
-  return prec == FR_F64 ? run_op_f64(c, 0, q, nullptr, R, s) : run_op_f32(c, 0, q, nullptr, R, s);
+  return run_op_prec(c, 0, q, nullptr, R, prec, s);
 }
 
 fr_status launch_jvp_exact(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec,
                            cudaStream_t s) {
-  return prec == FR_F64 ? run_op_f64(c, 1, q, v, Jv, s) : run_op_f32(c, 1, q, v, Jv, s);
+  return run_op_prec(c, 1, q, v, Jv, prec, s);
 }
 
 fr_status launch_jvp_prepare(fr_ctx* c, const void* q, fr_prec prec, cudaStream_t s) {
-  return prec == FR_F64 ? run_op_f64(c, 3, q, nullptr, nullptr, s) : run_op_f32(c, 3, q, nullptr, nullptr, s);
+  return run_op_prec(c, 3, q, nullptr, nullptr, prec, s);
 }
 
 fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec, cudaStream_t s) {
-  return prec == FR_F64 ? run_op_f64(c, 4, q, v, Jv, s) : run_op_f32(c, 4, q, v, Jv, s);
+  return run_op_prec(c, 4, q, v, Jv, prec, s);
 }
 
 fr_status launch_jvp_prepared_neg64(fr_ctx* c, const void* q, const void* v, double* w, fr_prec prec,
                                     cudaStream_t s) {
-  return prec == FR_F64 ? run_op_f64(c, 6, q, v, w, s) : run_op_f32(c, 6, q, v, w, s);
+  return run_op_prec(c, 6, q, v, w, prec, s);
 }
 
 fr_status launch_vjp(fr_ctx* c, const void* q, const void* w, void* JTw, fr_prec prec, cudaStream_t s) {
-  return prec == FR_F64 ? run_op_f64(c, 2, q, w, JTw, s) : run_op_f32(c, 2, q, w, JTw, s);
+  return run_op_prec(c, 2, q, w, JTw, prec, s);
 }
 
 // One block per element slot; threads walk the element's [v][sp] block.
@@ -178,17 +190,17 @@ fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
 }
 
 fr_status fr_pack(fr_ctx* c, const double* canon_dev, void* q_dev, fr_prec prec, void* stream) {
-  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32)) return FR_ERR_INVALID;
+  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) return FR_ERR_INVALID;
   return launch_pack(c, canon_dev, q_dev, prec, false, (cudaStream_t)stream);
 }
 
 fr_status fr_unpack(fr_ctx* c, const void* q_dev, fr_prec prec, double* canon_dev, void* stream) {
-  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32)) return FR_ERR_INVALID;
+  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) return FR_ERR_INVALID;
   return launch_pack(c, canon_dev, const_cast<void*>(q_dev), prec, true, (cudaStream_t)stream);
 }
 
 fr_status fr_residual(fr_ctx* c, const void* q_dev, void* R_dev, fr_prec prec, void* stream) {
-  if (!c || !q_dev || !R_dev || (prec != FR_F64 && prec != FR_F32)) {
+  if (!c || !q_dev || !R_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) {
     set_error("fr_residual: bad argument");
     return FR_ERR_INVALID;
   }
@@ -197,7 +209,7 @@ fr_status fr_residual(fr_ctx* c, const void* q_dev, void* R_dev, fr_prec prec, v
 
 fr_status fr_vjp(fr_ctx* c, const void* q_dev, const void* w_dev, void* JTw_dev, fr_prec prec,
                  void* stream) {
-  if (!c || !q_dev || !w_dev || !JTw_dev || (prec != FR_F64 && prec != FR_F32)) {
+  if (!c || !q_dev || !w_dev || !JTw_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) {
     set_error("fr_vjp: bad argument");
     return FR_ERR_INVALID;
   }
@@ -206,7 +218,7 @@ fr_status fr_vjp(fr_ctx* c, const void* q_dev, const void* w_dev, void* JTw_dev,
 
 fr_status fr_jvp(fr_ctx* c, const void* q_dev, const void* v_dev, void* Jv_dev, fr_prec prec,
                  fr_jv_mode mode, double eps, void* stream) {
-  if (!c || !q_dev || !v_dev || !Jv_dev || (prec != FR_F64 && prec != FR_F32)) {
+  if (!c || !q_dev || !v_dev || !Jv_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) {
     set_error("fr_jvp: bad argument");
     return FR_ERR_INVALID;
   }

@@ -434,8 +434,8 @@ static void release_graph_timers(fr_ctx* c, int pi) {
 
 static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double* V, int j, double* w,
                                cudaStream_t s) {
-  const int pi = op->jv_prec == FR_F32 ? 1 : 0;
-  const fr_prec prec = pi ? FR_F32 : FR_F64;
+  const int pi = op->jv_prec == FR_F64 ? 0 : 1;   // FP32 kernels for FR_F32 and FR_BF16OP
+  const fr_prec prec = op->jv_prec;
   const int64_t n = c->n_dof, ld = krylov_ld(c);
   if (!c->d_jidx) {
     if (cudaMalloc(&c->d_jidx, sizeof(int)) != cudaSuccess) return FR_ERR_NOMEM;
@@ -454,8 +454,8 @@ static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double*
   };
   if (!c->use_graphs || !c->jvp_graph_ok) return direct(s);
   const void* timed = c->timing.on ? (const void*)c : nullptr;
-  const void* key[4] = {qptr, V, w, timed};
-  if (c->jvp_graph[pi] && std::equal(key, key + 4, c->jvp_graph_key[pi])) {
+  const void* key[5] = {qptr, V, w, timed, (const void*)(intptr_t)(prec + 1)};
+  if (c->jvp_graph[pi] && std::equal(key, key + 5, c->jvp_graph_key[pi])) {
     if (cudaGraphLaunch(c->jvp_graph[pi], s) != cudaSuccess) {
       cudaGetLastError();
       c->jvp_graph_ok = false;
@@ -510,7 +510,7 @@ static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double*
     c->jvp_graph_ok = false;
     return FR_OK;   // the direct launches above already produced w
   }
-  std::copy(key, key + 4, c->jvp_graph_key[pi]);
+  std::copy(key, key + 5, c->jvp_graph_key[pi]);
   return FR_OK;
 }
 
@@ -539,7 +539,7 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
     float* J32 = vec32(c, 2);
     if (!q32 || !x32 || !J32) return FR_ERR_NOMEM;
     vcast_f64_f32(c, x, x32, n, s);
-    fr_status st = launch_jvp_prepared(c, q32, x32, J32, FR_F32, s);
+    fr_status st = launch_jvp_prepared(c, q32, x32, J32, op->jv_prec, s);
     if (st != FR_OK) return st;
     FR_LAUNCH_B(c, "vec", s, 20.0 * n, k_shift<float><<<egrid(n), 256, 0, s>>>(sigma, x, J32, y, n));
   }
@@ -567,11 +567,11 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     c->krylov_m = m;
     clear_graphs(c);
   }
-  if (op->mode == FR_JV_EXACT && op->jv_prec == FR_F32) {
+  if (op->mode == FR_JV_EXACT && op->jv_prec != FR_F64) {
     float* q32 = vec32(c, 0);
     if (!q32) return FR_ERR_NOMEM;
     vcast_f64_f32(c, op->q64_dev, q32, n, s);
-    fr_status ps = launch_jvp_prepare(c, q32, FR_F32, s);
+    fr_status ps = launch_jvp_prepare(c, q32, op->jv_prec, s);
     if (ps != FR_OK) return ps;
   } else if (op->mode == FR_JV_EXACT) {
     fr_status ps = launch_jvp_prepare(c, op->q64_dev, FR_F64, s);
@@ -751,6 +751,14 @@ fr_status gmres_solve(fr_ctx* c, const fr_shifted_op* op, const double* b_dev, d
     set_error("gmres_solve: finite-difference mode needs eps > 0");
     return FR_ERR_INVALID;
   }
+  if (op->mode != FR_JV_FD && op->mode != FR_JV_EXACT) {
+    set_error("gmres_solve: unknown product mode");
+    return FR_ERR_INVALID;
+  }
+  if (op->jv_prec != FR_F64 && op->jv_prec != FR_F32 && op->jv_prec != FR_BF16OP) {
+    set_error("gmres_solve: unknown product precision");
+    return FR_ERR_INVALID;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const double* R0 = nullptr;
   if (op->mode == FR_JV_FD) {
@@ -768,7 +776,8 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
                        fr_stage_stats* st, void* stream) {
   if (!c || !tab || !qn_dev || !qi_dev || !o || !st || tab->s < 2 || tab->s > 6 || stage < 2 ||
       stage > tab->s || !(dt > 0.0) || !(o->tol > 0.0) || !(o->dtau_init > 0.0) || !(o->dtau_max > 0.0) ||
-      !(o->f32_above >= 0.0)) {
+      !(o->f32_above >= 0.0) || (o->mode != FR_JV_FD && o->mode != FR_JV_EXACT) ||
+      (o->jv_prec != FR_F64 && o->jv_prec != FR_F32 && o->jv_prec != FR_BF16OP)) {
     set_error("esdirk_stage: bad argument");
     return FR_ERR_INVALID;
   }
