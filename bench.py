@@ -207,7 +207,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5):
+def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5, names=None):
     """Residual, JVP (exact and finite-difference) and VJP throughput: each op
     captured ten times into one CUDA graph, the graph replayed ten times (100
     evaluations) per run, median over five runs (CUDA events on the replay
@@ -229,6 +229,8 @@ def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5):
         "residual_bf16op": (lambda: ctx.residual(q32, out=outs[torch.float32], bf16_operators=True), 4, 2),
         "jvp_exact_bf16op": (lambda: ctx.jvp(q32, v32, out=outs[torch.float32], bf16_operators=True), 4, 3),
     }
+    if names is not None:
+        ops = {k: v for k, v in ops.items() if k in names}
     res = {}
     side = torch.cuda.Stream()
     for name, (fn, size, nvec) in ops.items():
@@ -258,6 +260,8 @@ def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5):
         res[name] = {"gdof_s": round(N / (ms / 1e3) / 1e9, 3), "ms": round(ms, 4),
                      "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4)}
         del g
+    if names is not None:
+        return res
     # accuracy of the reduced-precision operators against FP64 on the same
     # input (relative 2-norm): FP32 and the bfloat16-operator trial
     R64 = ctx.residual(q64)
@@ -268,6 +272,36 @@ def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5):
         res["residual_" + tag]["rel_err_vs_f64"] = float((Rx - R64).norm() / R64.norm())
         res["jvp_exact_" + tag]["rel_err_vs_f64"] = float((Jx - J64).norm() / J64.norm())
     return res
+
+
+def mixed_degree_ops(peak_gbs):
+    """Mixed-degree workloads (several buckets): FP64 residual and FP32 exact JVP
+    throughput with one launch per degree bucket, with the persistent
+    multi-bucket launch, and after the autotuner.  The cylinder O-grid
+    (98,304 curved hexahedra, p 1..4) and the batch of 32 2D vortex instances
+    (p 1..5, 8^2..64^2 quads)."""
+    import torch
+    import cases
+    from paper_1910_03693_gb300 import FRContext
+    out = {}
+    for label, (m, q, ph) in (("cylinder_64x96x16_p1-4", cases.workload_cylinder()),
+                              ("vortex_batch_32_p1-5", cases.workload_vortex_batch())):
+        ctx = FRContext(m, gamma=ph["gamma"], mu=ph.get("mu", 0.0), Pr=ph.get("Pr", 0.72), q_inf=ph.get("q_inf"))
+        N = ctx.n_dof
+        q64 = ctx.pack(torch.from_numpy(q).cuda())
+        row = {"n_dof": N, "n_elem": ctx.n_elem, "buckets": len(set(int(x) for x in ctx.p_map()))}
+        for cfg in ("per_bucket", "multi_bucket", "autotuned"):
+            if cfg == "autotuned":
+                t = ctx.autotune(q64)
+                row["autotuned_multi_launch"] = t["multi_launch"]
+            else:
+                ctx.set_tuning({"epb": [0] * 42, "multi_launch": cfg == "multi_bucket"})
+            r = op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=3, names=("residual_f64", "jvp_exact_f32"))
+            row[cfg] = {k: {"gdof_s": v["gdof_s"], "ms": v["ms"]} for k, v in r.items()}
+        out[label] = row
+        del ctx
+        torch.cuda.empty_cache()
+    return out
 
 
 def stage_fd64(ctx, tab, qn, N, R1, opts, **over):
@@ -423,6 +457,7 @@ def main():
     ops = op_throughput(ctx, qn[:N], N, peak)
     fd = stage_fd64(ctx, tab, qn, N, R1, opts)
     bf = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype="bf16op")
+    mixed = mixed_degree_ops(peak) if args.n == 32 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
@@ -443,6 +478,7 @@ def main():
                   "rel_final": [s["norm_final"] / s["norm0"] for s in stats]},
         "roofline": roof,
         "ops": ops,
+        "mixed_degree_ops": mixed,
         "stage_modes": {"exact_f32_jvp_ms": round(total_ms / args.steps, 3),
                         "exact_f32_jvp_final_abs": stats[-1]["norm_final"],
                         "fd_f64": fd, "exact_bf16op_jvp": bf},

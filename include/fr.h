@@ -287,13 +287,17 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
  * fr_autotune times every admissible epb for each degree present and each
  * kernel (trace, volume residual, volume JVP) in FP64 and FP32 on the state
  * q64_dev (FP64, state layout, n_dof), then one launch per bucket against the
- * multi-bucket launch, and keeps the fastest; it synchronises `stream` and
+ * multi-bucket launch for each kernel, and keeps the fastest; it synchronises `stream` and
  * changes no result beyond rounding order.  fr_tuning_get/fr_tuning_set read
  * and write the table, 2 x 3 x 7 int32 [precision f64,f32][kernel trace,
- * volume residual, volume JVP][P = p+1], 0 = default (as many whole elements
- * as fit 256 threads; a value whose elements exceed 256 threads also falls back
- * to it), and the flags below.  fr_tuning_set with table NULL changes only the
- * flags; entries outside [0, 256] or unknown flag bits give FR_ERR_INVALID. */
+ * volume residual, volume JVP][P = p+1]: for P >= 2 the elements per CTA,
+ * 0 = default (as many whole elements as fit 256 threads; a value whose
+ * elements exceed 256 threads also falls back to it); the slot P = 0 holds
+ * the multi-bucket choice of that precision and kernel (0 default = one launch
+ * over all buckets, 1 the same, 2 one launch per bucket), which
+ * FR_TUNE_MULTI_LAUNCH enables; and the flags below.  fr_tuning_set with table NULL changes only the
+ * flags; elements per CTA outside [0, 256], choices outside [0, 2] or unknown
+ * flag bits give FR_ERR_INVALID. */
 #define FR_TUNE_MULTI_LAUNCH 1  /* one persistent launch over all degree buckets */
 #define FR_TUNE_GRAPHS 2        /* Arnoldi products replayed from a CUDA graph */
 #define FR_TUNE_DIAG_METRICS 4  /* 3D meshes of axis-aligned affine elements:

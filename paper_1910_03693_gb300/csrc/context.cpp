@@ -276,6 +276,11 @@ fr_status build_layout(fr_ctx* c) {
   }
   int64_t sc = 0;
   for (auto& kv : inter) {
+    // master-face direction as the major key (element order kept within a
+    // direction): warps then see one normal axis, which the diagonal-metric
+    // face kernel branches on
+    std::stable_sort(kv.second.begin(), kv.second.end(),
+                     [](const FaceRec& a, const FaceRec& b) { return (a.mf >> 1) < (b.mf >> 1); });
     FaceGroup g;
     g.pm = kv.first.first;
     g.ps = kv.first.second;

@@ -74,6 +74,13 @@ static inline int epb_for(fr_ctx* c, int prec, int kind, int P) {
   return (t > 0 && t * nsp <= 256) ? t : dflt;
 }
 
+// One launch over all buckets for this precision and kernel kind: the master
+// switch, more than one bucket, and the per-kind choice (the autotuner writes
+// it into the unused P = 0 slot of the table: 0 default = yes, 1 yes, 2 no).
+static inline bool use_multi(fr_ctx* c, int prec, int kind) {
+  return c->multi_launch && c->buckets.size() > 1 && c->epb_tab[prec][kind][0] != 2;
+}
+
 static inline unsigned sm_count(fr_ctx* c) {
   int n = 0;
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
@@ -158,7 +165,7 @@ static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
   }
   const char* name = sizeof(T) == 8 ? "trace_f64" : "trace_f32";
   int n_items = 0;
-  const WorkItem* items = (c->multi_launch && c->buckets.size() > 1) ? work_items(c, prec, 0, &n_items) : nullptr;
+  const WorkItem* items = use_multi(c, prec, 0) ? work_items(c, prec, 0, &n_items) : nullptr;
   if (items) {
     TraceMulti<T> m;
     size_t smem = 0;
@@ -243,7 +250,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     nfl += MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC, DIAG);
   }
   int n_items = 0;
-  const WorkItem* items = (c->multi_launch && c->buckets.size() > 1) ? work_items(c, prec, kind, &n_items) : nullptr;
+  const WorkItem* items = use_multi(c, prec, kind) ? work_items(c, prec, kind, &n_items) : nullptr;
   if (items) {
     VolMulti<T> m;
     size_t smem = 0;
@@ -283,7 +290,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
   }
 }
 
-template <typename T, int ND, bool VISC, int MODE>
+template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
 static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) {
   for (const auto& g : c->fgroups) {
     FaceArgs<T> a;
@@ -307,8 +314,8 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
     const int64_t nm = (int64_t)g.n * ipow(a.Pm, ND - 1);
     FR_LAUNCH_BF(c, MODE == 1 ? (sizeof(T) == 8 ? "face_jvp_f64" : "face_jvp_f32")
                               : (sizeof(T) == 8 ? "face_res_f64" : "face_res_f32"),
-                 s, 0.0, MODE == 1 ? 0.0 : (double)nm * flops_face(ND, VISC),
-                 face_kernel<T, ND, VISC, MODE><<<nblocks(nm, 128), 128, 0, s>>>(a));
+                 s, 0.0, MODE == 1 ? 0.0 : (double)nm * flops_face(ND, VISC, DIAG),
+                 face_kernel<T, ND, VISC, MODE, DIAG><<<nblocks(nm, 128), 128, 0, s>>>(a));
     if (g.pm != g.ps) {
       const int64_t ns = (int64_t)g.n * ipow(a.Ps, ND - 1);
       FR_LAUNCH(c, "mortar_project", s,
@@ -339,7 +346,7 @@ template <typename T, int ND, bool VISC, bool DIAG = false>
 static void residual_impl(fr_ctx* c, const T* q, T* R, cudaStream_t s) {
   T* trq = (T*)c->d_trace_q;
   launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
-  launch_faces<T, ND, VISC, 0>(c, trq, nullptr, s);
+  launch_faces<T, ND, VISC, 0, DIAG>(c, trq, nullptr, s);
   launch_vols<T, ND, VISC, 0, DIAG>(c, q, nullptr, R, s);
 }
 
@@ -352,7 +359,7 @@ static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, b
   T* trv = (T*)c->d_trace_v;
   if (!q_traces_ready) launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
   launch_traces<T, ND, VISC, DIAG>(c, v, trv, s);
-  launch_faces<T, ND, VISC, 1>(c, trq, trv, s);
+  launch_faces<T, ND, VISC, 1, DIAG>(c, trq, trv, s);
   launch_vols<T, ND, VISC, 1, DIAG>(c, q, v, Jv, s, neg64);
 }
 
@@ -565,16 +572,28 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
   }
   (void)trv;
   clear_work_cache(c);
-  // one launch per bucket vs one multi-bucket launch, for the whole JVP
+  // per kernel kind: one launch per bucket against one multi-bucket launch,
+  // with the tuned elements per CTA (the multi kernel carries the register
+  // footprint of its largest degree, so large meshes usually prefer separate
+  // launches and small batches of buckets the single one)
+  c->multi_launch = true;
   if (c->buckets.size() > 1) {
-    c->multi_launch = false;
-    const float t_sep = time_best(reps, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });
-    c->multi_launch = true;
-    const float t_multi = time_best(reps, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });
-    c->multi_launch = t_multi <= t_sep;
-  } else {
-    c->multi_launch = multi_saved;
+    residual_impl<T, ND, VISC, DIAG>(c, q, scratch, s);
+    for (int kind = 0; kind < 3; ++kind) {
+      if (kind == 2) jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s);
+      float t[2];
+      for (int m = 0; m < 2; ++m) {
+        c->epb_tab[prec][kind][0] = m == 0 ? 2 : 1;
+        t[m] = time_best(reps + 2, s, [&] {
+          if (kind == 0) launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
+          else if (kind == 1) launch_vols<T, ND, VISC, 0, DIAG>(c, q, nullptr, scratch, s);
+          else launch_vols<T, ND, VISC, 1, DIAG>(c, q, q, scratch, s);
+        });
+      }
+      c->epb_tab[prec][kind][0] = t[1] <= t[0] ? 1 : 2;
+    }
   }
+  c->multi_launch = multi_saved;
 }
 
 // One operation for one (dimension, viscosity, metric) configuration.

@@ -326,7 +326,11 @@ __device__ __forceinline__ void slave_coef_at_mortar(const FaceArgs<T>& a, const
   }
 }
 
-template <typename T, int ND, bool VISC, int MODE>
+// DIAG: both sides have diagonal metrics (axis-aligned affine elements), so the
+// area vector and the BR2 lifting coefficients point along the master face's
+// axis dm and only the viscous flux row dm is needed.  Face records are sorted
+// by dm, so the branches on it are warp-uniform.
+template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
 __global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
   constexpr int NV = ND + 2;
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
@@ -375,19 +379,40 @@ __global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
       b.trv = trv;
       slave_at_mortar<ND>(b, r.st, NV, ND * NV, u, &GS[0][0]);
     }
+    if (DIAG) {
 #pragma unroll
-    for (int j = 0; j < ND; ++j)
+      for (int j = 0; j < ND; ++j)
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
-        Gc[j][v] = T(0.5) * (GM[j][v] + cM[j] * (qc[v] - qM[v]) + GS[j][v] + cS[j] * (qc[v] - qS[v]));
-    S fv[ND][NV];
-    flux_viscous<ND>(qc, Gc, a.gamma, a.mu, a.kappa, fv);
+        for (int v = 0; v < NV; ++v) Gc[j][v] = T(0.5) * (GM[j][v] + GS[j][v]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      S acc = szero<S>();
+      for (int j = 0; j < ND; ++j) {
+        if (j != dm) continue;
 #pragma unroll
-      for (int j = 0; j < ND; ++j) acc = acc + fv[j][v] * A[j];
-      Fn[v] = Fn[v] - acc;
+        for (int v = 0; v < NV; ++v) Gc[j][v] = Gc[j][v] + T(0.5) * (cM[j] * (qc[v] - qM[v]) + cS[j] * (qc[v] - qS[v]));
+      }
+      S fr[NV];
+      flux_viscous_row<ND>(qc, Gc, a.gamma, a.mu, a.kappa, dm, fr);
+      T Ad = T(0);
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+        if (j == dm) Ad = A[j];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fn[v] = Fn[v] - fr[v] * Ad;
+    } else {
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          Gc[j][v] = T(0.5) * (GM[j][v] + cM[j] * (qc[v] - qM[v]) + GS[j][v] + cS[j] * (qc[v] - qS[v]));
+      S fv[ND][NV];
+      flux_viscous<ND>(qc, Gc, a.gamma, a.mu, a.kappa, fv);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        S acc = szero<S>();
+#pragma unroll
+        for (int j = 0; j < ND; ++j) acc = acc + fv[j][v] * A[j];
+        Fn[v] = Fn[v] - acc;
+      }
     }
   }
   // master side

@@ -184,6 +184,46 @@ __device__ __forceinline__ void flux_viscous(const S* q, const S (*G)[ND + 2], T
   }
 }
 
+// Row d of the viscous flux, fv[d][v] (the flux through a face normal to axis
+// d): the same arithmetic as flux_viscous restricted to that row.
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void flux_viscous_row(const S* q, const S (*G)[ND + 2], T gamma, T mu, T kappa,
+                                                 int d, S* fr) {
+  constexpr int NV = ND + 2;
+  const S rinv = T(1) / q[0];
+  S vel[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) vel[i] = q[1 + i] * rinv;
+  const S Es = q[NV - 1] * rinv;
+  S du[ND][ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) du[i][j] = (G[j][1 + i] - vel[i] * G[j][0]) * rinv;
+  S div = szero<S>();
+#pragma unroll
+  for (int k = 0; k < ND; ++k) div = div + du[k][k];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    if (j != d) continue;
+    S dE = (G[j][NV - 1] - Es * G[j][0]) * rinv;
+    S s = szero<S>();
+#pragma unroll
+    for (int k = 0; k < ND; ++k) s = s + vel[k] * du[k][j];
+    const S dT = (gamma - T(1)) * (dE - s);
+    fr[0] = szero<S>();
+    S e = szero<S>();
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      S tau = mu * (du[i][j] + du[j][i]);
+      if (i == j) tau = tau - T(2.0 / 3.0) * mu * div;
+      fr[1 + i] = tau;
+      e = e + vel[i] * tau;
+    }
+    fr[NV - 1] = e + kappa * dT;
+  }
+}
+
 // Ghost state of a boundary: wall (-1) reverses momentum, far field (-2) is q_inf.
 template <int ND, typename S, typename T>
 __device__ __forceinline__ void ghost_state(const S* q, int kind, const T* qinf, S* g) {

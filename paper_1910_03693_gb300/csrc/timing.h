@@ -160,12 +160,18 @@ inline double flops_trace(int nd, int P, bool visc, bool diag = false) {
   if (visc) f += nv * 2 * P * nd + (diag ? 2 * nd * nv : nd * nv * (2 * nd + 1));
   return f;
 }
-inline double flops_face(int nd, bool visc) {
+inline double flops_face(int nd, bool visc, bool diag = false) {
   const int nv = nd + 2;
   double f = 2 * (6 + 3 * nd + 3 * nd) + 1 + 6 * nv + 3 * nd + 2;   // two normal fluxes, Rusanov, area
   if (visc) {
-    const double fv = 2 + nd + 3 * nd * nd + 3 * nd + 2 * nd * nd + 2 * nd + (nd - 1) + 3 * nd * nd + 2 * nd * nd + 2 * nd;
-    f += 2 * nv + 2 * (2 * nd + 1) + 8 * nd * nv + fv + 2 * nd * nv + nv + 4 * nv;
+    if (!diag) {
+      const double fv = 2 + nd + 3 * nd * nd + 3 * nd + 2 * nd * nd + 2 * nd + (nd - 1) + 3 * nd * nd + 2 * nd * nd + 2 * nd;
+      f += 2 * nv + 2 * (2 * nd + 1) + 8 * nd * nv + fv + 2 * nd * nv + nv + 4 * nv;
+    } else {
+      // lifting terms along the face axis only; one row of the viscous flux
+      const double fr = 2 + nd + 3 * nd * nd + (nd - 1) + 2 * nd + 5 + 3 * nd + 2 * nd + 2;
+      f += 2 * nv + 2 * (2 * nd + 1) + 2 * nd * nv + 6 * nv + fr + 2 * nv + nv + 4 * nv;
+    }
   }
   return f;
 }
