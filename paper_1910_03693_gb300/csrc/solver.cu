@@ -170,6 +170,7 @@ template <int KC>
 struct Unroll {
   static constexpr int U = KC <= 2 ? 4 : (KC <= 8 ? 2 : 1);
   static constexpr int CH = KC < 8 ? KC : 8;   // columns per load batch
+  static constexpr int A = KC <= 2 ? 4 : (KC <= 8 ? 2 : 1);   // accumulators per column
 };
 
 // Slot q of the vector w as FP64 values: w is FP64, or the FP32 output of the
@@ -214,9 +215,14 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
   constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
   using L = Slots<VEC>;
   using LW = WSlots<VEC, WT, NEG>;
-  double acc[KC + 1];
+  // A independent accumulators per column: FP64 FMAs have a long latency on
+  // GB300, and one chain per column leaves the FP64 pipe idle for few columns
+  constexpr int A = Unroll<KC>::A;
+  double acc[A][KC + 1];
 #pragma unroll
-  for (int kk = 0; kk <= KC; ++kk) acc[kk] = 0.0;
+  for (int a = 0; a < A; ++a)
+#pragma unroll
+    for (int kk = 0; kk <= KC; ++kk) acc[a][kk] = 0.0;
   const int64_t nw = n / L::W, stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t last = nw + ((VEC && (n & 1)) ? 0 : -1);   // highest slot holding data
   for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 <= last; q0 += U * stride) {
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
             if (c0 + t < k) {
 #pragma unroll
               for (int u = 0; u < U; ++u)   // explicit FMA chain: one FP64 op per product
-                acc[c0 + t] = fma(vv[u][t][1], wv[u][1], fma(vv[u][t][0], wv[u][0], acc[c0 + t]));
+                acc[u % A][c0 + t] = fma(vv[u][t][1], wv[u][1], fma(vv[u][t][0], wv[u][0], acc[u % A][c0 + t]));
             }
         }
       }
@@ -247,19 +253,24 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
     // much time as the 8 bytes it is paired with
     if (!V || with_norm) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) acc[KC] = fma(wv[u][1], wv[u][1], fma(wv[u][0], wv[u][0], acc[KC]));
+      for (int u = 0; u < U; ++u) acc[u % A][KC] = fma(wv[u][1], wv[u][1], fma(wv[u][0], wv[u][0], acc[u % A][KC]));
     }
   }
+  // fixed-order combination of the partial accumulators
+#pragma unroll
+  for (int a = 1; a < A; ++a)
+#pragma unroll
+    for (int kk = 0; kk <= KC; ++kk) acc[0][kk] += acc[a][kk];
   if (!V) {
-    const double one[1] = {acc[KC]};
+    const double one[1] = {acc[0][KC]};
     grid_sum<1>(one, 1, partial, out, ticket);
     return;
   }
   // slots 0..k-1: the dots; slot k: ||w||^2 (selects only, no runtime indexing)
   double o[KC + 1];
 #pragma unroll
-  for (int kk = 0; kk < KC; ++kk) o[kk] = kk < k ? acc[kk] : acc[KC];
-  o[KC] = acc[KC];
+  for (int kk = 0; kk < KC; ++kk) o[kk] = kk < k ? acc[0][kk] : acc[0][KC];
+  o[KC] = acc[0][KC];
   grid_sum<KC + 1>(o, with_norm ? k + 1 : k, partial, out, ticket);
 }
 
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
   __shared__ double hs[KC];
   if (threadIdx.x < KC) hs[threadIdx.x] = threadIdx.x < k ? scale[threadIdx.x] * scale[threadIdx.x] * raw[threadIdx.x] : 0.0;
   __syncthreads();
-  double acc[1] = {0.0};
+  double accu[U] = {};
   const int64_t nw = n / L::W, stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t last = nw + ((VEC && (n & 1)) ? 0 : -1);
   for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 <= last; q0 += U * stride) {
@@ -308,9 +319,12 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       L::store(w_out, q0 + u * stride, nw, n, x[u]);
-      acc[0] = fma(x[u][1], x[u][1], fma(x[u][0], x[u][0], acc[0]));
+      accu[u] = fma(x[u][1], x[u][1], fma(x[u][0], x[u][0], accu[u]));
     }
   }
+  double acc[1] = {accu[0]};
+#pragma unroll
+  for (int u = 1; u < U; ++u) acc[0] += accu[u];
   grid_sum<1>(acc, 1, partial, out, ticket);
 }
 
