@@ -14,7 +14,7 @@
 
 namespace frgb {
 
-constexpr int kRedBlocks = 1216;    // most blocks of a reduction: 8 per SM on 152 SMs (grid-stride)
+constexpr int kRedBlocks = 608;     // most blocks of a reduction: 4 per SM on 152 SMs (grid-stride)
 constexpr int kRedThreads = 256;
 constexpr int kMaxK = 64;           // most vectors in one multi-dot (restart length + 1)
 
@@ -170,7 +170,9 @@ template <int KC>
 struct Unroll {
   static constexpr int U = KC <= 2 ? 4 : (KC <= 8 ? 2 : 1);
   static constexpr int CH = KC < 8 ? KC : 8;   // columns per load batch
-  static constexpr int A = KC <= 2 ? 4 : (KC <= 8 ? 2 : 1);   // accumulators per column
+  // accumulators per column: more than one breaks the FMA dependence chain
+  // but costs registers and occupancy, and measured slower in the solver
+  static constexpr int A = 1;
 };
 
 // Slot q of the vector w as FP64 values: w is FP64, or the FP32 output of the
@@ -215,8 +217,6 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
   constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
   using L = Slots<VEC>;
   using LW = WSlots<VEC, WT, NEG>;
-  // A independent accumulators per column: FP64 FMAs have a long latency on
-  // GB300, and one chain per column leaves the FP64 pipe idle for few columns
   constexpr int A = Unroll<KC>::A;
   double acc[A][KC + 1];
 #pragma unroll
