@@ -275,6 +275,21 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
                      const fr_adapt_opts* opts, void* q_inout_dev, fr_prec prec,
                      int32_t* perm_out_dev, void* stream);
 
+/* One physical time step of an ESDIRK scheme (Eqs. ESDIRK_ns,
+ * ESDIRK_conservative): R(q^n), then stages 2..s by esdirk_stage (each stage
+ * starts from the previous stage value), then q^{n+1} = q^n + dt sum_i b_i
+ * R(q^i).  q_inout: FP64 state layout, in q^n, out q^{n+1}; a buffer of
+ * n_dof_capacity values when `adapt` is given.  stats: s-1 entries, one per
+ * implicit stage (optional).  With `adapt` (optional) the step ends with the
+ * spectral decay indicator of variable adapt_var and p_rebucket, as the paper
+ * does after every step (Sec. 3.1); the layout, n_dof and the degrees change.
+ * The context keeps s stage residuals and two state vectors (allocated on
+ * first use).  FR_ERR_NOT_CONVERGED if a stage misses its tolerance, in which
+ * case q_inout is left unchanged and no adaptation happens. */
+fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_inout_dev,
+                      const fr_newton_opts* opts, fr_stage_stats* stats, const fr_adapt_opts* adapt,
+                      int32_t adapt_var, void* stream);
+
 /* Launch configuration (the paper has no counterpart: it is the GPU work
  * decomposition).  The trace and volume kernels process `epb` elements per
  * CTA (one thread per solution point); with several degree buckets they run

@@ -104,6 +104,8 @@ SIGNATURES = {
     "fr_timing_report": [C.c_void_p, C.c_char_p, C.c_int64, C.POINTER(C.c_int64)],
     "p_rebucket": [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(AdaptOpts), C.c_void_p, C.c_int,
                    C.c_void_p, C.c_void_p],
+    "esdirk_step": [C.c_void_p, C.POINTER(Tableau), C.c_double, C.c_void_p, C.POINTER(NewtonOpts),
+                    C.POINTER(StageStats), C.POINTER(AdaptOpts), C.c_int32, C.c_void_p],
 }
 
 

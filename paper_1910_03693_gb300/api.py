@@ -231,6 +231,62 @@ class FRContext:
         return x, dict(iterations=st.iterations, restarts=st.restarts, converged=bool(st.converged),
                        rel_res=st.rel_res)
 
+    @staticmethod
+    def _tableau(A, b=None):
+        S = len(A)
+        tab = _lib.Tableau()
+        tab.s = S
+        for i in range(S):
+            for j in range(S):
+                tab.A[i * S + j] = float(A[i][j])
+        bb = A[-1] if b is None else b
+        for i in range(S):
+            tab.b[i] = float(bb[i])
+        return tab
+
+    @staticmethod
+    def _newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton, max_halvings,
+                     reorth, f32_above):
+        return _lib.NewtonOpts(float(tol), float(dtau_init), float(dtau_max), int(max_newton), int(max_halvings),
+                               _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
+                               _jv_prec(jv_dtype), float(eps),
+                               _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(f32_above))
+
+    @staticmethod
+    def _stage_dict(st):
+        return dict(newton=st.newton_iterations, gmres=st.gmres_iterations, halvings=st.halvings,
+                    converged=bool(st.converged), norm0=st.norm0, norm_final=st.norm_final,
+                    f32_evaluations=st.f32_evaluations, f64_evaluations=st.f64_evaluations)
+
+    def esdirk_step(self, A, dt, q, b=None, adapt=None, tol=1e-8, dtau_init=0.05, dtau_max=10.0, mode="exact",
+                    jv_dtype=torch.float32, eps=1e-6, m=30, rtol=0.1, max_it=100, max_newton=200,
+                    max_halvings=20, reorth=0, f32_above=0.0):
+        """One ESDIRK time step in place on ``q`` (FP64 state layout; n_dof_capacity
+        values when adapting).  ``adapt``: None, or dict(nu_max, nu_min, p_min,
+        p_max, var) to run the indicator and the rebucketing after the step.
+        Returns the per-stage statistics (stages 2..s)."""
+        q = _dev(q, "q")
+        assert q.dtype == torch.float64
+        tab = self._tableau(A, b)
+        o = self._newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton,
+                              max_halvings, reorth, f32_above)
+        stats = (_lib.StageStats * (len(A) - 1))()
+        ad = None
+        var = 1
+        if adapt is not None:
+            if q.numel() < self.n_dof_capacity:
+                raise ValueError("q must hold n_dof_capacity values when adapting")
+            ad = _lib.AdaptOpts(float(adapt.get("nu_max", 0.1)), float(adapt.get("nu_min", 0.001)),
+                                int(adapt["p_min"]), int(adapt["p_max"]))
+            var = int(adapt.get("var", 1))
+        rc = lib().esdirk_step(self.h, C.byref(tab), float(dt), _ptr(q), C.byref(o), stats,
+                               C.byref(ad) if ad is not None else None, var, _stream())
+        if rc not in (0, -4):
+            raise FRError("esdirk_step", rc)
+        if adapt is not None:
+            self.refresh_layout()
+        return [self._stage_dict(st) for st in stats]
+
     def esdirk_stage(self, A, stage, dt, qn, Rstages, qi, tol=1e-8, dtau_init=0.05, dtau_max=10.0,
                      mode="exact", jv_dtype=torch.float32, eps=1e-6, m=30, rtol=0.1, max_it=100,
                      max_newton=200, max_halvings=20, b=None, reorth=0, f32_above=0.0):

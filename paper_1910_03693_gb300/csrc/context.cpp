@@ -558,6 +558,7 @@ static void destroy_impl(fr_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_jidx) cudaFreeHost(c->h_jidx);
   cudaFree(c->d_krylov);
+  cudaFree(c->d_step);
   for (auto& v : c->d_vec64) cudaFree(v);
   for (auto& v : c->d_vec32) cudaFree(v);
   cudaFree(c->d_red);

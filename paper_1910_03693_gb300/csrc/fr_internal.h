@@ -149,7 +149,9 @@ struct fr_ctx {
   std::vector<frgb::BndGroup> bgroups;
   int32_t* d_nbr = nullptr;              // [E][nf] for the adaptation smoother
   // solver workspaces (lazily allocated)
-  double* d_krylov = nullptr;            // (m+1) * n_dof_cap basis
+  double* d_krylov = nullptr;
+  double* d_step = nullptr;              // esdirk_step: stage residuals, q^n, stage value, eta
+  int64_t step_cap = 0;                  // doubles in d_step            // (m+1) * n_dof_cap basis
   int krylov_m = 0;
   double* d_vec64[12] = {};   // 0-2 FD Jv, 3 Jv, 4-5 GMRES, 6-9 ESDIRK, 10-11 adaptation
   float* d_vec32[4] = {};

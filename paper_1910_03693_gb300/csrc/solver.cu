@@ -896,4 +896,60 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
   return st->converged ? FR_OK : FR_ERR_NOT_CONVERGED;
 }
 
+fr_status esdirk_step(fr_ctx* c, const fr_tableau* tab, double dt, double* q, const fr_newton_opts* o,
+                      fr_stage_stats* stats, const fr_adapt_opts* adapt, int32_t adapt_var, void* stream) {
+  if (!c || !tab || !q || !o || tab->s < 2 || tab->s > 6 || !(dt > 0.0) ||
+      (adapt && (adapt_var < 0 || adapt_var >= c->nv))) {
+    set_error("esdirk_step: bad argument");
+    return FR_ERR_INVALID;
+  }
+  const int S = tab->s;
+  for (int j = 0; j < S; ++j)
+    if (tab->A[j] != 0.0) {
+      set_error("esdirk_step: the first stage must be explicit (first row of A zero)");
+      return FR_ERR_INVALID;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = c->n_dof, cap = c->n_dof_cap;
+  // S stage residuals, q^n, the stage value, and eta (n_elem + 1)
+  const int64_t need = (S + 2) * cap + c->E + 1;
+  if (c->step_cap < need) {
+    cudaFree(c->d_step);
+    c->d_step = nullptr;
+    c->step_cap = 0;
+    if (cudaMalloc(&c->d_step, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("esdirk_step: workspace allocation failed");
+      return FR_ERR_NOMEM;
+    }
+    c->step_cap = need;
+  }
+  double* Rst[6] = {};
+  for (int i = 0; i < S; ++i) Rst[i] = c->d_step + i * cap;
+  double* qn = c->d_step + S * cap;
+  double* qi = qn + cap;
+  double* eta = qi + cap;
+  cudaMemcpyAsync(qn, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  fr_status e = launch_residual(c, qn, Rst[0], FR_F64, s);
+  if (e != FR_OK) return e;
+  cudaMemcpyAsync(qi, qn, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  // stage i starts from the value of stage i-1
+  for (int i = 2; i <= S; ++i) {
+    fr_stage_stats st;
+    std::memset(&st, 0, sizeof(st));
+    e = esdirk_stage(c, tab, i, dt, qn, Rst, qi, o, &st, stream);
+    if (stats) stats[i - 2] = st;
+    if (e != FR_OK) return e;
+  }
+  // q^{n+1} = q^n + dt sum_i b_i R(q^i)
+  cudaMemcpyAsync(q, qn, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  for (int i = 0; i < S; ++i)
+    if (tab->b[i] != 0.0) vaxpby(c, dt * tab->b[i], Rst[i], 1.0, q, n, s);
+  if (adapt) {
+    if ((e = spectral_decay_indicator(c, q, FR_F64, adapt_var, eta, eta + c->E, stream)) != FR_OK) return e;
+    if ((e = p_rebucket(c, eta, eta + c->E, adapt, q, FR_F64, nullptr, stream)) != FR_OK) return e;
+  }
+  return cuda_check(cudaStreamSynchronize(s), "esdirk_step");
+}
+
 }  // extern "C"
