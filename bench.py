@@ -327,6 +327,49 @@ def stage_fd64(ctx, tab, qn, N, R1, opts, **over):
             "norm_final": st["norm_final"]}
 
 
+def run_timesteps(args):
+    """ESDIRK3 time steps of the extruded NACA 0012 C-grid (256 x 64 x 24 hexahedra,
+    Re 6e4, Ma 0.2, 8 degrees), starting from p = 1 everywhere, with the indicator
+    and rebucketing after every step (p in 1..4), in the mixed-precision
+    exact-JVP mode and in the FP64 finite-difference mode; one JSON line with
+    the per-step times, iteration counts and degree histograms."""
+    import torch
+    import cases
+    from paper_1910_03693_gb300 import FRContext, esdirk_tableau
+    m, q, ph = cases.workload_naca()
+    A, b = esdirk_tableau(3)
+    dt = 0.005
+    out = {"workload": "naca0012_cgrid_256x64x24", "dt": dt, "tableau": "ESDIRK3",
+           "adapt": {"nu_max": 0.1, "nu_min": 0.001, "p_min": 1, "p_max": 4, "var": 1}, "modes": {}}
+    for mode, jv in (("exact", torch.float32), ("fd", torch.float64)):
+        ctx = FRContext(m, gamma=ph["gamma"], mu=ph["mu"], Pr=ph["Pr"], q_inf=ph["q_inf"], p_min=1, p_max=4)
+        buf = torch.zeros(ctx.n_dof_capacity, dtype=torch.float64, device="cuda")
+        ctx.pack(torch.from_numpy(q).cuda(), out=buf[:ctx.n_dof])
+        ctx.autotune(buf[:ctx.n_dof])
+        steps = []
+        for k in range(args.timestep):
+            n_before = ctx.n_dof
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = ctx.esdirk_step(A, dt, buf, b=b, adapt=out["adapt"], tol=1e-8, dtau_init=dt / 10, dtau_max=dt,
+                                 mode=mode, jv_dtype=jv, m=30, rtol=0.1, max_it=100)
+            e1.record()
+            torch.cuda.synchronize()
+            pm = ctx.p_map()
+            steps.append({"ms": round(e0.elapsed_time(e1), 2), "n_dof_in": n_before, "n_dof_out": ctx.n_dof,
+                          "newton": [s["newton"] for s in st], "gmres": [s["gmres"] for s in st],
+                          "converged": all(s["converged"] for s in st),
+                          "p_hist": [int((pm == p).sum()) for p in range(1, 5)]})
+            if not steps[-1]["converged"]:
+                break
+        out["modes"][f"{mode}_{'f32' if jv == torch.float32 else 'f64'}"] = steps
+        del ctx, buf
+        torch.cuda.empty_cache()
+    print(json.dumps({"timesteps": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,6 +378,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=32, help="elements per direction (default: the workload's 32)")
+    ap.add_argument("--timestep", type=int, default=0,
+                    help="instead of the stage benchmark: this many ESDIRK3 time steps of the NACA 0012 "
+                         "C-grid with p-adaptation after every step, in both product modes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -343,6 +389,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.timestep > 0:
+        return run_timesteps(args)
 
     import torch
     import torch.distributed as dist
