@@ -331,7 +331,8 @@ def run_timesteps(args):
     """ESDIRK3 time steps of the extruded NACA 0012 C-grid (256 x 64 x 24 hexahedra,
     Re 6e4, Ma 0.2, 8 degrees), starting from p = 1 everywhere, with the indicator
     and rebucketing after every step (p in 1..4), in the mixed-precision
-    exact-JVP mode and in the FP64 finite-difference mode; one JSON line with
+    exact-JVP mode (with and without the element-Jacobi preconditioner) and in
+    the FP64 finite-difference mode; one JSON line with
     the per-step times, iteration counts and degree histograms."""
     import torch
     import cases
@@ -341,7 +342,8 @@ def run_timesteps(args):
     dt = 0.005
     out = {"workload": "naca0012_cgrid_256x64x24", "dt": dt, "tableau": "ESDIRK3",
            "adapt": {"nu_max": 0.1, "nu_min": 0.001, "p_min": 1, "p_max": 4, "var": 1}, "modes": {}}
-    for mode, jv in (("exact", torch.float32), ("fd", torch.float64)):
+    for mode, jv, pc in (("exact", torch.float32, True), ("exact", torch.float32, False),
+                         ("fd", torch.float64, False)):
         ctx = FRContext(m, gamma=ph["gamma"], mu=ph["mu"], Pr=ph["Pr"], q_inf=ph["q_inf"], p_min=1, p_max=4)
         buf = torch.zeros(ctx.n_dof_capacity, dtype=torch.float64, device="cuda")
         ctx.pack(torch.from_numpy(q).cuda(), out=buf[:ctx.n_dof])
@@ -353,7 +355,7 @@ def run_timesteps(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             st = ctx.esdirk_step(A, dt, buf, b=b, adapt=out["adapt"], tol=1e-8, dtau_init=dt / 10, dtau_max=dt,
-                                 mode=mode, jv_dtype=jv, m=30, rtol=0.1, max_it=100)
+                                 mode=mode, jv_dtype=jv, m=30, rtol=0.1, max_it=100, precond=pc)
             e1.record()
             torch.cuda.synchronize()
             pm = ctx.p_map()
@@ -363,7 +365,7 @@ def run_timesteps(args):
                           "p_hist": [int((pm == p).sum()) for p in range(1, 5)]})
             if not steps[-1]["converged"]:
                 break
-        out["modes"][f"{mode}_{'f32' if jv == torch.float32 else 'f64'}"] = steps
+        out["modes"][f"{mode}_{'f32' if jv == torch.float32 else 'f64'}{'_element_jacobi' if pc else ''}"] = steps
         del ctx, buf
         torch.cuda.empty_cache()
     print(json.dumps({"timesteps": out}), flush=True)

@@ -178,6 +178,10 @@ typedef struct {
   fr_jv_mode mode;
   fr_prec jv_prec;
   double eps;              /* FD step (FR_JV_FD), paper: 1e-6 */
+  int32_t precond;         /* 1: left element-Jacobi preconditioning with the
+                              blocks of the last fr_precond_build (Sec. 2.3);
+                              the tolerance is then on the preconditioned
+                              residual ||M^-1 (b - A x)||                    */
 } fr_shifted_op;
 
 typedef struct {
@@ -224,6 +228,11 @@ typedef struct {
                               the FP64 residual below it (0: FP64 throughout).
                               Convergence is only declared on an FP64 F, and
                               the last F of the stage is always FP64.        */
+  int32_t precond;         /* left element-Jacobi preconditioning in GMRES;
+                              esdirk_step builds the blocks at q^n with
+                              sigma = 1/(w dt) + 1/dtau_max (Sec. 2.3: once
+                              per physical time step); esdirk_stage uses the
+                              blocks already built                            */
 } fr_newton_opts;
 
 typedef struct {
@@ -274,6 +283,22 @@ typedef struct {
 fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_dev,
                      const fr_adapt_opts* opts, void* q_inout_dev, fr_prec prec,
                      int32_t* perm_out_dev, void* stream);
+
+/* Element-Jacobi preconditioner (Sec. 2.3): the inverses of the diagonal
+ * blocks (one dense block per element, all of its DOFs) of
+ * sigma I - dR/dq(q).  fr_precond_build reads the blocks off the exact FP32
+ * JVP at q64_dev (FP64 state layout) with unit vectors, probing the elements
+ * of one colour of a distance-1 colouring of the face graph together, and
+ * inverts each by Gauss-Jordan elimination with partial pivoting in FP32; it
+ * synchronises `stream`.  Blocks of more than 144 DOFs (3D p >= 3) are not
+ * stored: those elements are preconditioned by 1/sigma.  Storage: the sum of
+ * the squared block sizes in floats.  FR_ERR_NONFINITE on a singular block.
+ * Rebucketing or retuning invalidates the blocks.  fr_precond_apply: z =
+ * M^-1 w (FP64 state layout, z may alias w).  fr_precond_release frees the
+ * block storage. */
+fr_status fr_precond_build(fr_ctx* ctx, const double* q64_dev, double sigma, void* stream);
+fr_status fr_precond_apply(fr_ctx* ctx, const double* w_dev, double* z_dev, void* stream);
+fr_status fr_precond_release(fr_ctx* ctx);
 
 /* One physical time step of an ESDIRK scheme (Eqs. ESDIRK_ns,
  * ESDIRK_conservative): R(q^n), then stages 2..s by esdirk_stage (each stage

@@ -43,7 +43,7 @@ class LayoutInfo(C.Structure):
 
 class ShiftedOp(C.Structure):
     _fields_ = [("sigma", C.c_double), ("q64_dev", C.c_void_p), ("mode", C.c_int),
-                ("jv_prec", C.c_int), ("eps", C.c_double)]
+                ("jv_prec", C.c_int), ("eps", C.c_double), ("precond", C.c_int32)]
 
 
 class GmresOpts(C.Structure):
@@ -62,7 +62,8 @@ class Tableau(C.Structure):
 class NewtonOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("dtau_init", C.c_double), ("dtau_max", C.c_double),
                 ("max_newton", C.c_int32), ("max_halvings", C.c_int32), ("mode", C.c_int),
-                ("jv_prec", C.c_int), ("eps", C.c_double), ("gmres", GmresOpts), ("f32_above", C.c_double)]
+                ("jv_prec", C.c_int), ("eps", C.c_double), ("gmres", GmresOpts), ("f32_above", C.c_double),
+                ("precond", C.c_int32)]
 
 
 class StageStats(C.Structure):
@@ -106,6 +107,9 @@ SIGNATURES = {
                    C.c_void_p, C.c_void_p],
     "esdirk_step": [C.c_void_p, C.POINTER(Tableau), C.c_double, C.c_void_p, C.POINTER(NewtonOpts),
                     C.POINTER(StageStats), C.POINTER(AdaptOpts), C.c_int32, C.c_void_p],
+    "fr_precond_build": [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p],
+    "fr_precond_apply": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "fr_precond_release": [C.c_void_p],
 }
 
 

@@ -213,17 +213,19 @@ class FRContext:
 
     # --------------------------------------------------------------- solvers
     def gmres(self, q64, b, sigma, mode="exact", jv_dtype=torch.float64, eps=1e-6, m=30, rtol=0.1,
-              max_it=100, out=None, reorth=0):
+              max_it=100, out=None, reorth=0, precond=False):
         """Solve (sigma I - dR/dq(q64)) x = b from x = 0 (FP64 Arnoldi).
 
         ``reorth``: 0 one classical Gram-Schmidt pass (the default of the paper's
-        Krylov library), 1 a second pass when needed (DGKS), 2 always two."""
+        Krylov library), 1 a second pass when needed (DGKS), 2 always two.
+        ``precond``: left element-Jacobi preconditioning with the blocks of the
+        last ``precond_build`` (tolerance on the preconditioned residual)."""
         q64, b = _dev(q64, "q64"), _dev(b, "b")
         assert q64.dtype == torch.float64 and b.dtype == torch.float64
         x = torch.empty_like(b) if out is None else _dev(out, "out")
         op = _lib.ShiftedOp(float(sigma), q64.data_ptr(),
                             _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
-                            _jv_prec(jv_dtype), float(eps))
+                            _jv_prec(jv_dtype), float(eps), 1 if precond else 0)
         opts = _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth))
         st = _lib.GmresStats()
         _check(lib().gmres_solve(self.h, C.byref(op), _ptr(b), _ptr(x), C.byref(opts), C.byref(st), _stream()),
@@ -246,11 +248,29 @@ class FRContext:
 
     @staticmethod
     def _newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton, max_halvings,
-                     reorth, f32_above):
+                     reorth, f32_above, precond=False):
         return _lib.NewtonOpts(float(tol), float(dtau_init), float(dtau_max), int(max_newton), int(max_halvings),
                                _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
                                _jv_prec(jv_dtype), float(eps),
-                               _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(f32_above))
+                               _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(f32_above),
+                               1 if precond else 0)
+
+    # ------------------------------------------------ element-Jacobi preconditioner
+    def precond_build(self, q64, sigma):
+        """Element-Jacobi blocks of sigma I - dR/dq(q64), inverted (Sec. 2.3)."""
+        q64 = _dev(q64, "q64")
+        assert q64.dtype == torch.float64
+        _check(lib().fr_precond_build(self.h, _ptr(q64), float(sigma), _stream()), "fr_precond_build")
+
+    def precond_apply(self, w, out=None):
+        """z = M^-1 w with the last built blocks (FP64 state layout)."""
+        w = _dev(w, "w")
+        z = torch.empty_like(w) if out is None else _dev(out, "out")
+        _check(lib().fr_precond_apply(self.h, _ptr(w), _ptr(z), _stream()), "fr_precond_apply")
+        return z
+
+    def precond_release(self):
+        _check(lib().fr_precond_release(self.h), "fr_precond_release")
 
     @staticmethod
     def _stage_dict(st):
@@ -260,7 +280,7 @@ class FRContext:
 
     def esdirk_step(self, A, dt, q, b=None, adapt=None, tol=1e-8, dtau_init=0.05, dtau_max=10.0, mode="exact",
                     jv_dtype=torch.float32, eps=1e-6, m=30, rtol=0.1, max_it=100, max_newton=200,
-                    max_halvings=20, reorth=0, f32_above=0.0):
+                    max_halvings=20, reorth=0, f32_above=0.0, precond=False):
         """One ESDIRK time step in place on ``q`` (FP64 state layout; n_dof_capacity
         values when adapting).  ``adapt``: None, or dict(nu_max, nu_min, p_min,
         p_max, var) to run the indicator and the rebucketing after the step.
@@ -269,7 +289,7 @@ class FRContext:
         assert q.dtype == torch.float64
         tab = self._tableau(A, b)
         o = self._newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton,
-                              max_halvings, reorth, f32_above)
+                              max_halvings, reorth, f32_above, precond)
         stats = (_lib.StageStats * (len(A) - 1))()
         ad = None
         var = 1
@@ -289,7 +309,7 @@ class FRContext:
 
     def esdirk_stage(self, A, stage, dt, qn, Rstages, qi, tol=1e-8, dtau_init=0.05, dtau_max=10.0,
                      mode="exact", jv_dtype=torch.float32, eps=1e-6, m=30, rtol=0.1, max_it=100,
-                     max_newton=200, max_halvings=20, b=None, reorth=0, f32_above=0.0):
+                     max_newton=200, max_halvings=20, b=None, reorth=0, f32_above=0.0, precond=False):
         """Solve ESDIRK stage ``stage`` (1-based, >= 2) in place in ``qi``.
 
         ``A`` is the s x s tableau (list of rows); ``Rstages[j]`` holds R(q^{j+1})
@@ -306,10 +326,8 @@ class FRContext:
         for i in range(S):
             tab.b[i] = float(bb[i])
         ptrs = (C.c_void_p * S)(*[(r.data_ptr() if r is not None else 0) for r in Rstages])
-        o = _lib.NewtonOpts(float(tol), float(dtau_init), float(dtau_max), int(max_newton), int(max_halvings),
-                            _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
-                            _jv_prec(jv_dtype), float(eps),
-                            _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(f32_above))
+        o = self._newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton,
+                              max_halvings, reorth, f32_above, precond)
         st = _lib.StageStats()
         rc = lib().esdirk_stage(self.h, C.byref(tab), int(stage), float(dt), _ptr(qn), ptrs, _ptr(qi),
                                 C.byref(o), C.byref(st), _stream())

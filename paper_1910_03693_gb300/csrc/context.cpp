@@ -178,6 +178,7 @@ void clear_graphs(fr_ctx* c) {
 }
 
 void clear_work_cache(fr_ctx* c) {
+  c->pc_ready = false;   // the layout or the tuning changed: blocks must be rebuilt
   for (auto& kv : c->work_cache) cudaFree(kv.second.first);
   c->work_cache.clear();
   clear_graphs(c);
@@ -559,6 +560,10 @@ static void destroy_impl(fr_ctx* c) {
   if (c->h_jidx) cudaFreeHost(c->h_jidx);
   cudaFree(c->d_krylov);
   cudaFree(c->d_step);
+  cudaFree(c->d_pc);
+  cudaFree(c->d_pc_off);
+  cudaFree(c->d_slot_color);
+  cudaFree(c->d_pc_status);
   for (auto& v : c->d_vec64) cudaFree(v);
   for (auto& v : c->d_vec32) cudaFree(v);
   cudaFree(c->d_red);

@@ -151,6 +151,16 @@ struct fr_ctx {
   // solver workspaces (lazily allocated)
   double* d_krylov = nullptr;
   double* d_step = nullptr;              // esdirk_step: stage residuals, q^n, stage value, eta
+  // element-Jacobi preconditioner (left): inverse blocks in slot order, column-major
+  std::vector<int> color;                // distance-1 colouring of the face graph (element id)
+  int n_colors = 0;
+  float* d_pc = nullptr;
+  int64_t pc_cap = 0;                    // floats in d_pc
+  int64_t* d_pc_off = nullptr;           // [E] block offset of each slot, -1 = no block (1/sigma)
+  int32_t* d_slot_color = nullptr;       // [E] colour of each slot
+  int* d_pc_status = nullptr;
+  bool pc_ready = false;
+  double pc_sigma = 0.0;
   int64_t step_cap = 0;                  // doubles in d_step            // (m+1) * n_dof_cap basis
   int krylov_m = 0;
   double* d_vec64[12] = {};   // 0-2 FD Jv, 3 Jv, 4-5 GMRES, 6-9 ESDIRK, 10-11 adaptation

@@ -38,6 +38,9 @@ fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv,
 fr_status launch_jvp_prepared_neg64(fr_ctx* c, const void* q, const void* v, double* w, fr_prec prec,
                                     cudaStream_t s);
 
+// z = M^-1 (a w + b u) with the element-Jacobi preconditioner (u optional; z may alias w)
+fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s);
+
 // Jv = (R(q + eps v) - R0) / eps in FP64; R0 = R(q) is computed when null.
 fr_status launch_fd_jv(fr_ctx* c, const double* q, const double* v, double* Jv, double eps,
                        const double* R0, cudaStream_t s);

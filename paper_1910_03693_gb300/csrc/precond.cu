@@ -1,0 +1,352 @@
+// Element-Jacobi preconditioner of Sec. 2.3: the inverses of the diagonal
+// blocks of sigma I - dR/dq, one dense block per element (all of its DOFs),
+// applied from the left in GMRES.
+//
+// Build (once per physical time step in the paper):
+//  * the blocks are read off the exact FP32 JVP with unit vectors: elements
+//    of one colour of a distance-1 colouring of the face graph are probed
+//    together (a face neighbour never shares the colour, so the product
+//    restricted to a probed element is that element's own column), one
+//    product per colour and local DOF index;
+//  * each block sigma I - J_ee is inverted in shared memory by Gauss-Jordan
+//    elimination with partial pivoting (FP32), and stored column-major.
+// Blocks larger than kPcMax DOFs (3D p >= 3) do not fit the elimination in
+// shared memory; those elements are preconditioned by 1/sigma.
+// Apply: z_e = M_e^-1 (a w_e + b u_e), FP32 arithmetic on FP64 vectors.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fr_launch.h"
+
+namespace frgb {
+
+constexpr int kPcMax = 144;   // largest block inverted (2 x 144^2 floats in shared memory)
+
+static inline int nsp_host(int nd, int p) { return nd == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1); }
+
+// v[state_off(s) + k] = 1 (and the entry k-1 cleared) for slots of colour `col`
+__global__ void k_pc_unit(float* __restrict__ v, const int64_t* __restrict__ state_off,
+                          const int32_t* __restrict__ slot_color, int slot_begin, int count, int nb, int col,
+                          int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int s = slot_begin + i;
+  if (slot_color[s] != col) return;
+  if (k > 0 && k - 1 < nb) v[state_off[s] + k - 1] = 0.0f;
+  if (k < nb) v[state_off[s] + k] = 1.0f;
+}
+
+// column k of B_s = sigma I - J_ss (column-major, B[k * nb + i]) for slots of colour `col`
+__global__ void k_pc_gather(float* __restrict__ B, const int64_t* __restrict__ pc_off, const float* __restrict__ J,
+                            const int64_t* __restrict__ state_off, const int32_t* __restrict__ slot_color,
+                            int slot_begin, int count, int nb, int col, int k, float sigma) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)count * nb) return;
+  const int i = (int)(t % nb);
+  const int s = slot_begin + (int)(t / nb);
+  if (slot_color[s] != col || pc_off[s] < 0) return;
+  const float val = (i == k ? sigma : 0.0f) - J[state_off[s] + i];
+  B[pc_off[s] + (int64_t)k * nb + i] = val;
+}
+
+// In-place inverse of one nb x nb block per CTA (column-major in global
+// memory) by Gauss-Jordan elimination on [A | I] in shared memory, partial
+// pivoting by rows.  A zero pivot sets *status and leaves the block as is.
+__global__ void k_pc_invert(float* __restrict__ B, const int64_t* __restrict__ pc_off, int slot_begin, int nb,
+                            int* __restrict__ status) {
+  extern __shared__ __align__(16) float sm[];
+  float* M = sm;                    // [nb][2 nb] row-major
+  __shared__ float pv[32];
+  __shared__ int pr[32];
+  __shared__ int piv;
+  const int s = slot_begin + blockIdx.x;
+  const int64_t off = pc_off[s];
+  if (off < 0) return;
+  float* A = B + off;
+  const int w2 = 2 * nb;
+  for (int t = threadIdx.x; t < nb * w2; t += blockDim.x) {
+    const int r = t / w2, cidx = t % w2;
+    M[t] = cidx < nb ? A[(int64_t)cidx * nb + r] : (cidx - nb == r ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int k = 0; k < nb; ++k) {
+    // pivot: the row r >= k with the largest |M[r][k]| (lowest row at a tie)
+    float best = -1.0f;
+    int br = k;
+    for (int r = k + threadIdx.x; r < nb; r += blockDim.x) {
+      const float a = fabsf(M[r * w2 + k]);
+      if (a > best) {
+        best = a;
+        br = r;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int orr = __shfl_down_sync(0xffffffffu, br, o);
+      if (ob > best || (ob == best && orr < br)) {
+        best = ob;
+        br = orr;
+      }
+    }
+    if (lane == 0) {
+      pv[warp] = best;
+      pr[warp] = br;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b0 = pv[0];
+      int r0 = pr[0];
+      for (int q = 1; q < nw; ++q)
+        if (pv[q] > b0 || (pv[q] == b0 && pr[q] < r0)) {
+          b0 = pv[q];
+          r0 = pr[q];
+        }
+      piv = (b0 > 0.0f) ? r0 : -1;
+      if (piv < 0) atomicExch(status, 1);
+    }
+    __syncthreads();
+    if (piv < 0) return;   // singular block: reported through status
+    if (piv != k)
+      for (int cidx = threadIdx.x; cidx < w2; cidx += blockDim.x) {
+        const float a = M[k * w2 + cidx];
+        M[k * w2 + cidx] = M[piv * w2 + cidx];
+        M[piv * w2 + cidx] = a;
+      }
+    __syncthreads();
+    const float inv = 1.0f / M[k * w2 + k];
+    __syncthreads();
+    for (int cidx = threadIdx.x; cidx < w2; cidx += blockDim.x) M[k * w2 + cidx] *= inv;
+    __syncthreads();
+    // eliminate column k from every other row (the factors read before any row changes)
+    for (int t = threadIdx.x; t < nb * w2; t += blockDim.x) {
+      const int r = t / w2, cidx = t % w2;
+      if (r == k || cidx == k) continue;
+      M[t] -= M[r * w2 + k] * M[k * w2 + cidx];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nb; r += blockDim.x)
+      if (r != k) M[r * w2 + k] = 0.0f;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int r = t % nb, cidx = t / nb;   // column-major output
+    A[(int64_t)cidx * nb + r] = M[r * w2 + nb + cidx];
+  }
+}
+
+// z_e = M_e^-1 (a w_e + b u_e); epb elements per CTA, one thread per row.
+// Elements without a stored block (pc_off < 0): z_e = (a w_e + b u_e) / sigma.
+__global__ void k_pc_apply(const float* __restrict__ B, const int64_t* __restrict__ pc_off,
+                           const int64_t* __restrict__ state_off, int slot_begin, int count, int nb, int epb,
+                           double a, const double* w, double b, const double* __restrict__ u, double* z,
+                           double inv_sigma) {
+  extern __shared__ __align__(16) float xs[];   // [epb][nb]
+  const int le = threadIdx.x / nb, i = threadIdx.x % nb;
+  const int e = blockIdx.x * epb + le;
+  const bool valid = le < epb && e < count;
+  int64_t base = 0, off = -1;
+  double x = 0.0;
+  if (valid) {
+    const int s = slot_begin + e;
+    base = state_off[s];
+    off = pc_off[s];
+    x = a * w[base + i] + (u ? b * u[base + i] : 0.0);
+    xs[le * nb + i] = (float)x;
+  }
+  __syncthreads();
+  if (!valid) return;
+  if (off < 0) {
+    z[base + i] = x * inv_sigma;
+    return;
+  }
+  const float* Bc = B + off;
+  const float* xe = xs + le * nb;
+  float acc = 0.0f;
+  for (int j = 0; j < nb; ++j) acc = fmaf(Bc[(int64_t)j * nb + i], xe[j], acc);
+  z[base + i] = (double)acc;
+}
+
+// z = (a w + b u) / sigma on every DOF of a bucket without stored blocks
+__global__ void k_pc_scale(const int64_t* __restrict__ state_off, int slot_begin, int count, int nb, double a,
+                           const double* w, double b, const double* __restrict__ u, double* z, double inv_sigma) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)count * nb) return;
+  const int64_t idx = state_off[slot_begin + (int)(t / nb)] + (int)(t % nb);
+  z[idx] = (a * w[idx] + (u ? b * u[idx] : 0.0)) * inv_sigma;
+}
+
+// Distance-1 colouring of the face graph (greedy in element order), once per context.
+void pc_color(fr_ctx* c) {
+  const int E = c->E, nf = c->nf;
+  c->color.assign(E, -1);
+  int nc = 0;
+  std::vector<char> used;
+  for (int e = 0; e < E; ++e) {
+    used.assign(nc + 1, 0);
+    for (int f = 0; f < nf; ++f) {
+      const int n = c->nbr[(size_t)e * nf + f];
+      if (n >= 0 && n != e && c->color[n] >= 0) used[c->color[n]] = 1;
+    }
+    int col = 0;
+    while (col < nc && used[col]) ++col;
+    c->color[e] = col;
+    nc = std::max(nc, col + 1);
+  }
+  c->n_colors = nc;
+}
+
+}  // namespace frgb
+
+using namespace frgb;
+
+extern "C" {
+
+fr_status fr_precond_build(fr_ctx* c, const double* q64_dev, double sigma, void* stream) {
+  if (!c || !q64_dev || !(sigma > 0.0)) {
+    set_error("fr_precond_build: bad argument");
+    return FR_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int E = c->E, nd = c->nd, nv = c->nv;
+  if (c->color.empty()) pc_color(c);
+  // block offsets per slot (floats), -1 for blocks larger than kPcMax
+  std::vector<int64_t> off(E, -1);
+  std::vector<int32_t> slot_color(E);
+  int64_t total = 0;
+  int kmax = 0;
+  for (const auto& b : c->buckets) {
+    const int nb = nv * nsp_host(nd, b.p);
+    for (int i = 0; i < b.count; ++i) {
+      const int sl = b.slot_begin + i;
+      slot_color[sl] = c->color[c->slot_elem[sl]];
+      if (nb <= kPcMax) {
+        off[sl] = total;
+        total += (int64_t)nb * nb;
+      }
+    }
+    if (nb <= kPcMax) kmax = std::max(kmax, nb);
+  }
+  if (!c->d_pc_off && cudaMalloc(&c->d_pc_off, sizeof(int64_t) * E) != cudaSuccess) return FR_ERR_NOMEM;
+  if (!c->d_slot_color && cudaMalloc(&c->d_slot_color, sizeof(int32_t) * E) != cudaSuccess) return FR_ERR_NOMEM;
+  if (total > c->pc_cap) {
+    cudaFree(c->d_pc);
+    c->d_pc = nullptr;
+    c->pc_cap = 0;
+    if (cudaMalloc(&c->d_pc, sizeof(float) * std::max<int64_t>(total, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("fr_precond_build: block storage allocation failed");
+      return FR_ERR_NOMEM;
+    }
+    c->pc_cap = total;
+  }
+  if (!c->d_pc_status && cudaMalloc(&c->d_pc_status, sizeof(int)) != cudaSuccess) return FR_ERR_NOMEM;
+  cudaMemcpyAsync(c->d_pc_off, off.data(), sizeof(int64_t) * E, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(c->d_slot_color, slot_color.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(c->d_pc_status, 0, sizeof(int), s);
+  c->pc_ready = false;
+  const int64_t n = c->n_dof;
+  float* q32 = vec32(c, 0);
+  float* v32 = vec32(c, 1);
+  float* J32 = vec32(c, 2);
+  if (!q32 || !v32 || !J32) return FR_ERR_NOMEM;
+  vcast_f64_f32(c, q64_dev, q32, n, s);
+  fr_status e = launch_jvp_prepare(c, q32, FR_F32, s);
+  if (e != FR_OK) return e;
+  const float sg = (float)sigma;
+  for (int col = 0; col < c->n_colors && kmax > 0; ++col) {
+    cudaMemsetAsync(v32, 0, sizeof(float) * n, s);
+    for (int k = 0; k < kmax; ++k) {
+      for (const auto& b : c->buckets) {
+        const int nb = nv * nsp_host(nd, b.p);
+        if (nb > kPcMax) continue;
+        FR_LAUNCH(c, "precond_build", s,
+                  k_pc_unit<<<(b.count + 255) / 256, 256, 0, s>>>(v32, c->d_state_off, c->d_slot_color,
+                                                                  b.slot_begin, b.count, nb, col, k));
+      }
+      if ((e = launch_jvp_prepared(c, q32, v32, J32, FR_F32, s)) != FR_OK) return e;
+      for (const auto& b : c->buckets) {
+        const int nb = nv * nsp_host(nd, b.p);
+        if (nb > kPcMax || k >= nb) continue;
+        const int64_t nt = (int64_t)b.count * nb;
+        FR_LAUNCH(c, "precond_build", s,
+                  k_pc_gather<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c->d_pc, c->d_pc_off, J32, c->d_state_off,
+                                                                          c->d_slot_color, b.slot_begin, b.count, nb,
+                                                                          col, k, sg));
+      }
+    }
+  }
+  for (const auto& b : c->buckets) {
+    const int nb = nv * nsp_host(nd, b.p);
+    if (nb > kPcMax || b.count == 0) continue;
+    const size_t smem = sizeof(float) * 2 * (size_t)nb * nb;
+    cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    FR_LAUNCH(c, "precond_build", s,
+              k_pc_invert<<<b.count, 256, smem, s>>>(c->d_pc, c->d_pc_off, b.slot_begin, nb, c->d_pc_status));
+  }
+  int status = 0;
+  cudaMemcpyAsync(&status, c->d_pc_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  fr_status st = cuda_check(cudaStreamSynchronize(s), "fr_precond_build");
+  if (st != FR_OK) return st;
+  if (status) {
+    set_error("fr_precond_build: singular element block");
+    return FR_ERR_NONFINITE;
+  }
+  c->pc_sigma = sigma;
+  c->pc_ready = true;
+  return FR_OK;
+}
+
+fr_status fr_precond_release(fr_ctx* c) {
+  if (!c) return FR_ERR_INVALID;
+  cudaFree(c->d_pc);
+  c->d_pc = nullptr;
+  c->pc_cap = 0;
+  c->pc_ready = false;
+  return FR_OK;
+}
+
+}  // extern "C"
+
+namespace frgb {
+
+// z = M^-1 (a w + b u) on every element (z may alias w)
+fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s) {
+  if (!c->pc_ready) {
+    set_error("element-Jacobi preconditioner not built (fr_precond_build) for the current layout");
+    return FR_ERR_INVALID;
+  }
+  const int nd = c->nd, nv = c->nv;
+  for (const auto& bk : c->buckets) {
+    if (bk.count == 0) continue;
+    const int nb = nv * nsp_host(nd, bk.p);
+    if (nb > kPcMax) {   // no stored blocks in this bucket: 1/sigma
+      const int64_t nt = (int64_t)bk.count * nb;
+      FR_LAUNCH_B(c, "precond_apply", s, 24.0 * nt,
+                  k_pc_scale<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c->d_state_off, bk.slot_begin, bk.count, nb,
+                                                                        a, w, b, u, z, 1.0 / c->pc_sigma));
+      continue;
+    }
+    const int epb = nb >= 256 ? 1 : 256 / nb;
+    const int threads = epb * nb;
+    const unsigned grid = (unsigned)((bk.count + epb - 1) / epb);
+    const double bytes = (double)bk.count * nb * (24.0 + 4.0 * nb);
+    FR_LAUNCH_B(c, "precond_apply", s, bytes,
+                k_pc_apply<<<grid, threads, sizeof(float) * threads, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
+                                                                          bk.slot_begin, bk.count, nb, epb, a, w, b,
+                                                                          u, z, 1.0 / c->pc_sigma));
+  }
+  return cuda_check(cudaGetLastError(), "precond_apply");
+}
+
+}  // namespace frgb
+
+extern "C" fr_status fr_precond_apply(fr_ctx* c, const double* w_dev, double* z_dev, void* stream) {
+  if (!c || !w_dev || !z_dev) {
+    set_error("fr_precond_apply: null argument");
+    return FR_ERR_INVALID;
+  }
+  return precond_apply(c, 1.0, w_dev, 0.0, nullptr, z_dev, (cudaStream_t)stream);
+}

@@ -608,18 +608,25 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   if (!w || !r || !xs) return FR_ERR_NOMEM;
   std::memset(st, 0, sizeof(*st));
   cudaMemsetAsync(x, 0, sizeof(double) * n, s);
-  double beta0 = b_norm;
+  // left preconditioning: GMRES on M^-1 (sigma I - J) x = M^-1 b
+  const bool pc = op->precond != 0;
+  if (pc && !c->pc_ready) {
+    set_error("gmres_solve: preconditioning requested but no element-Jacobi blocks are built for this layout");
+    return FR_ERR_INVALID;
+  }
+  double beta0 = pc ? -1.0 : b_norm;
   fr_status e = FR_OK;
-  if (!(beta0 >= 0.0) && (e = norm2(c, b, n, &beta0, s)) != FR_OK) return e;
+  cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (pc && (e = precond_apply(c, 1.0, r, 0.0, nullptr, r, s)) != FR_OK) return e;
+  if (!(beta0 >= 0.0) && (e = norm2(c, r, n, &beta0, s)) != FR_OK) return e;
   if (!std::isfinite(beta0)) {
     set_error("gmres_solve: non-finite right-hand side");
     return FR_ERR_NONFINITE;
   }
   if (beta0 == 0.0) {
     st->converged = 1;
-    return FR_OK;
+    return cuda_check(cudaStreamSynchronize(s), "gmres");
   }
-  cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
   int it = 0;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(kMaxK), h2(kMaxK);
   double res = beta0;
@@ -671,6 +678,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
         FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(V + (int64_t)j * ld, sh[j], xs, n));
         if ((e = apply_op(c, op, R0, xs, w, s, false)) != FR_OK) return e;
       }
+      if (pc && (e = precond_apply(c, 1.0, w, op->sigma * sh[j], V + (int64_t)j * ld, w, s)) != FR_OK) return e;
       ++it;
       // classical Gram-Schmidt: one pass (reorth 0), a second pass when the
       // first removed more than half of ||w||^2, ||w_new|| < 0.7 ||w|| (DGKS,
@@ -696,7 +704,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       }
       const double hn = std::sqrt(c->h_red[2 * kMaxK]);
       for (int i = 0; i <= j; ++i) H[i * m + j] = h[i] + h2[i];
-      H[j * m + j] += op->sigma;          // Hessenberg of sigma I - J from that of -J
+      if (!pc) H[j * m + j] += op->sigma;   // Hessenberg of sigma I - J from that of -J
       H[(j + 1) * m + j] = hn;
       if (!std::isfinite(hn)) {
         set_error("gmres_solve: non-finite Arnoldi vector");
@@ -743,6 +751,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     if ((e = apply_op(c, op, R0, x, w, s)) != FR_OK) return e;
     cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
     vaxpby(c, -1.0, w, 1.0, r, n, s);
+    if (pc && (e = precond_apply(c, 1.0, r, 0.0, nullptr, r, s)) != FR_OK) return e;
   }
   st->iterations = it;
   st->rel_res = res / beta0;
@@ -858,6 +867,7 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
   op.mode = o->mode;
   op.jv_prec = o->mode == FR_JV_FD ? FR_F64 : o->jv_prec;
   op.eps = o->eps;
+  op.precond = o->precond;
   for (int m = 0; m < o->max_newton; ++m) {
     if (f32 && norm <= o->f32_above * st->norm0) {
       // close enough to the FP32 noise: FP64 from here on, starting with this F
@@ -930,7 +940,13 @@ fr_status esdirk_step(fr_ctx* c, const fr_tableau* tab, double dt, double* q, co
   double* qi = qn + cap;
   double* eta = qi + cap;
   cudaMemcpyAsync(qn, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-  fr_status e = launch_residual(c, qn, Rst[0], FR_F64, s);
+  fr_status e;
+  if (o->precond) {
+    // once per physical time step, at q^n, with the largest shift the stages use (Sec. 2.3)
+    const double sigma_pc = 1.0 / (tab->A[1 * S + 1] * dt) + 1.0 / o->dtau_max;
+    if ((e = fr_precond_build(c, qn, sigma_pc, stream)) != FR_OK) return e;
+  }
+  e = launch_residual(c, qn, Rst[0], FR_F64, s);
   if (e != FR_OK) return e;
   cudaMemcpyAsync(qi, qn, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
   // stage i starts from the value of stage i-1

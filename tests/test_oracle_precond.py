@@ -99,3 +99,19 @@ def test_left_preconditioned_gmres_solves_the_full_system_in_fewer_iterations():
     assert s0["converged"] and s1["converged"]
     assert s1["iterations"] < s0["iterations"]
     assert float((x1 - xref).abs().max()) <= 1e-8 * float(xref.abs().max())
+
+
+def test_blocks_of_selected_elements_equal_the_dense_slices():
+    """The element-by-element construction (unit vectors of one element's DOFs)
+    gives the dense Jacobian's diagonal blocks."""
+    from oracle import precond as P
+    m, q, ph = _system()
+    qt = torch.from_numpy(q)
+    full = P.element_blocks(_CACHE["fr"], qt, 3.0, J=_CACHE["J"])
+    some = P.element_blocks(_CACHE["fr"], qt, 3.0, elements=[1, 6])
+    for e in range(m.n_elem):
+        if e in (1, 6):
+            assert torch.allclose(some[e][2], full[e][2], rtol=0, atol=1e-12 * float(full[e][2].abs().max()))
+        else:
+            assert some[e][2] is None
+
