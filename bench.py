@@ -277,7 +277,8 @@ def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5, names=None):
 def mixed_degree_ops(peak_gbs):
     """Mixed-degree workloads (several buckets): FP64 residual and FP32 exact JVP
     throughput with one launch per degree bucket, with the persistent
-    multi-bucket launch, and after the autotuner.  The cylinder O-grid
+    multi-bucket launch under each element-weight model of its tile order
+    (n_sp (p+1), n_sp, n_sp^2, n_sp^3), and after the autotuner.  The cylinder O-grid
     (98,304 curved hexahedra, p 1..4) and the batch of 32 2D vortex instances
     (p 1..5, 8^2..64^2 quads)."""
     import torch
@@ -290,12 +291,15 @@ def mixed_degree_ops(peak_gbs):
         N = ctx.n_dof
         q64 = ctx.pack(torch.from_numpy(q).cuda())
         row = {"n_dof": N, "n_elem": ctx.n_elem, "buckets": len(set(int(x) for x in ctx.p_map()))}
-        for cfg in ("per_bucket", "multi_bucket", "autotuned"):
+        for cfg in ("per_bucket", "multi_bucket", "multi_w_nsp", "multi_w_nsp2", "multi_w_nsp3", "autotuned"):
             if cfg == "autotuned":
                 t = ctx.autotune(q64)
                 row["autotuned_multi_launch"] = t["multi_launch"]
             else:
-                ctx.set_tuning({"epb": [0] * 42, "multi_launch": cfg == "multi_bucket"})
+                # tiles ordered by the paper's candidate element weights (slot [0][0][1])
+                tab = [0] * 42
+                tab[1] = {"multi_w_nsp": 1, "multi_w_nsp2": 2, "multi_w_nsp3": 3}.get(cfg, 0)
+                ctx.set_tuning({"epb": tab, "multi_launch": cfg != "per_bucket"})
             r = op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=3, names=("residual_f64", "jvp_exact_f32"))
             row[cfg] = {k: {"gdof_s": v["gdof_s"], "ms": v["ms"]} for k, v in r.items()}
         out[label] = row

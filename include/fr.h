@@ -284,6 +284,13 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
                      const fr_adapt_opts* opts, void* q_inout_dev, fr_prec prec,
                      int32_t* perm_out_dev, void* stream);
 
+/* Nodal polynomial filter (Sec. 4, after Fischer and Mullen): every element
+ * of degree p > p_above (paper: 2) becomes (1 - alpha) q + alpha P_{p-1} q,
+ * P_{p-1} the modal truncation to degree p - 1 (paper: alpha = 0.2, applied
+ * to p = 3 with projection onto p = 2).  q_dev: FP64 state layout, in place.
+ * alpha in [0, 1]. */
+fr_status fr_filter(fr_ctx* ctx, double* q_dev, double alpha, int32_t p_above, void* stream);
+
 /* Element-Jacobi preconditioner (Sec. 2.3): the inverses of the diagonal
  * blocks (one dense block per element, all of its DOFs) of
  * sigma I - dR/dq(q).  fr_precond_build reads the blocks off the exact FP32
@@ -335,9 +342,11 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
  * elements exceed 256 threads also falls back to it); the slot P = 0 holds
  * the multi-bucket choice of that precision and kernel (0 default = one launch
  * over all buckets, 1 the same, 2 one launch per bucket), which
- * FR_TUNE_MULTI_LAUNCH enables; and the flags below.  fr_tuning_set with table NULL changes only the
- * flags; elements per CTA outside [0, 256], choices outside [0, 2] or unknown
- * flag bits give FR_ERR_INVALID. */
+ * FR_TUNE_MULTI_LAUNCH enables; slot [0][0][P = 1] holds the element weight
+ * that orders the multi-bucket work table (0 n_sp (p+1), 1 n_sp, 2 n_sp^2,
+ * 3 n_sp^3: the paper's candidate weights, Sec. 3.2); and the flags below.  fr_tuning_set with table NULL changes only the
+ * flags; elements per CTA outside [0, 256], choices outside [0, 2], weight
+ * models outside [0, 3] or unknown flag bits give FR_ERR_INVALID. */
 #define FR_TUNE_MULTI_LAUNCH 1  /* one persistent launch over all degree buckets */
 #define FR_TUNE_GRAPHS 2        /* Arnoldi products replayed from a CUDA graph */
 #define FR_TUNE_DIAG_METRICS 4  /* 3D meshes of axis-aligned affine elements:

@@ -138,3 +138,20 @@ def bucket_order(p) -> np.ndarray:
     """Element ids sorted by (p, id): position -> element id."""
     p = np.asarray(p, dtype=np.int64)
     return np.lexsort((np.arange(len(p)), p))
+
+
+def nodal_filter(fr, q: torch.Tensor, alpha: float = 0.2, p_above: int = 2) -> torch.Tensor:
+    """Nodal polynomial filter (Sec. 4, after Fischer and Mullen): every element
+    of degree p > p_above becomes (1 - alpha) q + alpha P_{p-1} q, P_{p-1} the
+    projection onto the degree p-1 space (the modal truncation above).  The
+    paper states it for p = 3 and projection onto p = 2; for higher degrees the
+    projection is onto p - 1.  Lower-degree elements are unchanged."""
+    parts = fr.to_groups(q)
+    out = {}
+    for p, s in parts.items():
+        if p > p_above:
+            out[p] = (1.0 - alpha) * s + alpha * truncate(s, p, fr.nd)
+        else:
+            out[p] = s
+    return fr.from_groups(out)
+

@@ -110,6 +110,7 @@ SIGNATURES = {
     "fr_precond_build": [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p],
     "fr_precond_apply": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "fr_precond_release": [C.c_void_p],
+    "fr_filter": [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p],
 }
 
 

@@ -269,6 +269,13 @@ class FRContext:
         _check(lib().fr_precond_apply(self.h, _ptr(w), _ptr(z), _stream()), "fr_precond_apply")
         return z
 
+    def filter(self, q, alpha=0.2, p_above=2):
+        """Nodal polynomial filter in place on ``q`` (FP64 state layout)."""
+        q = _dev(q, "q")
+        assert q.dtype == torch.float64
+        _check(lib().fr_filter(self.h, _ptr(q), float(alpha), int(p_above), _stream()), "fr_filter")
+        return q
+
     def precond_release(self):
         _check(lib().fr_precond_release(self.h), "fr_precond_release")
 

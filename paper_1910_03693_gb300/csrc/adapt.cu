@@ -120,6 +120,49 @@ static void launch_indicator(fr_ctx* c, const T* q, int var, double* eta, cudaSt
   }
 }
 
+// Nodal polynomial filter: q <- q - alpha (q - P_{p-1} q) = (1 - alpha) q +
+// alpha P_{p-1} q, one thread per (element, variable): modal coefficients
+// direction by direction, the modes with some index equal to p kept (they are
+// q - P_{p-1} q), back to nodal values, subtracted with weight alpha.
+template <int ND, int P>
+__global__ void k_filter(double* __restrict__ q, const BasisTab<double>* __restrict__ basis, int64_t state_base,
+                         int count, double alpha) {
+  constexpr int NV = ND + 2;
+  constexpr int NSP = ND == 2 ? P * P : P * P * P;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)count * NV) return;
+  const BasisTab<double>& B = basis[P];
+  double* s = q + state_base + tid * NSP;   // element tid / NV, variable tid % NV
+  double c[NSP], t[NSP];
+  for (int k = 0; k < NSP; ++k) c[k] = s[k];
+  for (int d = 0; d < ND; ++d) {
+    const int stride = d == 0 ? 1 : (d == 1 ? P : P * P);
+    for (int k = 0; k < NSP; ++k) {
+      const int id = (k / stride) % P, base = k - id * stride;
+      double acc = 0.0;
+      for (int m = 0; m < P; ++m) acc += B.modal[id][m] * c[base + m * stride];
+      t[k] = acc;
+    }
+    for (int k = 0; k < NSP; ++k) c[k] = t[k];
+  }
+  for (int k = 0; k < NSP; ++k) {
+    const int i0 = k % P, i1 = (k / P) % P, i2 = ND == 3 ? k / (P * P) : 0;
+    const bool top = i0 == P - 1 || i1 == P - 1 || (ND == 3 && i2 == P - 1);
+    if (!top) c[k] = 0.0;
+  }
+  for (int d = 0; d < ND; ++d) {
+    const int stride = d == 0 ? 1 : (d == 1 ? P : P * P);
+    for (int k = 0; k < NSP; ++k) {
+      const int id = (k / stride) % P, base = k - id * stride;
+      double acc = 0.0;
+      for (int m = 0; m < P; ++m) acc += B.nodal[id][m] * c[base + m * stride];
+      t[k] = acc;
+    }
+    for (int k = 0; k < NSP; ++k) c[k] = t[k];
+  }
+  for (int k = 0; k < NSP; ++k) s[k] -= alpha * c[k];
+}
+
 // ---------------------------------------------------------------------------
 // adaptation
 // ---------------------------------------------------------------------------
@@ -437,6 +480,31 @@ fr_status p_rebucket(fr_ctx* c, const double* eta_dev, const double* eta_max_dev
     if (e != FR_OK) return e;
   }
   return cuda_check(cudaGetLastError(), "p_rebucket");
+}
+
+fr_status fr_filter(fr_ctx* c, double* q_dev, double alpha, int32_t p_above, void* stream) {
+  if (!c || !q_dev || !(alpha >= 0.0 && alpha <= 1.0)) {
+    set_error("fr_filter: bad argument");
+    return FR_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (const auto& b : c->buckets) {
+    if (b.p <= p_above || b.count == 0 || alpha == 0.0) continue;
+    const int P = b.p + 1, NSP = c->nd == 2 ? P * P : P * P * P;
+    const int64_t nt = (int64_t)b.count * c->nv;
+    const unsigned grid = (unsigned)((nt + 127) / 128);
+    const double nb = 16.0 * nt * NSP;
+#define FILT_CASE(ND, PP) \
+  case PP: FR_LAUNCH_B(c, "filter", s, nb, k_filter<ND, PP><<<grid, 128, 0, s>>>((double*)q_dev, c->d_basis64, b.state_base, b.count, alpha)); break;
+    if (c->nd == 2) {
+      switch (P) { FILT_CASE(2, 2) FILT_CASE(2, 3) FILT_CASE(2, 4) FILT_CASE(2, 5) FILT_CASE(2, 6) }
+    } else {
+      switch (P) { FILT_CASE(3, 2) FILT_CASE(3, 3) FILT_CASE(3, 4) FILT_CASE(3, 5) FILT_CASE(3, 6) }
+    }
+#undef FILT_CASE
+    (void)NSP;
+  }
+  return cuda_check(cudaGetLastError(), "fr_filter");
 }
 
 fr_status fr_esdirk_tableau(int32_t order, fr_tableau* t) {

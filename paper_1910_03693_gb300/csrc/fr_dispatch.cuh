@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
@@ -87,8 +88,21 @@ static inline unsigned sm_count(fr_ctx* c) {
   return n > 0 ? (unsigned)n : 152u;
 }
 
+// Element weight of the multi-bucket work table (tuning slot [0][0][P = 1]):
+// 0 n_sp (p+1) (the default), 1 n_sp, 2 n_sp^2, 3 n_sp^3 -- the paper's
+// candidate element weights for repartitioning (Sec. 3.2), reused as CTA
+// work weights for the order in which the persistent launch takes tiles.
+static inline double element_weight(int model, int nsp, int P) {
+  switch (model) {
+    case 1: return (double)nsp;
+    case 2: return (double)nsp * nsp;
+    case 3: return (double)nsp * nsp * nsp;
+    default: return (double)nsp * P;
+  }
+}
+
 // Work table of the multi-bucket launch: tiles of epb elements, ordered by
-// decreasing cost n_sp (p+1) per tile (higher degrees first), bucket order.
+// decreasing weight per tile (higher degrees first), bucket order.
 static const WorkItem* work_items(fr_ctx* c, int prec, int kind, int* n_items) {
   const int key = prec * 16 + kind;
   for (auto& kv : c->work_cache)
@@ -102,7 +116,7 @@ static const WorkItem* work_items(fr_ctx* c, int prec, int kind, int* n_items) {
     const int P = b.p + 1, e = epb_for(c, prec, kind, P);
     for (int f = 0; f < b.count; f += e) {
       const int ne = std::min(e, b.count - f);
-      items.push_back({(double)ne * nsp_of(c->nd, P) * P, WorkItem{(int32_t)bi, (int32_t)f}});
+      items.push_back({ne * element_weight(c->epb_tab[0][0][1], nsp_of(c->nd, P), P), WorkItem{(int32_t)bi, (int32_t)f}});
     }
   }
   std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
@@ -594,6 +608,22 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
     }
   }
   c->multi_launch = multi_saved;
+  // keep the tuned table only if the residual plus the JVP beat the default
+  // configuration end to end (the per-kernel timings above see each group alone)
+  auto both = [&] {
+    residual_impl<T, ND, VISC, DIAG>(c, q, scratch, s);
+    jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s);
+  };
+  int tuned[3][kPM + 1];
+  std::memcpy(tuned, c->epb_tab[prec], sizeof(tuned));
+  clear_work_cache(c);
+  const float t_tuned = time_best(reps + 2, s, both);
+  std::memset(c->epb_tab[prec], 0, sizeof(tuned));
+  for (int k = 0; k < 3; ++k) c->epb_tab[prec][k][1] = tuned[k][1];   // the weight model is not tuned
+  clear_work_cache(c);
+  const float t_default = time_best(reps + 2, s, both);
+  if (t_tuned <= t_default) std::memcpy(c->epb_tab[prec], tuned, sizeof(tuned));
+  clear_work_cache(c);
 }
 
 // One operation for one (dimension, viscosity, metric) configuration.

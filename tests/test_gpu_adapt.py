@@ -94,3 +94,21 @@ def test_rebucket_fp32_and_repeat(built):
         assert np.array_equal(ctx.p_map(), p_ref.astype(np.int8))
     got = ctx.unpack(buf[:ctx.n_dof]).cpu().numpy()
     assert np.abs(got - qq.numpy()).max() <= 2e-6 * np.abs(qq.numpy()).max()
+
+
+@pytest.mark.parametrize("name", ["vortex2d_mixed_p1-4", "box_curved_mixed_p1-3", "cylinder_4x12x2_mixed",
+                                  "vortex_batch_5"])
+def test_nodal_filter_matches_oracle(built, name):
+    """The nodal filter (alpha 0.2, degrees above 2) against the oracle's, FP64
+    to 1e-13 of max|q|; elements of degree <= 2 bit-identical."""
+    from oracle import adapt as OA
+    from helpers import small_workloads
+    m, q, ph = small_workloads()[name]
+    fr = oracle_fr(m, ph)
+    ref = OA.nodal_filter(fr, torch.from_numpy(q), 0.2, 2).numpy()
+    ctx = gpu_ctx(m, ph)
+    qs = ctx.pack(torch.from_numpy(q).cuda())
+    got = ctx.unpack(ctx.filter(qs, 0.2, 2)).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(q).max()
+    low = np.repeat(m.p <= 2, [(int(p) + 1) ** m.nd * m.nv for p in m.p])
+    assert np.array_equal(got[low], q[low])

@@ -224,3 +224,29 @@ def test_diagonal_metric_kernels_match_general(built, works, name):
             assert torch.equal(x, y)
         else:
             assert _close(x, y), float((x - y).abs().max())
+
+
+@pytest.mark.parametrize("name", ["cylinder_4x12x2_mixed", "vortex_batch_5"])
+def test_work_weight_models_do_not_change_results(built, works, name):
+    """The element weight that orders the multi-bucket work table (n_sp (p+1),
+    n_sp, n_sp^2, n_sp^3) only changes which CTA takes which tile: residual and
+    JVP are bit-identical."""
+    m, q, ph = works[name]
+    qg = generic_state(q)
+    v = cases.uniform(309, q.size) - 0.5
+    ctx = gpu_ctx(m, ph)
+    qd, vd = torch.from_numpy(qg).cuda(), torch.from_numpy(v).cuda()
+    ref = None
+    for model in range(4):
+        tab = [0] * 42
+        tab[1] = model
+        ctx.set_tuning({"epb": tab, "multi_launch": True})
+        got = _ops(ctx, qd, vd)
+        if ref is None:
+            ref = got
+        for x, y in zip(got, ref):
+            assert torch.equal(x, y)
+    with pytest.raises(Exception):
+        bad = [0] * 42
+        bad[1] = 4
+        ctx.set_tuning({"epb": bad})

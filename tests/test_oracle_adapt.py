@@ -129,3 +129,46 @@ def test_adapt_state_round_trip_on_vortex():
     q = torch.from_numpy(q)
     back = adapt.transfer(fr3, adapt.transfer(fr2, q, fr3), fr2)
     assert torch.allclose(back, q, atol=1e-12)
+
+
+def _filter_mesh():
+    """Affine 3D box (|J| constant per element) with degrees 1..4."""
+    m = cases.periodic_box(3, 3, 0.0, 1.0, 2)
+    m = m.with_p(np.array([1, 2, 3, 4, 3, 2, 1, 4, 3] * 3, dtype=np.int8))
+    return m
+
+
+def test_nodal_filter_pins():
+    """Elements of degree <= 2 are untouched; a state of degree p - 1 in every
+    element is a fixed point; the element integrals (weights w |J|) of every
+    variable are kept (the dropped Legendre modes integrate to zero on affine
+    elements); a single top mode is scaled by 1 - alpha."""
+    m = _filter_mesh()
+    fr = _fr(m)
+    q = torch.from_numpy(cases.random_state(m, 61))
+    qf = adapt.nodal_filter(fr, q, alpha=0.2, p_above=2)
+    parts, fparts = fr.to_groups(q), fr.to_groups(qf)
+    for p in parts:
+        if p <= 2:
+            assert torch.equal(parts[p], fparts[p])
+        else:
+            assert float((parts[p] - fparts[p]).abs().max()) > 0
+    W = fr.quadrature_weights()
+    Q, QF, WW = (t.reshape(-1, fr.nv) for t in (q, qf, W))
+    off = fr.offsets // fr.nv
+    for e in range(m.n_elem):
+        a, b = int(off[e]), int(off[e + 1])
+        assert torch.allclose((WW[a:b] * QF[a:b]).sum(0), (WW[a:b] * Q[a:b]).sum(0), rtol=0, atol=1e-13)
+    # degree p - 1 polynomials: the truncation of any state, filtered again, stays put
+    low = {p: (adapt.truncate(s, p, 3) if p > 2 else s) for p, s in parts.items()}
+    ql = fr.from_groups(low)
+    assert torch.allclose(adapt.nodal_filter(fr, ql, 0.2, 2), ql, rtol=0, atol=1e-13 * float(ql.abs().max()))
+    # a pure top mode P_p(xi) P_0(eta) P_p(zeta) is scaled by 1 - alpha
+    from oracle.basis import basis as B1
+    for p in (3, 4):
+        x = B1(p).x
+        lp = legendre(p, x)[0]
+        mode = lp[:, None, None] * lp[None, None, :] * torch.ones(1, p + 1, 1, dtype=torch.float64)
+        s = mode.expand(2, fr.nv, p + 1, p + 1, p + 1).clone()
+        f = (1.0 - 0.3) * s + 0.3 * adapt.truncate(s, p, 3)
+        assert torch.allclose(f, 0.7 * s, rtol=0, atol=1e-13)
