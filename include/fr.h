@@ -284,7 +284,7 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
                      const fr_adapt_opts* opts, void* q_inout_dev, fr_prec prec,
                      int32_t* perm_out_dev, void* stream);
 
-/* Nodal polynomial filter (Sec. 4, after Fischer and Mullen): every element
+/* Nodal polynomial filter (Sec. 4.2, after Fischer and Mullen): every element
  * of degree p > p_above (paper: 2) becomes (1 - alpha) q + alpha P_{p-1} q,
  * P_{p-1} the modal truncation to degree p - 1 (paper: alpha = 0.2, applied
  * to p = 3 with projection onto p = 2).  q_dev: FP64 state layout, in place.

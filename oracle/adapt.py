@@ -141,7 +141,7 @@ def bucket_order(p) -> np.ndarray:
 
 
 def nodal_filter(fr, q: torch.Tensor, alpha: float = 0.2, p_above: int = 2) -> torch.Tensor:
-    """Nodal polynomial filter (Sec. 4, after Fischer and Mullen): every element
+    """Nodal polynomial filter (Sec. 4.2, after Fischer and Mullen): every element
     of degree p > p_above becomes (1 - alpha) q + alpha P_{p-1} q, P_{p-1} the
     projection onto the degree p-1 space (the modal truncation above).  The
     paper states it for p = 3 and projection onto p = 2; for higher degrees the
