@@ -322,7 +322,7 @@ class FRContext:
         ``A`` is the s x s tableau (list of rows); ``Rstages[j]`` holds R(q^{j+1})
         for j < stage-1 and receives R(q^stage) in slot stage-1 when not None.
         ``f32_above`` > 0 (exact mode): F from the FP32 residual while
-        ||F||/||F0|| is above it, FP64 below; convergence is judged in FP64."""
+        ||F||/||F0|| is above it, FP64 below; convergence is decided in FP64."""
         S = len(A)
         tab = _lib.Tableau()
         tab.s = S
