@@ -570,6 +570,10 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     set_error("gmres_solve: need 1 <= m <= 63, max_it >= 1, rtol > 0, reorth in {0, 1, 2}");
     return FR_ERR_INVALID;
   }
+  if (op->precond && !c->pc_ready) {
+    set_error("gmres_solve: preconditioning requested but no element-Jacobi blocks are built for this layout");
+    return FR_ERR_INVALID;
+  }
   if (ensure_red(c) != FR_OK) return FR_ERR_NOMEM;
   if (!c->d_krylov || c->krylov_m < m) {
     cudaFree(c->d_krylov);
@@ -610,10 +614,6 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   cudaMemsetAsync(x, 0, sizeof(double) * n, s);
   // left preconditioning: GMRES on M^-1 (sigma I - J) x = M^-1 b
   const bool pc = op->precond != 0;
-  if (pc && !c->pc_ready) {
-    set_error("gmres_solve: preconditioning requested but no element-Jacobi blocks are built for this layout");
-    return FR_ERR_INVALID;
-  }
   double beta0 = pc ? -1.0 : b_norm;
   fr_status e = FR_OK;
   cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
