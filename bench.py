@@ -48,6 +48,19 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def _cpu_model():
+    """Model name of the host CPU (for the oracle baseline's context)."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part", "processor name")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def kernel_roofline(name, launches, ms, nbytes, nflops, hbm_gbs):
     """Bound, achieved, peak and fraction of one kernel from its algorithmic bytes
     and operations: the roofline it reaches first decides the bound."""
@@ -543,7 +556,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, thr, dt = oracle_sample_throughput(args.n)
-        line["cpu_baseline"] = {"value": g, "unit": "GDOF/s", "cores": thr, "kind": "oracle",
+        line["cpu_baseline"] = {"value": g, "unit": "GDOF/s", "cores": thr, "kind": "oracle", "cpu": _cpu_model(),
                                 "sample": f"one FP64 residual + one exact JVP of the full workload ({N} DOF), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
