@@ -37,6 +37,10 @@
  *    mortar interpolation and projection) rounded to bfloat16, 8 significant
  *    bits: the trial of BF16 operators.  Pack, unpack and the indicator
  *    treat it as FR_F32.
+ *    FR_DF (fr_residual and the stage's early Newton iterates only): FP64
+ *    buffers in the FP64 state layout, evaluated in double-float arithmetic
+ *    (each value an unevaluated sum of two FP32 numbers, about 48
+ *    significant bits, error-free transformations on the FP32 pipe).
  */
 #ifndef FR_H
 #define FR_H
@@ -58,7 +62,7 @@ typedef enum {
   FR_ERR_TIMEOUT = -6         /* a bounded device-side wait gave up               */
 } fr_status;
 
-typedef enum { FR_F64 = 0, FR_F32 = 1, FR_BF16OP = 2 } fr_prec;
+typedef enum { FR_F64 = 0, FR_F32 = 1, FR_BF16OP = 2, FR_DF = 3 } fr_prec;
 typedef enum { FR_JV_FD = 0, FR_JV_EXACT = 1 } fr_jv_mode;
 
 /* Boundary kinds used in fr_mesh_desc.nbr (negative values). */
@@ -223,16 +227,19 @@ typedef struct {
   fr_prec jv_prec;         /* precision of the exact JVP                      */
   double eps;
   fr_gmres_opts gmres;
-  double f32_above;        /* exact mode: F uses the FP32 residual while the
-                              last ||F|| / ||F(q^{0})|| is above this value,
-                              the FP64 residual below it (0: FP64 throughout).
-                              Convergence is only declared on an FP64 F, and
-                              the last F of the stage is always FP64.        */
+  double low_above;        /* exact mode: F uses the residual in precision
+                              low_prec while the last ||F|| / ||F(q^{0})|| is
+                              above this value, the FP64 residual below it (0:
+                              FP64 throughout).  Convergence is only declared
+                              on an FP64 F, and the last F of the stage is
+                              always FP64.                                    */
   int32_t precond;         /* left element-Jacobi preconditioning in GMRES;
                               esdirk_step builds the blocks at q^n with
                               sigma = 1/(w dt) + 1/dtau_max (Sec. 2.3: once
                               per physical time step); esdirk_stage uses the
                               blocks already built                            */
+  fr_prec low_prec;        /* FR_DF (double-float) or FR_F32; read only when
+                              low_above > 0                                   */
 } fr_newton_opts;
 
 typedef struct {
@@ -241,7 +248,7 @@ typedef struct {
   int32_t halvings;
   int32_t converged;
   double norm0, norm_final;
-  int32_t f32_evaluations; /* stage residuals evaluated in FP32              */
+  int32_t low_evaluations; /* stage residuals evaluated in low_prec          */
   int32_t f64_evaluations; /* stage residuals evaluated in FP64              */
 } fr_stage_stats;
 
@@ -290,6 +297,15 @@ fr_status p_rebucket(fr_ctx* ctx, const double* eta_dev, const double* eta_max_d
  * to p = 3 with projection onto p = 2).  q_dev: FP64 state layout, in place.
  * alpha in [0, 1]. */
 fr_status fr_filter(fr_ctx* ctx, double* q_dev, double alpha, int32_t p_above, void* stream);
+
+/* Double-float arithmetic of FR_DF, elementwise on device arrays of n FP64
+ * values: a, b, c are converted to double-float (nearest FP32 plus the FP32
+ * rounding of the remainder), op 0 a + b, 1 a - b, 2 a * b, 3 a * b + c,
+ * 4 a / b, 5 sqrt(a), and the result is written as the FP64 value of its
+ * two parts.  b is read for ops 0-4, c for op 3 (else they may be null).
+ * Exposed for checking the arithmetic against exact rational results. */
+fr_status fr_dfloat_eval(int32_t op, const double* a, const double* b, const double* c, double* out, int64_t n,
+                         void* stream);
 
 /* Element-Jacobi preconditioner (Sec. 2.3): the inverses of the diagonal
  * blocks (one dense block per element, all of its DOFs) of

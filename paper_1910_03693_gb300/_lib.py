@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfrgb.so")
 
 FR_OK = 0
-FR_F64, FR_F32, FR_BF16OP = 0, 1, 2
+FR_F64, FR_F32, FR_BF16OP, FR_DF = 0, 1, 2, 3
 FR_JV_FD, FR_JV_EXACT = 0, 1
 STATUS = {0: "FR_OK", -1: "FR_ERR_INVALID", -2: "FR_ERR_CUDA", -3: "FR_ERR_NOMEM",
           -4: "FR_ERR_NOT_CONVERGED", -5: "FR_ERR_NONFINITE", -6: "FR_ERR_TIMEOUT"}
@@ -62,15 +62,15 @@ class Tableau(C.Structure):
 class NewtonOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("dtau_init", C.c_double), ("dtau_max", C.c_double),
                 ("max_newton", C.c_int32), ("max_halvings", C.c_int32), ("mode", C.c_int),
-                ("jv_prec", C.c_int), ("eps", C.c_double), ("gmres", GmresOpts), ("f32_above", C.c_double),
-                ("precond", C.c_int32)]
+                ("jv_prec", C.c_int), ("eps", C.c_double), ("gmres", GmresOpts), ("low_above", C.c_double),
+                ("precond", C.c_int32), ("low_prec", C.c_int)]
 
 
 class StageStats(C.Structure):
     _fields_ = [("newton_iterations", C.c_int32), ("gmres_iterations", C.c_int32),
                 ("halvings", C.c_int32), ("converged", C.c_int32),
                 ("norm0", C.c_double), ("norm_final", C.c_double),
-                ("f32_evaluations", C.c_int32), ("f64_evaluations", C.c_int32)]
+                ("low_evaluations", C.c_int32), ("f64_evaluations", C.c_int32)]
 
 
 class AdaptOpts(C.Structure):
@@ -111,6 +111,7 @@ SIGNATURES = {
     "fr_precond_apply": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "fr_precond_release": [C.c_void_p],
     "fr_filter": [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p],
+    "fr_dfloat_eval": [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
 }
 
 

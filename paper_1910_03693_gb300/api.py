@@ -50,6 +50,14 @@ def _prec(t, bf16_operators=False):
     raise TypeError(f"unsupported dtype {t.dtype}" + (" (bfloat16 operators need FP32 buffers)" if bf16_operators else ""))
 
 
+def _low_prec(name):
+    if name == "df":
+        return _lib.FR_DF
+    if name == "f32":
+        return _lib.FR_F32
+    raise ValueError(f"low-precision residual must be 'df' or 'f32', not {name!r}")
+
+
 def _jv_prec(jv_dtype):
     """torch.float64 / torch.float32, or "bf16op" for FP32 products with bfloat16 operators."""
     if isinstance(jv_dtype, str):
@@ -150,12 +158,20 @@ class FRContext:
         return out
 
     # ---------------------------------------------------------------- operators
-    def residual(self, q, out=None, bf16_operators=False):
+    def residual(self, q, out=None, bf16_operators=False, double_float=False):
         """R(q) in the precision of q; ``bf16_operators`` (FP32 q): the operator
-        matrices rounded to bfloat16 (the BF16-operator trial)."""
+        matrices rounded to bfloat16 (the BF16-operator trial);
+        ``double_float`` (FP64 q): FP64 in and out, evaluated in double-float
+        arithmetic (pairs of FP32 values, about 48 significant bits)."""
         q = _dev(q, "q")
         out = torch.empty_like(q) if out is None else _dev(out, "out")
-        _check(lib().fr_residual(self.h, _ptr(q), _ptr(out), _prec(q, bf16_operators), _stream()), "fr_residual")
+        if double_float:
+            if q.dtype != torch.float64:
+                raise TypeError("double-float evaluation takes and returns FP64 buffers")
+            prec = _lib.FR_DF
+        else:
+            prec = _prec(q, bf16_operators)
+        _check(lib().fr_residual(self.h, _ptr(q), _ptr(out), prec, _stream()), "fr_residual")
         return out
 
     def jvp(self, q, v, out=None, mode="exact", eps=1e-6, bf16_operators=False):
@@ -248,12 +264,12 @@ class FRContext:
 
     @staticmethod
     def _newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton, max_halvings,
-                     reorth, f32_above, precond=False):
+                     reorth, low_above, precond=False, low_precision="df"):
         return _lib.NewtonOpts(float(tol), float(dtau_init), float(dtau_max), int(max_newton), int(max_halvings),
                                _lib.FR_JV_EXACT if mode == "exact" else _lib.FR_JV_FD,
                                _jv_prec(jv_dtype), float(eps),
-                               _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(f32_above),
-                               1 if precond else 0)
+                               _lib.GmresOpts(int(m), float(rtol), int(max_it), int(reorth)), float(low_above),
+                               1 if precond else 0, _low_prec(low_precision))
 
     # ------------------------------------------------ element-Jacobi preconditioner
     def precond_build(self, q64, sigma):
@@ -283,11 +299,11 @@ class FRContext:
     def _stage_dict(st):
         return dict(newton=st.newton_iterations, gmres=st.gmres_iterations, halvings=st.halvings,
                     converged=bool(st.converged), norm0=st.norm0, norm_final=st.norm_final,
-                    f32_evaluations=st.f32_evaluations, f64_evaluations=st.f64_evaluations)
+                    low_evaluations=st.low_evaluations, f64_evaluations=st.f64_evaluations)
 
     def esdirk_step(self, A, dt, q, b=None, adapt=None, tol=1e-8, dtau_init=0.05, dtau_max=10.0, mode="exact",
                     jv_dtype=torch.float32, eps=1e-6, m=30, rtol=0.1, max_it=100, max_newton=200,
-                    max_halvings=20, reorth=0, f32_above=0.0, precond=False):
+                    max_halvings=20, reorth=0, low_above=0.0, low_precision="df", precond=False):
         """One ESDIRK time step in place on ``q`` (FP64 state layout; n_dof_capacity
         values when adapting).  ``adapt``: None, or dict(nu_max, nu_min, p_min,
         p_max, var) to run the indicator and the rebucketing after the step.
@@ -296,7 +312,7 @@ class FRContext:
         assert q.dtype == torch.float64
         tab = self._tableau(A, b)
         o = self._newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton,
-                              max_halvings, reorth, f32_above, precond)
+                              max_halvings, reorth, low_above, precond, low_precision)
         stats = (_lib.StageStats * (len(A) - 1))()
         ad = None
         var = 1
@@ -316,13 +332,15 @@ class FRContext:
 
     def esdirk_stage(self, A, stage, dt, qn, Rstages, qi, tol=1e-8, dtau_init=0.05, dtau_max=10.0,
                      mode="exact", jv_dtype=torch.float32, eps=1e-6, m=30, rtol=0.1, max_it=100,
-                     max_newton=200, max_halvings=20, b=None, reorth=0, f32_above=0.0, precond=False):
+                     max_newton=200, max_halvings=20, b=None, reorth=0, low_above=0.0, low_precision="df",
+                     precond=False):
         """Solve ESDIRK stage ``stage`` (1-based, >= 2) in place in ``qi``.
 
         ``A`` is the s x s tableau (list of rows); ``Rstages[j]`` holds R(q^{j+1})
         for j < stage-1 and receives R(q^stage) in slot stage-1 when not None.
-        ``f32_above`` > 0 (exact mode): F from the FP32 residual while
-        ||F||/||F0|| is above it, FP64 below; convergence is decided in FP64."""
+        ``low_above`` > 0 (exact mode): F from the residual in
+        ``low_precision`` ("df" double-float, or "f32") while ||F||/||F0|| is
+        above it, FP64 below; convergence is decided in FP64."""
         S = len(A)
         tab = _lib.Tableau()
         tab.s = S
@@ -334,7 +352,7 @@ class FRContext:
             tab.b[i] = float(bb[i])
         ptrs = (C.c_void_p * S)(*[(r.data_ptr() if r is not None else 0) for r in Rstages])
         o = self._newton_opts(tol, dtau_init, dtau_max, mode, jv_dtype, eps, m, rtol, max_it, max_newton,
-                              max_halvings, reorth, f32_above, precond)
+                              max_halvings, reorth, low_above, precond, low_precision)
         st = _lib.StageStats()
         rc = lib().esdirk_stage(self.h, C.byref(tab), int(stage), float(dt), _ptr(qn), ptrs, _ptr(qi),
                                 C.byref(o), C.byref(st), _stream())
@@ -342,7 +360,7 @@ class FRContext:
             raise FRError("esdirk_stage", rc)
         return dict(newton=st.newton_iterations, gmres=st.gmres_iterations, halvings=st.halvings,
                     converged=bool(st.converged), norm0=st.norm0, norm_final=st.norm_final,
-                    f32_evaluations=st.f32_evaluations, f64_evaluations=st.f64_evaluations)
+                    low_evaluations=st.low_evaluations, f64_evaluations=st.f64_evaluations)
 
 
     # ------------------------------------------------------------ adaptation
@@ -368,6 +386,20 @@ class FRContext:
                                 _stream()), "p_rebucket")
         self.refresh_layout()
         return perm
+
+
+DFLOAT_OPS = {"add": 0, "sub": 1, "mul": 2, "fma": 3, "div": 4, "sqrt": 5}
+
+
+def dfloat_eval(op, a, b=None, c=None):
+    """One double-float operation of the FR_DF arithmetic, elementwise on FP64
+    CUDA tensors: "add", "sub", "mul", "fma" (a * b + c), "div", "sqrt"."""
+    a = _dev(a, "a")
+    out = torch.empty_like(a)
+    ptr = lambda t: _ptr(_dev(t, "operand")) if t is not None else None
+    _check(lib().fr_dfloat_eval(DFLOAT_OPS[op], _ptr(a), ptr(b), ptr(c), _ptr(out), a.numel(), _stream()),
+           "fr_dfloat_eval")
+    return out
 
 
 def esdirk_tableau(order=3):

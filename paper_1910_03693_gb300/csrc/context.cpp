@@ -539,7 +539,13 @@ static void destroy_impl(fr_ctx* c) {
     cudaFree(c->d_gvol32[p]);
     cudaFree(c->d_gface64[p]);
     cudaFree(c->d_gface32[p]);
+    cudaFree(c->d_gvol_df[p]);
+    cudaFree(c->d_gface_df[p]);
   }
+  cudaFree(c->d_basis_df);
+  cudaFree(c->d_mortar_df);
+  cudaFree(c->d_gaff_df);
+  cudaFree(c->d_qdf);
   cudaFree(c->d_trace_q);
   cudaFree(c->d_trace_v);
   cudaFree(c->d_fout);

@@ -19,15 +19,33 @@ static inline int ipow(int b, int e) {
   return r;
 }
 
+// Tables of the arithmetic type T: FP64, FP32 (or the bfloat16-rounded FP32
+// operators when c->bf16op), double-float (created on first use).
 template <typename T>
 inline BasisTab<T>* basis_ptr(fr_ctx* c) {
+  if (is_dfloat<T>::value) return (BasisTab<T>*)c->d_basis_df;
   return std::is_same<T, double>::value ? (BasisTab<T>*)c->d_basis64
                                         : (BasisTab<T>*)(c->bf16op ? c->d_basis16 : c->d_basis32);
 }
 template <typename T>
 inline MortarTab<T>* mortar_ptr(fr_ctx* c, int Pm, int Ps) {
+  if (is_dfloat<T>::value) return (MortarTab<T>*)c->d_mortar_df + Pm * (kPM + 1) + Ps;
   return std::is_same<T, double>::value ? (MortarTab<T>*)(c->d_mortar64 + Pm * (kPM + 1) + Ps)
                                         : (MortarTab<T>*)((c->bf16op ? c->d_mortar16 : c->d_mortar32) + Pm * (kPM + 1) + Ps);
+}
+template <typename T>
+inline const T* typed(const double* a64, const float* a32, const void* adf) {
+  if (is_dfloat<T>::value) return (const T*)adf;
+  return std::is_same<T, double>::value ? (const T*)a64 : (const T*)a32;
+}
+
+// row of the launch-configuration table: FP64 and double-float kernels share
+// the FP64 row (same operand size and shared-memory footprint)
+template <typename T>
+constexpr int prec_row() { return std::is_same<T, float>::value ? 1 : 0; }
+template <typename T>
+inline const char* kname(const char* f64, const char* f32, const char* df) {
+  return is_dfloat<T>::value ? df : (std::is_same<T, double>::value ? f64 : f32);
 }
 
 template <typename T>
@@ -35,7 +53,7 @@ inline GeoView<T> geo_view(fr_ctx* c, int p) {
   GeoView<T> g{};
   const int nd = c->nd, NKV = geo_nk_vol(nd), NKF = geo_nk_face(nd), P = p + 1;
   const int NSP = ipow(P, nd), NFP = ipow(P, nd - 1);
-  const T* aff = std::is_same<T, double>::value ? (const T*)c->d_gaff64 : (const T*)c->d_gaff32;
+  const T* aff = typed<T>(c->d_gaff64, c->d_gaff32, c->d_gaff_df);
   if (c->affine) {
     g.vol = aff;
     g.ves = NKF;
@@ -47,11 +65,11 @@ inline GeoView<T> geo_view(fr_ctx* c, int p) {
     g.fks = 1;
     g.fps = 0;
   } else {
-    g.vol = std::is_same<T, double>::value ? (const T*)c->d_gvol64[p] : (const T*)c->d_gvol32[p];
+    g.vol = typed<T>(c->d_gvol64[p], c->d_gvol32[p], c->d_gvol_df[p]);
     g.ves = (int64_t)NKV * NSP;
     g.vks = NSP;
     g.vps = 1;
-    g.face = std::is_same<T, double>::value ? (const T*)c->d_gface64[p] : (const T*)c->d_gface32[p];
+    g.face = typed<T>(c->d_gface64[p], c->d_gface32[p], c->d_gface_df[p]);
     g.fes = (int64_t)c->nf * NKF * NFP;
     g.ffs = NKF * NFP;
     g.fks = NFP;
@@ -170,14 +188,14 @@ static TraceArgs<T> trace_args(fr_ctx* c, const Bucket& b, const T* q, T* trace)
 // traces of every bucket: one launch per bucket, or one multi-bucket launch
 template <typename T, int ND, bool VISC, bool DIAG = false>
 static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
-  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const int prec = prec_row<T>();
   double nb = 0.0, nfl = 0.0;
   for (const auto& b : c->buckets) {
     const int P = b.p + 1;
-    nb += (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
+    nb += (double)b.count * values_trace(ND, P, VISC) * sizeof(T);
     nfl += (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC, DIAG);
   }
-  const char* name = sizeof(T) == 8 ? "trace_f64" : "trace_f32";
+  const char* name = kname<T>("trace_f64", "trace_f32", "trace_df");
   int n_items = 0;
   const WorkItem* items = use_multi(c, prec, 0) ? work_items(c, prec, 0, &n_items) : nullptr;
   if (items) {
@@ -205,7 +223,7 @@ static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
   for (const auto& b : c->buckets) {
     const TraceArgs<T> a = trace_args<T, ND, VISC>(c, b, q, trace);
     const int P = b.p + 1, e = epb_for(c, prec, 0, P);
-    const double nbb = (double)b.count * (ND + 2) * ipow(P, ND) * sizeof(T);
+    const double nbb = (double)b.count * values_trace(ND, P, VISC) * sizeof(T);
     const double nfb = (double)b.count * 2 * ND * ipow(P, ND - 1) * flops_trace(ND, P, VISC, DIAG);
     FR_LAUNCH_BF(c, name, s, nbb, nfb, {
       switch (P) {
@@ -230,12 +248,14 @@ static void launch_vol_p(const VolArgs<T>& a, int epb, cudaStream_t s) {
 }
 
 template <typename T>
-static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* out, double* out_neg64 = nullptr) {
+static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* out, double* out_neg64 = nullptr,
+                           double* out64 = nullptr) {
   VolArgs<T> a;
   a.q = q;
   a.v = v;
   a.out = out;
   a.out_neg64 = out_neg64;
+  a.out64 = out64;
   a.fout = (const T*)c->d_fout;
   a.slot_elem = c->d_slot_elem;
   a.basis = basis_ptr<T>(c);
@@ -252,15 +272,17 @@ static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T
 
 // volume kernel of every bucket: one launch per bucket, or one multi-bucket launch
 template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
-static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t s, double* out_neg64 = nullptr) {
+static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t s, double* out_neg64 = nullptr,
+                        double* out64 = nullptr) {
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
-  const int prec = sizeof(T) == 8 ? 0 : 1, kind = MODE == 1 ? 2 : 1;
-  const char* name = MODE == 1 ? (sizeof(T) == 8 ? "vol_jvp_f64" : "vol_jvp_f32")
-                               : (sizeof(T) == 8 ? "vol_res_f64" : "vol_res_f32");
+  const int prec = prec_row<T>(), kind = MODE == 1 ? 2 : 1;
+  const char* name = MODE == 1 ? kname<T>("vol_jvp_f64", "vol_jvp_f32", "vol_jvp_df")
+                               : kname<T>("vol_res_f64", "vol_res_f32", "vol_res_df");
+  const double out_ratio = (out_neg64 || out64) ? 8.0 / sizeof(T) : 1.0;
   double nb = 0.0, nfl = 0.0;
   for (const auto& b : c->buckets) {
     const int P = b.p + 1;
-    nb += (double)b.count * (ND + 2) * nsp_of(ND, P) * sizeof(T) * (MODE == 1 ? 3 : 2);
+    nb += (double)b.count * values_volume(ND, P, VISC, MODE == 1, out_ratio) * sizeof(T);
     nfl += MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC, DIAG);
   }
   int n_items = 0;
@@ -271,7 +293,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     for (size_t i = 0; i < c->buckets.size(); ++i) {
       const Bucket& b = c->buckets[i];
       const int P = b.p + 1, e = epb_for(c, prec, kind, P);
-      m.b[i] = vol_args<T>(c, b, q, v, out, out_neg64);
+      m.b[i] = vol_args<T>(c, b, q, v, out, out_neg64, out64);
       m.P[i] = P;
       m.epb[i] = e;
       smem = std::max(smem, (size_t)e * (ND + 2) * (1 + ND) * nsp_of(ND, P) * sizeof(S));
@@ -288,9 +310,9 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     return;
   }
   for (const auto& b : c->buckets) {
-    const VolArgs<T> a = vol_args<T>(c, b, q, v, out, out_neg64);
+    const VolArgs<T> a = vol_args<T>(c, b, q, v, out, out_neg64, out64);
     const int P = b.p + 1, e = epb_for(c, prec, kind, P);
-    const double nbb = (double)b.count * (ND + 2) * nsp_of(ND, P) * sizeof(T) * (MODE == 1 ? 3 : 2);
+    const double nbb = (double)b.count * values_volume(ND, P, VISC, MODE == 1, out_ratio) * sizeof(T);
     const double nfb = MODE == 1 ? 0.0 : (double)b.count * nsp_of(ND, P) * flops_volume(ND, P, VISC, DIAG);
     FR_LAUNCH_BF(c, name, s, nbb, nfb, {
       switch (P) {
@@ -326,9 +348,10 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
     a.nvt = c->nvt;
     a.scratch_base = g.scratch_base;
     const int64_t nm = (int64_t)g.n * ipow(a.Pm, ND - 1);
-    FR_LAUNCH_BF(c, MODE == 1 ? (sizeof(T) == 8 ? "face_jvp_f64" : "face_jvp_f32")
-                              : (sizeof(T) == 8 ? "face_res_f64" : "face_res_f32"),
-                 s, 0.0, MODE == 1 ? 0.0 : (double)nm * flops_face(ND, VISC, DIAG),
+    FR_LAUNCH_BF(c, MODE == 1 ? kname<T>("face_jvp_f64", "face_jvp_f32", "face_jvp_df")
+                              : kname<T>("face_res_f64", "face_res_f32", "face_res_df"),
+                 s, (double)nm * values_face(ND, VISC, MODE == 1) * sizeof(T),
+                 MODE == 1 ? 0.0 : (double)nm * flops_face(ND, VISC, DIAG),
                  face_kernel<T, ND, VISC, MODE, DIAG><<<nblocks(nm, 128), 128, 0, s>>>(a));
     if (g.pm != g.ps) {
       const int64_t ns = (int64_t)g.n * ipow(a.Ps, ND - 1);
@@ -362,6 +385,15 @@ static void residual_impl(fr_ctx* c, const T* q, T* R, cudaStream_t s) {
   launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
   launch_faces<T, ND, VISC, 0, DIAG>(c, trq, nullptr, s);
   launch_vols<T, ND, VISC, 0, DIAG>(c, q, nullptr, R, s);
+}
+
+// Double-float residual: q in double-float, R written in FP64 by the volume kernel.
+template <typename T, int ND, bool VISC, bool DIAG = false>
+static void residual_out64_impl(fr_ctx* c, const T* q, double* R, cudaStream_t s) {
+  T* trq = (T*)c->d_trace_q;
+  launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
+  launch_faces<T, ND, VISC, 0, DIAG>(c, trq, nullptr, s);
+  launch_vols<T, ND, VISC, 0, DIAG>(c, q, nullptr, nullptr, s, nullptr, R);
 }
 
 // JVP; with q_traces_ready the traces of q in d_trace_q are reused (q is
@@ -524,7 +556,7 @@ static float time_best(int reps, cudaStream_t s, F&& f) {
 
 template <typename T, int ND, bool VISC, bool DIAG = false>
 static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStream_t s) {
-  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const int prec = prec_row<T>();
   T* trq = (T*)c->d_trace_q;
   T* trv = (T*)c->d_trace_v;
   const bool multi_saved = c->multi_launch;
@@ -647,6 +679,13 @@ static void run_op_cfg(fr_ctx* c, int op, const void* q, const void* v, void* ou
   void NAME(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s) {        \
     if (c->visc) run_op_cfg<T, ND, true, DIAG>(c, op, q, v, out, s);                           \
     else run_op_cfg<T, ND, false, DIAG>(c, op, q, v, out, s);                                  \
+  }
+
+// The double-float residual of one configuration (q already in double-float).
+#define FR_RUN_RES_DF(NAME, ND, DIAG)                                                              \
+  void NAME(fr_ctx* c, const void* q, double* R, cudaStream_t s) {                                  \
+    if (c->visc) residual_out64_impl<dfloat, ND, true, DIAG>(c, (const dfloat*)q, R, s);          \
+    else residual_out64_impl<dfloat, ND, false, DIAG>(c, (const dfloat*)q, R, s);                 \
   }
 
 }  // namespace frgb

@@ -148,7 +148,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
       for (int v = 0; v < NV; ++v) {
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < P; ++k) acc += B.ext[s][k] * sq[v * NSP + line_sp<ND, P>(d, t, k)];
+        for (int k = 0; k < P; ++k) acc = madd(acc, B.ext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
         out[(f * a.nvt + v) * NFP + t] = acc;
         if (VISC) sqf[(f * NV + v) * NFP + t] = acc;
       }
@@ -174,17 +174,17 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
       T dq[ND];
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc += B.dext[s][k] * sq[v * NSP + line_sp<ND, P>(d, t, k)];
+      for (int k = 0; k < P; ++k) acc = madd(acc, B.dext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
       dq[d] = acc;
       const T* face = sqf + (f * NV + v) * NFP;
       acc = T(0);
 #pragma unroll
-      for (int m = 0; m < P; ++m) acc += B.D[ia][m] * face[ND == 2 ? m : m + P * ib];
+      for (int m = 0; m < P; ++m) acc = madd(acc, B.D[ia][m], face[ND == 2 ? m : m + P * ib]);
       dq[ta] = acc;
       if (ND == 3) {
         acc = T(0);
 #pragma unroll
-        for (int m = 0; m < P; ++m) acc += B.D[ib][m] * face[ia + P * m];
+        for (int m = 0; m < P; ++m) acc = madd(acc, B.D[ib][m], face[ia + P * m]);
         dq[tb] = acc;
       }
 #pragma unroll
@@ -194,7 +194,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
           g = Sf[j][j] * dq[j];
         } else {
 #pragma unroll
-          for (int dd = 0; dd < ND; ++dd) g += Sf[dd][j] * dq[dd];
+          for (int dd = 0; dd < ND; ++dd) g = madd(g, Sf[dd][j], dq[dd]);
         }
         out[(f * a.nvt + NV + j * NV + v) * NFP + t] = g * Jinv;
       }
@@ -586,6 +586,7 @@ struct VolArgs {
   const T* v;          // tangent (JVP)
   T* out;
   double* out_neg64;   // JVP only, optional: -J v written in FP64 instead of out
+  double* out64;       // double-float residual: R written in FP64 (out unused)
   const T* fout;
   const int32_t* slot_elem;
   const BasisTab<T>* basis;
@@ -651,13 +652,13 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
         for (int v = 0; v < NV; ++v) {
           S acc = szero<S>();
 #pragma unroll
-          for (int k = 0; k < P; ++k) acc = acc + B.D[idx[d]][k] * sq[v * NSP + base + k * stride];
+          for (int k = 0; k < P; ++k) acc = madd(acc, B.D[idx[d]][k], sq[v * NSP + base + k * stride]);
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
             const T* blk = fo + (2 * d + s) * FOUT_STRIDE;
             S dq;
             set_scalar(dq, blk[(NV + v) * NFP + tf], MODE == 1 ? blk[(2 * NV + v) * NFP + tf] : T(0));
-            acc = acc + B.dg[s][idx[d]] * dq;
+            acc = madd(acc, B.dg[s][idx[d]], dq);
           }
           gref[d][v] = acc;
         }
@@ -715,13 +716,13 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
       const S* line = sF + (d * NV + v) * NSP + base;
       S acc = szero<S>();
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc = acc + B.Dh[idx[d]][k] * line[k * stride];
+      for (int k = 0; k < P; ++k) acc = madd(acc, B.Dh[idx[d]][k], line[k * stride]);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         S com;
         const T c = fo[(2 * d + s) * FOUT_STRIDE + v * NFP + tf];
         if (MODE == 1) set_scalar(com, T(0), c); else set_scalar(com, c, T(0));
-        acc = acc + B.dg[s][idx[d]] * com;
+        acc = madd(acc, B.dg[s][idx[d]], com);
       }
       div[v] = div[v] + acc;
     }
@@ -729,10 +730,14 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     S r = (T(0) - div[v]) * Jinv;
-    if (MODE == 1 && a.out_neg64)
-      a.out_neg64[a.state_base + (i * NV + v) * NSP + sp] = -(double)tangent(r);
-    else
-      a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
+    if constexpr (is_dfloat<T>::value) {
+      a.out64[a.state_base + (i * NV + v) * NSP + sp] = to_double(value(r));
+    } else {
+      if (MODE == 1 && a.out_neg64)
+        a.out_neg64[a.state_base + (i * NV + v) * NSP + sp] = -(double)tangent(r);
+      else
+        a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
+    }
   }
 }
 

@@ -12,12 +12,14 @@ namespace frgb {
 
 Timing& timing_of(fr_ctx* c);
 
-// FR_F64 -> FP64 kernels; FR_F32 -> FP32 kernels; FR_BF16OP -> FP32 kernels
+// FR_F64 -> FP64 kernels; FR_DF -> double-float kernels (residual only);
+// FR_F32 -> FP32 kernels; FR_BF16OP -> FP32 kernels
 // reading the bfloat16-rounded operator tables (the kernel arguments point at
 // them, so a captured graph keeps the tables it was captured with)
 static fr_status run_op_prec(fr_ctx* c, int op, const void* q, const void* v, void* out, fr_prec prec,
                              cudaStream_t s) {
   if (prec == FR_F64) return run_op_f64(c, op, q, v, out, s);
+  if (prec == FR_DF) return run_op_df(c, op, q, v, out, s);
   c->bf16op = prec == FR_BF16OP;
   const fr_status st = run_op_f32(c, op, q, v, out, s);
   c->bf16op = false;
@@ -201,7 +203,7 @@ fr_status fr_unpack(fr_ctx* c, const void* q_dev, fr_prec prec, double* canon_de
 }
 
 fr_status fr_residual(fr_ctx* c, const void* q_dev, void* R_dev, fr_prec prec, void* stream) {
-  if (!c || !q_dev || !R_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) {
+  if (!c || !q_dev || !R_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP && prec != FR_DF)) {
     set_error("fr_residual: bad argument");
     return FR_ERR_INVALID;
   }

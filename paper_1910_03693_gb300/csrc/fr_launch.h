@@ -22,6 +22,8 @@ void vcast_f32_f64(fr_ctx* c, const float* x, double* y, int64_t n, cudaStream_t
 // op 6: as op 4, writing -J(q) v in FP64 into out.
 fr_status run_op_f64(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 fr_status run_op_f32(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
+// residual only (op 0): FP64 state in, FP64 R out, double-float arithmetic
+fr_status run_op_df(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 
 // per-configuration entry points behind run_op_f64/f32 (2D; 3D; 3D with
 // diagonal metrics, the axis-aligned affine elements)
@@ -31,6 +33,9 @@ void run_f64_3d_diag(fr_ctx* c, int op, const void* q, const void* v, void* out,
 void run_f32_2d(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 void run_f32_3d(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
 void run_f32_3d_diag(fr_ctx* c, int op, const void* q, const void* v, void* out, cudaStream_t s);
+void run_df_2d(fr_ctx* c, const void* q, double* R, cudaStream_t s);
+void run_df_3d(fr_ctx* c, const void* q, double* R, cudaStream_t s);
+void run_df_3d_diag(fr_ctx* c, const void* q, double* R, cudaStream_t s);
 
 fr_status launch_jvp_prepare(fr_ctx* c, const void* q, fr_prec prec, cudaStream_t s);
 fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv, fr_prec prec, cudaStream_t s);

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
+
 namespace frgb {
 
 template <typename T>
@@ -54,6 +56,12 @@ __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) {
   T r = a / b.v;
   return {r, -r * b.d / b.v};
 }
+
+// acc + a * b: one FMA in FP64/FP32 (the compiler contracts it), one fused
+// double-float operation for dfloat
+template <typename S, typename A, typename B>
+__device__ __forceinline__ S madd(S acc, A a, B b) { return acc + a * b; }
+__device__ __forceinline__ dfloat madd(dfloat acc, dfloat a, dfloat b) { return dfma(a, b, acc); }
 
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }

@@ -799,7 +799,8 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
                        fr_stage_stats* st, void* stream) {
   if (!c || !tab || !qn_dev || !qi_dev || !o || !st || tab->s < 2 || tab->s > 6 || stage < 2 ||
       stage > tab->s || !(dt > 0.0) || !(o->tol > 0.0) || !(o->dtau_init > 0.0) || !(o->dtau_max > 0.0) ||
-      !(o->f32_above >= 0.0) || (o->mode != FR_JV_FD && o->mode != FR_JV_EXACT) ||
+      !(o->low_above >= 0.0) || (o->low_above > 0.0 && o->low_prec != FR_F32 && o->low_prec != FR_DF) ||
+      (o->mode != FR_JV_FD && o->mode != FR_JV_EXACT) ||
       (o->jv_prec != FR_F64 && o->jv_prec != FR_F32 && o->jv_prec != FR_BF16OP)) {
     set_error("esdirk_stage: bad argument");
     return FR_ERR_INVALID;
@@ -832,24 +833,27 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
     if (tab->A[i * S + j] != 0.0) vaxpby(c, dt * tab->A[i * S + j] * inv_wdt, Rstages_dev[j], 1.0, rhs, n, s);
   std::memset(st, 0, sizeof(*st));
   // F from the FP64 residual, or (mixed mode, while ||F|| is large) from the
-  // FP32 residual of the FP32-rounded state; the FP32 buffers are the GMRES
-  // product scratch, idle between solves
-  const bool mixedF = o->mode == FR_JV_EXACT && o->f32_above > 0.0;
-  float* q32 = mixedF ? vec32(c, 1) : nullptr;
-  float* R32 = mixedF ? vec32(c, 2) : nullptr;
-  if (mixedF && (!q32 || !R32)) return FR_ERR_NOMEM;
-  bool f32 = mixedF;
+  // double-float residual of the FP64 state or the FP32 residual of the
+  // FP32-rounded state; the FP32 buffers are the GMRES product scratch, idle
+  // between solves
+  const bool mixedF = o->mode == FR_JV_EXACT && o->low_above > 0.0;
+  const bool low32 = mixedF && o->low_prec == FR_F32;
+  float* q32 = low32 ? vec32(c, 1) : nullptr;
+  float* R32 = low32 ? vec32(c, 2) : nullptr;
+  if (low32 && (!q32 || !R32)) return FR_ERR_NOMEM;
+  bool low = mixedF;
   auto evalF = [&](double* norm) -> fr_status {
     fr_status ee;
-    if (f32) {
+    if (low && low32) {
       vcast_f64_f32(c, qi_dev, q32, n, s);
       if ((ee = launch_residual(c, q32, R32, FR_F32, s)) != FR_OK) return ee;
       FR_LAUNCH_B(c, "vec", s, 28.0 * n, k_stage_F<float><<<egrid(n), 256, 0, s>>>(qi_dev, R32, rhs, inv_wdt, F, n));
-      st->f32_evaluations += 1;
+      st->low_evaluations += 1;
     } else {
-      if ((ee = launch_residual(c, qi_dev, R, FR_F64, s)) != FR_OK) return ee;
+      if ((ee = launch_residual(c, qi_dev, R, low ? FR_DF : FR_F64, s)) != FR_OK) return ee;
       FR_LAUNCH_B(c, "vec", s, 32.0 * n, k_stage_F<double><<<egrid(n), 256, 0, s>>>(qi_dev, R, rhs, inv_wdt, F, n));
-      st->f64_evaluations += 1;
+      if (low) st->low_evaluations += 1;
+      else st->f64_evaluations += 1;
     }
     if ((ee = norm2(c, F, n, norm, s)) != FR_OK) return ee;
     if (!std::isfinite(*norm)) {
@@ -869,12 +873,14 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
   op.eps = o->eps;
   op.precond = o->precond;
   for (int m = 0; m < o->max_newton; ++m) {
-    if (f32 && norm <= o->f32_above * st->norm0) {
-      // close enough to the FP32 noise: FP64 from here on, starting with this F
-      f32 = false;
+    // FP64 from here on, starting with this F, once ||F|| is below the
+    // threshold, or once an iteration reduced it by less than 10 %: the noise
+    // floor of the low-precision residual may lie above the threshold
+    if (low && (norm <= o->low_above * st->norm0 || (norm_prev > 0.0 && norm > 0.9 * norm_prev))) {
+      low = false;
       if ((e = evalF(&norm)) != FR_OK) return e;
     }
-    if (!f32 && norm <= o->tol * st->norm0) {
+    if (!low && norm <= o->tol * st->norm0) {
       st->converged = 1;
       break;
     }
@@ -893,8 +899,8 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
     if ((e = evalF(&norm)) != FR_OK) return e;
     st->newton_iterations += 1;
   }
-  if (f32) {   // iteration limit reached in the FP32 phase: the stage ends on an FP64 F
-    f32 = false;
+  if (low) {   // iteration limit reached in the low-precision phase: the stage ends on an FP64 F
+    low = false;
     if ((e = evalF(&norm)) != FR_OK) return e;
   }
   if (norm <= o->tol * st->norm0) st->converged = 1;

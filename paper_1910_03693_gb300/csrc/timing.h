@@ -175,4 +175,28 @@ inline double flops_face(int nd, bool visc, bool diag = false) {
   }
   return f;
 }
+// Algorithmic data movement (values; times the operand size gives bytes):
+// what each kernel has to read and write at least, geometry excluded.
+// Traces, per element: the state in, every face's q (and for NS the gradient) out.
+inline double values_trace(int nd, int P, bool visc) {
+  const int nv = nd + 2, nsp = nd == 2 ? P * P : P * P * P, nfp = nd == 2 ? P : P * P;
+  return (double)nv * nsp + 2.0 * nd * nfp * (visc ? nv * (1 + nd) : nv);
+}
+// Volume kernel, per element: the state (and the tangent), the face outputs it
+// reads (common flux; for NS also q^com - q; the JVP's tangents of both), and
+// the result, in units of the operand size except the result (out_ratio =
+// result size / operand size, 2 for an FP64 result of FP32 kernels).
+inline double values_volume(int nd, int P, bool visc, bool jvp, double out_ratio = 1.0) {
+  const int nv = nd + 2, nsp = nd == 2 ? P * P : P * P * P, nfp = nd == 2 ? P : P * P;
+  const double in = (double)nv * nsp * (jvp ? 2 : 1) + 2.0 * nd * nfp * nv * (visc ? (jvp ? 3 : 2) : 1);
+  return in + out_ratio * nv * nsp;
+}
+// Interior face kernel, per mortar point (conforming faces): both sides'
+// traces (and tangent traces) in, both sides' outputs out.
+inline double values_face(int nd, bool visc, bool jvp) {
+  const int nv = nd + 2;
+  const double in = 2.0 * (visc ? nv * (1 + nd) : nv) * (jvp ? 2 : 1);
+  const double out = 2.0 * nv * (visc ? (jvp ? 3 : 2) : 1);
+  return in + out;
+}
 }  // namespace frgb

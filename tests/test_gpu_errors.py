@@ -62,6 +62,8 @@ def test_stage_and_step_reject_bad_arguments(setup):
     with pytest.raises(FRError):
         ctx.esdirk_step(A, 0.01, torch.zeros(ctx.n_dof_capacity, dtype=torch.float64, device="cuda"), b=b,
                         adapt=dict(p_min=1, p_max=3, var=9))
+    with pytest.raises(ValueError):  # the low-precision residual is double-float or FP32
+        ctx.esdirk_stage(A, 2, 0.01, qs, [R1, R2, None, None], qi, low_above=1e-6, low_precision="bf16")
     _still_works(ctx, qs)
 
 

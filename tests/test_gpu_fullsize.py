@@ -43,6 +43,16 @@ def test_tgv_full_residual(built, tgv):
         assert ok, (str(dtype), rel, fs)
 
 
+def test_tgv_full_df_residual(built, tgv):
+    """The double-float residual the bench's early Newton iterates use."""
+    m, q, ph, fr = tgv
+    ctx = gpu_ctx(m, ph, 3, 3)
+    Rref = fr.residual(torch.from_numpy(q)).numpy()
+    R = ctx.unpack(ctx.residual(ctx.pack(torch.from_numpy(q).cuda()), double_float=True)).cpu().numpy()
+    ok, rel, fs = parity_ok(R, Rref, m, q, 2e-10)
+    assert ok, (rel, fs)
+
+
 def test_tgv_full_fp32_exact_jvp(built, tgv):
     """The JVP the bench's GMRES applies (FP32, exact), on a generic nearby state."""
     from oracle import linearize as L
@@ -57,11 +67,13 @@ def test_tgv_full_fp32_exact_jvp(built, tgv):
     assert ok, (rel, fs)
 
 
-def test_tgv_full_stage_solves_oracle_stage_equation(built, tgv):
+@pytest.mark.parametrize("low_above", [0.0, 1e-8])
+def test_tgv_full_stage_solves_oracle_stage_equation(built, tgv, low_above):
     """ESDIRK3 stage 2 exactly as bench.py runs it (dt 0.01, FP32 exact-JVP
-    GMRES(60) with one Gram-Schmidt pass, FP64 F, tolerance 1e-8): the converged q^2 makes the oracle's
-    stage residual F(q) = -q/(w dt) + R(q) + (q^n + dt a21 R(q^n))/(w dt)
-    small to the same tolerance."""
+    GMRES(60) with one Gram-Schmidt pass, tolerance 1e-8; F in FP64 throughout,
+    or double-float until ||F|| <= 1e-8 ||F0|| and FP64 after): the converged
+    q^2 makes the oracle's stage residual
+    F(q) = -q/(w dt) + R(q) + (q^n + dt a21 R(q^n))/(w dt) small to the same tolerance."""
     from paper_1910_03693_gb300 import esdirk_tableau
     m, q, ph, fr = tgv
     A, _ = esdirk_tableau(3)
@@ -72,8 +84,10 @@ def test_tgv_full_stage_solves_oracle_stage_equation(built, tgv):
     qi = qn.clone()
     R2 = torch.empty_like(qn)
     st = ctx.esdirk_stage(A, 2, dt, qn, [R1, R2, None, None], qi, tol=1e-8, dtau_init=dt / 10, dtau_max=dt,
-                          mode="exact", jv_dtype=torch.float32, m=60, rtol=0.1, max_it=100, reorth=0)
+                          mode="exact", jv_dtype=torch.float32, m=60, rtol=0.1, max_it=100, reorth=0,
+                          low_above=low_above, low_precision="df")
     assert st["converged"]
+    assert (st["low_evaluations"] > 0) == (low_above > 0)
     w = A[1][1]
     qi_h = torch.from_numpy(ctx.unpack(qi).cpu().numpy())
     qn_h = torch.from_numpy(q)
