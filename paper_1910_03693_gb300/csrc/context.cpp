@@ -545,7 +545,6 @@ static void destroy_impl(fr_ctx* c) {
   cudaFree(c->d_basis_df);
   cudaFree(c->d_mortar_df);
   cudaFree(c->d_gaff_df);
-  cudaFree(c->d_qdf);
   cudaFree(c->d_trace_q);
   cudaFree(c->d_trace_v);
   cudaFree(c->d_fout);

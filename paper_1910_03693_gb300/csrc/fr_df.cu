@@ -1,5 +1,6 @@
-// Double-float entry of the FR residual: FP64 state in, FP64 residual out,
-// every operation in between in double-float arithmetic on the FP32 pipe.
+// Double-float entry of the FR residual: FP64 state in (converted on load by
+// the trace and volume kernels), FP64 residual out, every operation in
+// between in double-float arithmetic on the FP32 pipe.
 // The double-float copies of the operator and geometry tables are made on the
 // device from the FP64 ones the first time they are needed.
 #include <algorithm>
@@ -54,11 +55,6 @@ static fr_status ensure_df(fr_ctx* c, cudaStream_t s) {
         return st;
     }
   }
-  if (!c->d_qdf && cudaMalloc(&c->d_qdf, sizeof(dfloat) * c->n_dof_cap) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("double-float state: allocation failed");
-    return FR_ERR_NOMEM;
-  }
   c->df_ready = true;
   return FR_OK;
 }
@@ -70,11 +66,10 @@ fr_status run_op_df(fr_ctx* c, int op, const void* q, const void*, void* out, cu
   }
   const fr_status st = ensure_df(c, s);
   if (st != FR_OK) return st;
-  const int64_t n = c->n_dof;
-  FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_to_dfloat<<<grid_for(n), 256, 0, s>>>((const double*)q, (dfloat*)c->d_qdf, n));
-  if (c->nd == 2) run_df_2d(c, c->d_qdf, (double*)out, s);
-  else if (c->diag) run_df_3d_diag(c, c->d_qdf, (double*)out, s);
-  else run_df_3d(c, c->d_qdf, (double*)out, s);
+  // the kernels read the FP64 state and convert it on load
+  if (c->nd == 2) run_df_2d(c, q, (double*)out, s);
+  else if (c->diag) run_df_3d_diag(c, q, (double*)out, s);
+  else run_df_3d(c, q, (double*)out, s);
   return cuda_check(cudaGetLastError(), "FR kernel launch");
 }
 

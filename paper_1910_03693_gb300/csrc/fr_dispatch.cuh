@@ -387,7 +387,8 @@ static void residual_impl(fr_ctx* c, const T* q, T* R, cudaStream_t s) {
   launch_vols<T, ND, VISC, 0, DIAG>(c, q, nullptr, R, s);
 }
 
-// Double-float residual: q in double-float, R written in FP64 by the volume kernel.
+// Double-float residual: q is the FP64 state (converted on load), R written
+// in FP64 by the volume kernel.
 template <typename T, int ND, bool VISC, bool DIAG = false>
 static void residual_out64_impl(fr_ctx* c, const T* q, double* R, cudaStream_t s) {
   T* trq = (T*)c->d_trace_q;
@@ -681,7 +682,7 @@ static void run_op_cfg(fr_ctx* c, int op, const void* q, const void* v, void* ou
     else run_op_cfg<T, ND, false, DIAG>(c, op, q, v, out, s);                                  \
   }
 
-// The double-float residual of one configuration (q already in double-float).
+// The double-float residual of one configuration (q: the FP64 state).
 #define FR_RUN_RES_DF(NAME, ND, DIAG)                                                              \
   void NAME(fr_ctx* c, const void* q, double* R, cudaStream_t s) {                                  \
     if (c->visc) residual_out64_impl<dfloat, ND, true, DIAG>(c, (const dfloat*)q, R, s);          \

@@ -126,14 +126,13 @@ struct fr_ctx {
   float* d_gvol32[frgb::kMaxDeg + 1] = {};
   double* d_gface64[frgb::kMaxDeg + 1] = {};
   float* d_gface32[frgb::kMaxDeg + 1] = {};
-  // double-float copies of the tables and a double-float state buffer,
-  // created on the first FR_DF residual (type frgb::dfloat, 8 bytes a value)
+  // double-float copies of the tables, created on the first FR_DF residual
+  // (type frgb::dfloat, 8 bytes a value)
   void* d_basis_df = nullptr;
   void* d_mortar_df = nullptr;
   void* d_gaff_df = nullptr;
   void* d_gvol_df[frgb::kMaxDeg + 1] = {};
   void* d_gface_df[frgb::kMaxDeg + 1] = {};
-  void* d_qdf = nullptr;
   bool df_ready = false;
   // layout
   std::vector<frgb::Bucket> buckets;     // one per degree present, ascending p

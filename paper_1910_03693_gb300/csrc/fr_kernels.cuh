@@ -83,6 +83,14 @@ __device__ __forceinline__ int orient_inv(int code, int uu, int P, int nd) {
   return ia + P * ib;
 }
 
+// State value i: for the double-float kernels the state pointer holds the FP64
+// state, converted on load (the FP64 pipe is otherwise idle in those kernels).
+template <typename T>
+__device__ __forceinline__ T load_state(const T* q, int64_t i) {
+  if constexpr (is_dfloat<T>::value) return to_dfloat(reinterpret_cast<const double*>(q)[i]);
+  else return q[i];
+}
+
 template <typename T>
 __device__ __forceinline__ T geo_vol(const GeoView<T>& g, int64_t e, int k, int sp) {
   return g.vol[e * g.ves + (int64_t)k * g.vks + (int64_t)sp * g.vps];
@@ -98,7 +106,7 @@ __device__ __forceinline__ T geo_face(const GeoView<T>& g, int64_t e, int f, int
 // ---------------------------------------------------------------------------
 template <typename T>
 struct TraceArgs {
-  const T* q;
+  const T* q;            // double-float kernels: the FP64 state (see load_state)
   T* trace;
   const int32_t* slot_elem;
   const BasisTab<T>* basis;
@@ -137,7 +145,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
   const BasisTab<T>& B = a.basis[P];
   if (valid) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sq[v * NSP + lt] = a.q[a.state_base + (i * NV + v) * NSP + lt];
+    for (int v = 0; v < NV; ++v) sq[v * NSP + lt] = load_state(a.q, a.state_base + (i * NV + v) * NSP + lt);
   }
   __syncthreads();
   T* out = a.trace + a.trace_base + (valid ? i * NF * (int64_t)a.nvt * NFP : 0);
@@ -146,9 +154,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
       const int f = fp / NFP, t = fp % NFP, d = f >> 1, s = f & 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T acc = T(0);
+        Acc<T> ac = acc_init(T(0));
 #pragma unroll
-        for (int k = 0; k < P; ++k) acc = madd(acc, B.ext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
+        for (int k = 0; k < P; ++k) acc_madd(ac, B.ext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
+        const T acc = acc_value(ac);
         out[(f * a.nvt + v) * NFP + t] = acc;
         if (VISC) sqf[(f * NV + v) * NFP + t] = acc;
       }
@@ -172,20 +181,20 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T dq[ND];
-      T acc = T(0);
+      Acc<T> ac = acc_init(T(0));
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc = madd(acc, B.dext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
-      dq[d] = acc;
+      for (int k = 0; k < P; ++k) acc_madd(ac, B.dext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
+      dq[d] = acc_value(ac);
       const T* face = sqf + (f * NV + v) * NFP;
-      acc = T(0);
+      ac = acc_init(T(0));
 #pragma unroll
-      for (int m = 0; m < P; ++m) acc = madd(acc, B.D[ia][m], face[ND == 2 ? m : m + P * ib]);
-      dq[ta] = acc;
+      for (int m = 0; m < P; ++m) acc_madd(ac, B.D[ia][m], face[ND == 2 ? m : m + P * ib]);
+      dq[ta] = acc_value(ac);
       if (ND == 3) {
-        acc = T(0);
+        ac = acc_init(T(0));
 #pragma unroll
-        for (int m = 0; m < P; ++m) acc = madd(acc, B.D[ib][m], face[ia + P * m]);
-        dq[tb] = acc;
+        for (int m = 0; m < P; ++m) acc_madd(ac, B.D[ib][m], face[ia + P * m]);
+        dq[tb] = acc_value(ac);
       }
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(128) bnd_kernel(BndArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct VolArgs {
-  const T* q;
+  const T* q;          // double-float kernels: the FP64 state (see load_state)
   const T* v;          // tangent (JVP)
   T* out;
   double* out_neg64;   // JVP only, optional: -J v written in FP64 instead of out
@@ -622,7 +631,7 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
   if (valid) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      T x = a.q[a.state_base + (i * NV + v) * NSP + sp];
+      T x = load_state(a.q, a.state_base + (i * NV + v) * NSP + sp);
       T dx = MODE == 1 ? a.v[a.state_base + (i * NV + v) * NSP + sp] : T(0);
       set_scalar(q[v], x, dx);
       sq[v * NSP + sp] = q[v];
@@ -650,17 +659,17 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
         const int tf = face_pt<ND, P>(d, idx);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          S acc = szero<S>();
+          Acc<S> acc = acc_init(szero<S>());
 #pragma unroll
-          for (int k = 0; k < P; ++k) acc = madd(acc, B.D[idx[d]][k], sq[v * NSP + base + k * stride]);
+          for (int k = 0; k < P; ++k) acc_madd(acc, B.D[idx[d]][k], sq[v * NSP + base + k * stride]);
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
             const T* blk = fo + (2 * d + s) * FOUT_STRIDE;
             S dq;
             set_scalar(dq, blk[(NV + v) * NFP + tf], MODE == 1 ? blk[(2 * NV + v) * NFP + tf] : T(0));
-            acc = madd(acc, B.dg[s][idx[d]], dq);
+            acc_madd(acc, B.dg[s][idx[d]], dq);
           }
-          gref[d][v] = acc;
+          gref[d][v] = acc_value(acc);
         }
       }
       S G[ND][NV];
@@ -714,17 +723,17 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const S* line = sF + (d * NV + v) * NSP + base;
-      S acc = szero<S>();
+      Acc<S> acc = acc_init(szero<S>());
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc = madd(acc, B.Dh[idx[d]][k], line[k * stride]);
+      for (int k = 0; k < P; ++k) acc_madd(acc, B.Dh[idx[d]][k], line[k * stride]);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         S com;
         const T c = fo[(2 * d + s) * FOUT_STRIDE + v * NFP + tf];
         if (MODE == 1) set_scalar(com, T(0), c); else set_scalar(com, c, T(0));
-        acc = madd(acc, B.dg[s][idx[d]], com);
+        acc_madd(acc, B.dg[s][idx[d]], com);
       }
-      div[v] = div[v] + acc;
+      div[v] = div[v] + acc_value(acc);
     }
   }
 #pragma unroll
@@ -742,7 +751,7 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
 }
 
 template <typename T, int ND, int P, bool VISC, int MODE, bool DIAG>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) vol_kernel(VolArgs<T> a, int epb) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : (is_dfloat<T>::value ? 2 : 1)) vol_kernel(VolArgs<T> a, int epb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   vol_body<T, ND, P, VISC, MODE, DIAG>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
 }
@@ -757,7 +766,7 @@ struct VolMulti {
 };
 
 template <typename T, int ND, bool VISC, int MODE, bool DIAG>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) vol_multi_kernel(VolMulti<T> m) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : (is_dfloat<T>::value ? 2 : 1)) vol_multi_kernel(VolMulti<T> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
     const WorkItem it = m.items[w];

@@ -63,6 +63,39 @@ template <typename S, typename A, typename B>
 __device__ __forceinline__ S madd(S acc, A a, B b) { return acc + a * b; }
 __device__ __forceinline__ dfloat madd(dfloat acc, dfloat a, dfloat b) { return dfma(a, b, acc); }
 
+// Accumulator of a short contraction c + sum_k a_k b_k: the plain type for
+// FP64, FP32 and dual numbers; for double-float an unnormalised pair whose
+// high part is summed exactly (TwoSum) and whose error terms are summed in
+// FP32, normalised once at the end (12 FP32 operations a term instead of 15;
+// the FP32 sum of the error terms adds about n u^2 sum_k |a_k b_k|).
+template <typename S>
+struct Acc {
+  S v;
+};
+template <typename S>
+__device__ __forceinline__ Acc<S> acc_init(S x) { return Acc<S>{x}; }
+template <typename S, typename A, typename B>
+__device__ __forceinline__ void acc_madd(Acc<S>& c, A a, B b) { c.v = madd(c.v, a, b); }
+template <typename S>
+__device__ __forceinline__ S acc_value(const Acc<S>& c) { return c.v; }
+
+template <>
+struct Acc<dfloat> {
+  float s, e;
+};
+__device__ __forceinline__ Acc<dfloat> acc_init(dfloat x) { return Acc<dfloat>{x.hi, x.lo}; }
+__device__ __forceinline__ void acc_madd(Acc<dfloat>& c, dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  float s, t;
+  dfl::two_sum(c.s, p, s, t);
+  c.s = s;
+  c.e = __fadd_rn(c.e, __fadd_rn(t, pe));
+}
+__device__ __forceinline__ dfloat acc_value(const Acc<dfloat>& c) { return dfl::renorm(c.s, c.e); }
+
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 template <typename T>
