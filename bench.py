@@ -361,9 +361,10 @@ def run_timesteps(args):
     """ESDIRK3 time steps of the extruded NACA 0012 C-grid (256 x 64 x 24 hexahedra,
     Re 6e4, Ma 0.2, 8 degrees), starting from p = 1 everywhere, with the indicator
     and rebucketing after every step (p in 1..4), in the mixed-precision
-    exact-JVP mode (with and without the element-Jacobi preconditioner) and in
-    the FP64 finite-difference mode; one JSON line with
-    the per-step times, iteration counts and degree histograms."""
+    exact-JVP mode (with the element-Jacobi preconditioner, with and without
+    the double-float F of the early Newton iterates; without preconditioner)
+    and in the FP64 finite-difference mode; one JSON line with the per-step
+    times, iteration counts and degree histograms."""
     import torch
     import cases
     from paper_1910_03693_gb300 import FRContext, esdirk_tableau
@@ -372,8 +373,8 @@ def run_timesteps(args):
     dt = 0.005
     out = {"workload": "naca0012_cgrid_256x64x24", "dt": dt, "tableau": "ESDIRK3",
            "adapt": {"nu_max": 0.1, "nu_min": 0.001, "p_min": 1, "p_max": 4, "var": 1}, "modes": {}}
-    for mode, jv, pc in (("exact", torch.float32, True), ("exact", torch.float32, False),
-                         ("fd", torch.float64, False)):
+    for mode, jv, pc, low in (("exact", torch.float32, True, 1e-8), ("exact", torch.float32, True, 0.0),
+                              ("exact", torch.float32, False, 0.0), ("fd", torch.float64, False, 0.0)):
         ctx = FRContext(m, gamma=ph["gamma"], mu=ph["mu"], Pr=ph["Pr"], q_inf=ph["q_inf"], p_min=1, p_max=4)
         buf = torch.zeros(ctx.n_dof_capacity, dtype=torch.float64, device="cuda")
         ctx.pack(torch.from_numpy(q).cuda(), out=buf[:ctx.n_dof])
@@ -385,17 +386,21 @@ def run_timesteps(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             st = ctx.esdirk_step(A, dt, buf, b=b, adapt=out["adapt"], tol=1e-8, dtau_init=dt / 10, dtau_max=dt,
-                                 mode=mode, jv_dtype=jv, m=30, rtol=0.1, max_it=100, precond=pc)
+                                 mode=mode, jv_dtype=jv, m=30, rtol=0.1, max_it=100, precond=pc,
+                                 low_above=low, low_precision="df")
             e1.record()
             torch.cuda.synchronize()
             pm = ctx.p_map()
             steps.append({"ms": round(e0.elapsed_time(e1), 2), "n_dof_in": n_before, "n_dof_out": ctx.n_dof,
                           "newton": [s["newton"] for s in st], "gmres": [s["gmres"] for s in st],
+                          "F_evals_df": [s["low_evaluations"] for s in st],
+                          "F_evals_f64": [s["f64_evaluations"] for s in st],
                           "converged": all(s["converged"] for s in st),
                           "p_hist": [int((pm == p).sum()) for p in range(1, 5)]})
             if not steps[-1]["converged"]:
                 break
-        out["modes"][f"{mode}_{'f32' if jv == torch.float32 else 'f64'}{'_element_jacobi' if pc else ''}"] = steps
+        key = f"{mode}_{'f32' if jv == torch.float32 else 'f64'}{'_element_jacobi' if pc else ''}"
+        out["modes"][key + ("_df_F" if low > 0 else "")] = steps
         del ctx, buf
         torch.cuda.empty_cache()
     print(json.dumps({"timesteps": out}), flush=True)
