@@ -52,8 +52,9 @@ static unsigned red_blocks(int64_t n) {
 // writes its sums (warp-shuffle then shared-memory tree, fixed order) to its
 // own slot of `partial`; the last block to arrive (arrival counter) adds the
 // slots in a fixed order, writes out[] and re-arms the counter.
+// Returns true in the block that wrote out[] (after its threads < k stored it).
 template <int KC>
-__device__ __forceinline__ void grid_sum(const double (&vals)[KC], int k, double* __restrict__ partial,
+__device__ __forceinline__ bool grid_sum(const double (&vals)[KC], int k, double* __restrict__ partial,
                                          double* __restrict__ out, unsigned* __restrict__ ticket) {
   __shared__ double red[kRedThreads / 32][KC];
   __shared__ bool last;
@@ -78,7 +79,7 @@ __device__ __forceinline__ void grid_sum(const double (&vals)[KC], int k, double
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   // the last block: thread t adds the slots t, t + blockDim, ... (all loads of
   // a thread issued together), then the same warp/shared-memory tree as above
@@ -113,6 +114,7 @@ __device__ __forceinline__ void grid_sum(const double (&vals)[KC], int k, double
     out[threadIdx.x] = t;
   }
   if (threadIdx.x == 0) *ticket = 0u;
+  return true;
 }
 
 // Slot q of a vector seen as pairs (VEC: 16-byte loads of two values) or
@@ -276,13 +278,19 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
 
 // w_out = w_in - sum_kk s_kk^2 raw[kk] V[kk] (the stored columns V[kk] scaled
 // by s_kk are the orthonormal basis, raw[kk] = V[kk]^T w_in); out[0] =
-// ||w_out||^2.  w_out may be w_in (in place, FP64).
+// ||w_out||^2.  w_out may be w_in (in place, FP64).  With next_scale, the
+// block that finishes the norm also stores 1/||w_out|| there (0 for a zero
+// vector) and next_j into *jidx: the scale and index of the next Arnoldi
+// product, set without a round trip through the host (the host computes the
+// same IEEE quotient for its own copy).
 template <int KC, bool VEC, typename WT, bool NEG>
 __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __restrict__ V, int64_t ldv, int k,
                                                               const double* __restrict__ raw,
                                                               const double* __restrict__ scale, const WT* w_in,
                                                               double* w_out, int64_t n, double* __restrict__ partial,
-                                                              double* __restrict__ out, unsigned* __restrict__ ticket) {
+                                                              double* __restrict__ out, unsigned* __restrict__ ticket,
+                                                              double* __restrict__ next_scale, int* __restrict__ jidx,
+                                                              int next_j) {
   constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
   using L = Slots<VEC>;
   using LW = WSlots<VEC, WT, NEG>;
@@ -325,20 +333,46 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
   double acc[1] = {accu[0]};
 #pragma unroll
   for (int u = 1; u < U; ++u) acc[0] += accu[u];
-  grid_sum<1>(acc, 1, partial, out, ticket);
+  if (grid_sum<1>(acc, 1, partial, out, ticket) && threadIdx.x == 0 && next_scale) {
+    const double hn = sqrt(out[0]);
+    *next_scale = hn != 0.0 ? 1.0 / hn : 0.0;
+    *jidx = next_j;
+  }
+}
+
+// Blocks of one reduction launch: at most `grid`, and no more than the SMs
+// hold at once for this kernel (its register count decides), so that the
+// grid-stride loop runs as whole waves; the occupancy query runs once per
+// kernel instantiation.
+template <auto KERN>
+static unsigned wave_grid(unsigned grid) {
+  static int resident = 0;
+  if (resident == 0) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, KERN, kRedThreads, 0) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    resident = std::max(1, per_sm * std::max(sms, 1));
+  }
+  return std::max(1u, std::min(grid, (unsigned)resident));
 }
 
 // launch KERNEL<KC, VEC, WT, NEG> with the smallest KC >= k; VEC when every
 // vector starts on a 16-byte boundary and the column stride is even
+#define FR_KC_LAUNCH(KC_, V_, grid, KERNEL, WT, NEG, ...) \
+  KERNEL<KC_, V_, WT, NEG><<<wave_grid<KERNEL<KC_, V_, WT, NEG>>(grid), kRedThreads, 0, s>>>(__VA_ARGS__)
 #define FR_KC_CASES(k, V_, grid, KERNEL, WT, NEG, ...)                                                   \
   do {                                                                                                  \
-    if ((k) <= 1) KERNEL<1, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                     \
-    else if ((k) <= 2) KERNEL<2, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
-    else if ((k) <= 4) KERNEL<4, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
-    else if ((k) <= 8) KERNEL<8, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                \
-    else if ((k) <= 16) KERNEL<16, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
-    else if ((k) <= 32) KERNEL<32, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);              \
-    else KERNEL<64, V_, WT, NEG><<<grid, kRedThreads, 0, s>>>(__VA_ARGS__);                             \
+    if ((k) <= 1) FR_KC_LAUNCH(1, V_, grid, KERNEL, WT, NEG, __VA_ARGS__);                              \
+    else if ((k) <= 2) FR_KC_LAUNCH(2, V_, grid, KERNEL, WT, NEG, __VA_ARGS__);                         \
+    else if ((k) <= 4) FR_KC_LAUNCH(4, V_, grid, KERNEL, WT, NEG, __VA_ARGS__);                         \
+    else if ((k) <= 8) FR_KC_LAUNCH(8, V_, grid, KERNEL, WT, NEG, __VA_ARGS__);                         \
+    else if ((k) <= 16) FR_KC_LAUNCH(16, V_, grid, KERNEL, WT, NEG, __VA_ARGS__);                       \
+    else if ((k) <= 32) FR_KC_LAUNCH(32, V_, grid, KERNEL, WT, NEG, __VA_ARGS__);                       \
+    else FR_KC_LAUNCH(64, V_, grid, KERNEL, WT, NEG, __VA_ARGS__);                                      \
   } while (0)
 #define FR_KC_DISPATCH(k, vec, grid, KERNEL, WT, NEG, ...)                                              \
   do {                                                                                                  \
@@ -446,22 +480,17 @@ static void release_graph_timers(fr_ctx* c, int pi) {
   c->graph_timers[pi].clear();
 }
 
-static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double* V, int j, double* w,
-                               cudaStream_t s) {
+// The column index is read from c->d_jidx: the caller sets it (the update
+// of the previous Arnoldi step stores it on the device).
+static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double* V, double* w, cudaStream_t s) {
   const int pi = op->jv_prec == FR_F64 ? 0 : 1;   // FP32 kernels for FR_F32 and FR_BF16OP
   const fr_prec prec = op->jv_prec;
   const int64_t n = c->n_dof, ld = krylov_ld(c);
-  if (!c->d_jidx) {
-    if (cudaMalloc(&c->d_jidx, sizeof(int)) != cudaSuccess) return FR_ERR_NOMEM;
-    if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
-    for (int k = 0; k < kMaxK; ++k) c->h_jidx[k] = k;
-  }
   // the q the traces were prepared from: the FP32 copy for FP32 products
   const void* qptr = pi ? (const void*)vec32(c, 0) : (const void*)op->q64_dev;
   void* x = pi ? (void*)vec32(c, 1) : (void*)vec64(c, 10);
   if (!qptr || !x) return FR_ERR_NOMEM;
   collect_graph_timers(c);
-  cudaMemcpyAsync(c->d_jidx, c->h_jidx + j, sizeof(int), cudaMemcpyHostToDevice, s);
   auto direct = [&](cudaStream_t st) -> fr_status {
     gather_col(c, pi, V, ld, x, n, st);
     return launch_jvp_prepared_neg64(c, qptr, x, w, prec, st);
@@ -575,6 +604,11 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     return FR_ERR_INVALID;
   }
   if (ensure_red(c) != FR_OK) return FR_ERR_NOMEM;
+  if (!c->d_jidx) {   // index of the column the next Arnoldi product reads
+    if (cudaMalloc(&c->d_jidx, sizeof(int)) != cudaSuccess) return FR_ERR_NOMEM;
+    if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
+    for (int k = 0; k < kMaxK; ++k) c->h_jidx[k] = k;
+  }
   if (!c->d_krylov || c->krylov_m < m) {
     cudaFree(c->d_krylov);
     c->d_krylov = nullptr;
@@ -641,13 +675,15 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   };
   // one Gram-Schmidt pass against columns 0..kk-1: dots of w_in into `raw`,
   // then w_out = w_in - sum s_i^2 raw_i u_i with ||w_out||^2 into N
+  // (the update also stores the scale of the new column and the index of
+  // the next product on the device: kk is the new column's index)
   auto gs_pass = [&](int kk, const double* w_in, double* w_out, double* raw, int with_norm) {
     FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
                 FR_KC_DISPATCH(kk, vec, grid, k_multidot, double, false, V, ld, kk, w_in, n, part, raw, ticket,
                                with_norm));
     FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
                 FR_KC_DISPATCH(kk, vec, grid, k_orth_update, double, false, V, ld, kk, raw, sdev, w_in, w_out, n,
-                               part, c->d_red + kOutN, ticket));
+                               part, c->d_red + kOutN, ticket, sdev + kk, c->d_jidx, kk));
   };
   bool first = true;
   while (true) {
@@ -673,7 +709,8 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     for (int j = 0; j < m; ++j) {
       // product w = -J v_j
       if (exact) {
-        if ((e = exact_product(c, op, V, j, w, s)) != FR_OK) return e;
+        if (j == 0) cudaMemcpyAsync(c->d_jidx, c->h_jidx, sizeof(int), cudaMemcpyHostToDevice, s);
+        if ((e = exact_product(c, op, V, w, s)) != FR_OK) return e;
       } else {
         FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(V + (int64_t)j * ld, sh[j], xs, n));
         if ((e = apply_op(c, op, R0, xs, w, s, false)) != FR_OK) return e;
@@ -729,7 +766,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       g[j] = cs[j] * g[j];
       res = std::fabs(g[j + 1]);
       k = j + 1;
-      if (hn != 0.0) set_scale(j + 1, 1.0 / hn);
+      if (hn != 0.0) sh[j + 1] = 1.0 / hn;   // the device copy was stored by the update
       if (res <= o->rtol * beta0 || it >= o->max_it || hn == 0.0) break;
     }
     for (int i = k - 1; i >= 0; --i) {
