@@ -210,7 +210,7 @@ class FR:
             A = _sign(sm)[:, None, None] * GM["geom"].Sf[mE, mF, dm]        # [F, j, nfp]
             absA = torch.sqrt((A * A).sum(1))
             n = A / absA[:, None]
-            Fn = ph.rusanov(qM, qS, n) * absA[:, None]
+            Fn = ph.common_flux(qM, qS, n) * absA[:, None]
             qc = None
             if visc:
                 qc = 0.5 * (qM + qS)
@@ -238,7 +238,7 @@ class FR:
             A = _sign(s)[:, None, None] * Gg["geom"].Sf[Ei, Fi, d]
             absA = torch.sqrt((A * A).sum(1))
             n = A / absA[:, None]
-            Fn = ph.rusanov(qM, qG, n) * absA[:, None]
+            Fn = ph.common_flux(qM, qG, n) * absA[:, None]
             qc = None
             if visc:
                 qc = 0.5 * (qM + qG)

@@ -15,11 +15,14 @@ class Euler:
     K = -mu C_p/Pr grad T = -mu gamma/((gamma-1) Pr) grad(p/rho).
     """
 
-    def __init__(self, nd, gamma=1.4, mu=0.0, Pr=0.72, q_inf=None):
+    def __init__(self, nd, gamma=1.4, mu=0.0, Pr=0.72, q_inf=None, flux="rusanov"):
         self.nd, self.nv = nd, nd + 2
         self.gamma, self.mu, self.Pr = float(gamma), float(mu), float(Pr)
         self.viscous = self.mu > 0.0
         self.q_inf = None if q_inf is None else torch.as_tensor(q_inf, dtype=torch.float64)
+        if flux not in ("rusanov", "roe"):
+            raise ValueError(flux)
+        self.flux_kind = flux
 
     # -- inviscid -------------------------------------------------------------
     def primitives(self, q):
@@ -62,6 +65,74 @@ class Euler:
         lamL, lamR = self.wave_speed(qL, n), self.wave_speed(qR, n)
         lam = torch.where(lamR > lamL, lamR, lamL)
         return 0.5 * (fL + fR) - 0.5 * lam[:, None] * (qR - qL)
+
+    def common_flux(self, qL, qR, n):
+        """The common inviscid normal flux of the face: Rusanov or Roe."""
+        return self.roe(qL, qR, n) if self.flux_kind == "roe" else self.rusanov(qL, qR, n)
+
+    def roe_average(self, qL, qR):
+        """Roe's averages (Roe 1981): sqrt(rho)-weighted velocity and total
+        enthalpy H = (rho E + p) / rho, and the sound speed from them."""
+        g = self.gamma
+        rL, vL, pL = self.primitives(qL)
+        rR, vR, pR = self.primitives(qR)
+        sL, sR = torch.sqrt(rL), torch.sqrt(rR)
+        HL = (qL[:, self.nd + 1] + pL) / rL
+        HR = (qR[:, self.nd + 1] + pR) / rR
+        w = sL + sR
+        u = (sL[:, None] * vL + sR[:, None] * vR) / w[:, None]
+        H = (sL * HL + sR * HR) / w
+        c = torch.sqrt((g - 1.0) * (H - 0.5 * (u * u).sum(1)))
+        return u, H, c
+
+    def roe_eigensystem(self, u, H, c, n):
+        """Eigenvalues and right eigenvectors of the normal flux Jacobian
+        d(f.n)/dq at the averaged state (velocity u, enthalpy H, sound speed c):
+        u.n - c, u.n (entropy and nd - 1 shear waves along tangents of n),
+        u.n + c.  Points are moved to the leading axes: lam [..., nv],
+        R [..., nv, nv] with the eigenvectors as columns."""
+        nd, nv = self.nd, self.nv
+        # points first: [N, nd, *pts] -> [N, *pts, nd]
+        perm = (0,) + tuple(range(2, u.dim())) + (1,)
+        u, n = u.permute(perm), n.permute(perm)
+        H, c = H, c
+        un = (u * n).sum(-1)
+        # tangents: e_i minus its normal part for the axis least aligned with n,
+        # then (3D) the cross product completes the frame
+        ai = torch.argmin(torch.abs(n), dim=-1)
+        e = torch.nn.functional.one_hot(ai, nd).to(n.dtype)
+        t1 = e - (e * n).sum(-1, keepdim=True) * n
+        t1 = t1 / torch.sqrt((t1 * t1).sum(-1, keepdim=True))
+        tans = [t1]
+        if nd == 3:
+            tans.append(torch.linalg.cross(n, t1, dim=-1))
+        one = torch.ones_like(un)
+        zero = torch.zeros_like(un)
+        cols = [torch.cat([one[..., None], u - c[..., None] * n, (H - c * un)[..., None]], -1),
+                torch.cat([one[..., None], u, (0.5 * (u * u).sum(-1))[..., None]], -1)]
+        for t in tans:
+            cols.append(torch.cat([zero[..., None], t, (u * t).sum(-1)[..., None]], -1))
+        cols.append(torch.cat([one[..., None], u + c[..., None] * n, (H + c * un)[..., None]], -1))
+        R = torch.stack(cols, dim=-1)
+        lam = torch.stack([un - c] + [un] * nd + [un + c], dim=-1)
+        return lam, R
+
+    def roe(self, qL, qR, n):
+        """Roe's common normal flux (the paper's Sec. 2.2 formula): average of
+        the two normal fluxes minus half of R |Lambda| R^-1 (qR - qL), the
+        eigensystem of the normal flux Jacobian at Roe's averaged state.  No
+        entropy fix (the paper names none); |x| is the branch x < 0 ? -x : x
+        (derivative +1 at 0, as in the wave speed)."""
+        fL = (self.flux(qL) * n[:, :, None]).sum(1)
+        fR = (self.flux(qR) * n[:, :, None]).sum(1)
+        u, H, c = self.roe_average(qL, qR)
+        lam, R = self.roe_eigensystem(u, H, c, n)
+        perm = (0,) + tuple(range(2, qL.dim())) + (1,)
+        dq = (qR - qL).permute(perm)
+        alpha = torch.linalg.solve(R, dq[..., None])[..., 0]        # wave strengths R^-1 dq
+        diss = (R @ (torch.where(lam < 0, -lam, lam) * alpha)[..., None])[..., 0]
+        inv = [0, qL.dim() - 1] + list(range(1, qL.dim() - 1))
+        return 0.5 * (fL + fR) - 0.5 * diss.permute(inv)
 
     # -- viscous --------------------------------------------------------------
     def viscous_flux(self, q, G):
@@ -115,3 +186,7 @@ class Advection:
     def rusanov(self, qL, qR, n):
         an = (self.a.reshape((1, self.nd) + (1,) * (n.dim() - 2)) * n).sum(1)
         return 0.5 * an[:, None] * (qL + qR) - 0.5 * torch.abs(an)[:, None] * (qR - qL)
+
+    def common_flux(self, qL, qR, n):
+        """The upwind flux (for a scalar the Roe and Rusanov fluxes coincide)."""
+        return self.rusanov(qL, qR, n)

@@ -49,13 +49,13 @@ def oracle_fr(mesh, phys):
     from oracle.fr import FR
     from oracle.physics import Euler
     return FR(mesh, Euler(mesh.nd, phys["gamma"], phys.get("mu", 0.0), phys.get("Pr", 0.72),
-                          phys.get("q_inf")))
+                          phys.get("q_inf"), flux=phys.get("flux", "rusanov")))
 
 
 def gpu_ctx(mesh, phys, p_min=None, p_max=None):
     from paper_1910_03693_gb300 import FRContext
     return FRContext(mesh, gamma=phys["gamma"], mu=phys.get("mu", 0.0), Pr=phys.get("Pr", 0.72),
-                     q_inf=phys.get("q_inf"), p_min=p_min, p_max=p_max)
+                     q_inf=phys.get("q_inf"), p_min=p_min, p_max=p_max, flux=phys.get("flux", "rusanov"))
 
 
 def rel_err(a, b):
