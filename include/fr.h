@@ -95,12 +95,18 @@ typedef struct {
 } fr_mesh_desc;
 
 /* Physics (Sec. 2.1): gamma, constant mu (0 = Euler) and Pr; q_inf is the
- * conservative free-stream state used by far-field boundaries (nv values). */
+ * conservative free-stream state used by far-field boundaries (nv values).
+ * flux: the common inviscid flux of the faces (Sec. 2.2), FR_FLUX_RUSANOV or
+ * FR_FLUX_ROE (Roe's averaged-Jacobian flux, no entropy fix); both have the
+ * exact JVP and VJP. */
+#define FR_FLUX_RUSANOV 0
+#define FR_FLUX_ROE 1
 typedef struct {
   double gamma;
   double mu;
   double Pr;
   double q_inf[5];
+  int32_t flux;
 } fr_physics;
 
 /* Degree range of the context.  1 <= p_min <= p_max <= 5.  Every buffer the

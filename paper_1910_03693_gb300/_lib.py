@@ -27,7 +27,10 @@ class MeshDesc(C.Structure):
 
 class Physics(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("Pr", C.c_double),
-                ("q_inf", C.c_double * 5)]
+                ("q_inf", C.c_double * 5), ("flux", C.c_int32)]
+
+
+FLUX = {"rusanov": 0, "roe": 1}
 
 
 class Limits(C.Structure):

@@ -81,7 +81,7 @@ class FRContext:
     with the conventions of ``include/fr.h``.
     """
 
-    def __init__(self, mesh, gamma=1.4, mu=0.0, Pr=0.72, q_inf=None, p_min=None, p_max=None):
+    def __init__(self, mesh, gamma=1.4, mu=0.0, Pr=0.72, q_inf=None, p_min=None, p_max=None, flux="rusanov"):
         p = np.ascontiguousarray(mesh.p, dtype=np.int8)
         p_min = int(p.min()) if p_min is None else int(p_min)
         p_max = int(p.max()) if p_max is None else int(p_max)
@@ -102,7 +102,9 @@ class FRContext:
         if q_inf is not None:
             for k, v in enumerate(np.asarray(q_inf, dtype=np.float64).reshape(-1)[:5]):
                 qi[k] = float(v)
-        ph = _lib.Physics(float(gamma), float(mu), float(Pr), qi)
+        if flux not in _lib.FLUX:
+            raise ValueError(f"common flux must be one of {sorted(_lib.FLUX)}, not {flux!r}")
+        ph = _lib.Physics(float(gamma), float(mu), float(Pr), qi, _lib.FLUX[flux])
         lim = _lib.Limits(p_min, p_max)
         h = C.c_void_p()
         torch.cuda.init()

@@ -332,8 +332,9 @@ static fr_status create_impl(const fr_mesh_desc* m, const fr_physics* ph, const 
     set_error("fr_create: need 1 <= p_min <= p_max <= 5");
     return FR_ERR_INVALID;
   }
-  if (!(ph->gamma > 1.0) || ph->mu < 0.0 || (ph->mu > 0.0 && !(ph->Pr > 0.0))) {
-    set_error("fr_create: need gamma > 1, mu >= 0, Pr > 0");
+  if (!(ph->gamma > 1.0) || ph->mu < 0.0 || (ph->mu > 0.0 && !(ph->Pr > 0.0)) ||
+      (ph->flux != FR_FLUX_RUSANOV && ph->flux != FR_FLUX_ROE)) {
+    set_error("fr_create: need gamma > 1, mu >= 0, Pr > 0 and a known common flux");
     return FR_ERR_INVALID;
   }
   c->nd = m->nd;
@@ -349,6 +350,7 @@ static fr_status create_impl(const fr_mesh_desc* m, const fr_physics* ph, const 
   c->phys.Pr = ph->Pr;
   c->phys.kappa = c->visc ? ph->mu * ph->gamma / ((ph->gamma - 1.0) * ph->Pr) : 0.0;
   for (int v = 0; v < 5; ++v) c->phys.q_inf[v] = ph->q_inf[v];
+  c->phys.flux = ph->flux;
   const int nd = c->nd, nf = c->nf, E = c->E, nn = c->geom_order + 1;
   c->nodes.assign(m->nodes, m->nodes + (size_t)E * ipow(nn, nd) * nd);
   c->nbr.assign(m->nbr, m->nbr + (size_t)E * nf);

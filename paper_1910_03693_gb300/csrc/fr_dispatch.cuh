@@ -342,6 +342,7 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
     a.gamma = (T)c->phys.gamma;
     a.mu = (T)c->phys.mu;
     a.kappa = (T)c->phys.kappa;
+    a.flux = c->phys.flux;
     a.n = g.n;
     a.Pm = g.pm + 1;
     a.Ps = g.ps + 1;
@@ -370,6 +371,7 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
     a.gamma = (T)c->phys.gamma;
     a.mu = (T)c->phys.mu;
     a.kappa = (T)c->phys.kappa;
+    a.flux = c->phys.flux;
     for (int v = 0; v < 5; ++v) a.qinf[v] = (T)c->phys.q_inf[v];
     a.n = g.n;
     a.P = g.p + 1;
@@ -475,6 +477,7 @@ static void vjp_impl(fr_ctx* c, const T* q, const T* w, T* out, cudaStream_t s) 
     a.gamma = (T)c->phys.gamma;
     a.mu = (T)c->phys.mu;
     a.kappa = (T)c->phys.kappa;
+    a.flux = c->phys.flux;
     a.n = g.n;
     a.Pm = g.pm + 1;
     a.Ps = g.ps + 1;
@@ -498,6 +501,7 @@ static void vjp_impl(fr_ctx* c, const T* q, const T* w, T* out, cudaStream_t s) 
     a.gamma = (T)c->phys.gamma;
     a.mu = (T)c->phys.mu;
     a.kappa = (T)c->phys.kappa;
+    a.flux = c->phys.flux;
     for (int v = 0; v < 5; ++v) a.qinf[v] = (T)c->phys.q_inf[v];
     a.n = g.n;
     a.P = g.p + 1;

@@ -96,6 +96,7 @@ struct BndGroup {
 struct PhysParams {
   double gamma, mu, Pr, kappa;
   double q_inf[5];
+  int flux;   // FR_FLUX_RUSANOV or FR_FLUX_ROE
 };
 
 }  // namespace frgb

@@ -269,6 +269,7 @@ struct FaceArgs {
   GeoView<T> geo_m, geo_s;
   T gamma, mu, kappa;
   int n, Pm, Ps, nvt;
+  int flux;            // common inviscid flux: 0 Rusanov, 1 Roe
   int64_t scratch_base;
 };
 
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
     n[j] = A[j] * inv_absA;
   }
   S Fn[NV];
-  rusanov<ND>(qM, qS, n, absA, a.gamma, Fn);
+  common_flux<ND>(a.flux, qM, qS, n, absA, a.gamma, Fn);
   S qc[NV];
   if (VISC) {
 #pragma unroll
@@ -519,6 +520,7 @@ struct BndArgs {
   T gamma, mu, kappa;
   T qinf[5];
   int n, P, kind;
+  int flux;            // common inviscid flux: 0 Rusanov, 1 Roe
 };
 
 template <typename T, int ND, bool VISC, int MODE>
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(128) bnd_kernel(BndArgs<T> a) {
     n[j] = A[j] * inv_absA;
   }
   S Fn[NV];
-  rusanov<ND>(qM, qG, n, absA, a.gamma, Fn);
+  common_flux<ND>(a.flux, qM, qG, n, absA, a.gamma, Fn);
   S qc[NV];
   if (VISC) {
 #pragma unroll

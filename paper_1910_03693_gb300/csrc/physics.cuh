@@ -168,6 +168,81 @@ __device__ __forceinline__ S normal_flux(const S* q, const T* n, T gamma, S* fn)
   return dabs(un) + dsqrt(gamma * pres * rinv);
 }
 
+// Normal flux f(q).n alone (no wave speed).
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void normal_flux_only(const S* q, const T* n, T gamma, S* fn) {
+  constexpr int NV = ND + 2;
+  const S rinv = T(1) / q[0];
+  S mn = szero<S>(), mu2 = szero<S>();
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    mn = mn + q[1 + i] * n[i];
+    mu2 = mu2 + q[1 + i] * q[1 + i];
+  }
+  const S un = mn * rinv;
+  const S pres = (gamma - T(1)) * (q[NV - 1] - T(0.5) * mu2 * rinv);
+  fn[0] = mn;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) fn[1 + i] = q[1 + i] * un + pres * n[i];
+  fn[NV - 1] = (q[NV - 1] + pres) * un;
+}
+
+// Roe's flux times the face area: ((fL.n + fR.n)/2 - |A| (qR - qL)/2) |A_f|,
+// |A| the absolute normal flux Jacobian at Roe's averages (sqrt(rho)-weighted
+// velocity and total enthalpy), applied through the closed-form wave
+// strengths of the acoustic (u.n -+ c), entropy and shear (u.n) waves instead
+// of the eigenvector matrices.  No entropy fix; |x| via dabs (sign(0) = +1).
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void roe(const S* qL, const S* qR, const T* n, T absA, T gamma, S* Fn) {
+  constexpr int NV = ND + 2;
+  S fL[NV], fR[NV];
+  normal_flux_only<ND>(qL, n, gamma, fL);
+  normal_flux_only<ND>(qR, n, gamma, fR);
+  const S riL = T(1) / qL[0], riR = T(1) / qR[0];
+  S uL[ND], uR[ND], kL = szero<S>(), kR = szero<S>();
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    uL[i] = qL[1 + i] * riL;
+    uR[i] = qR[1 + i] * riR;
+    kL = kL + qL[1 + i] * uL[i];
+    kR = kR + qR[1 + i] * uR[i];
+  }
+  const S pL = (gamma - T(1)) * (qL[NV - 1] - T(0.5) * kL);
+  const S pR = (gamma - T(1)) * (qR[NV - 1] - T(0.5) * kR);
+  const S HL = (qL[NV - 1] + pL) * riL, HR = (qR[NV - 1] + pR) * riR;
+  const S sL = dsqrt(qL[0]), sR = dsqrt(qR[0]);
+  const S wi = T(1) / (sL + sR);
+  S u[ND], q2 = szero<S>(), un = szero<S>(), dun = szero<S>(), udu = szero<S>();
+  S du[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    u[i] = (sL * uL[i] + sR * uR[i]) * wi;
+    du[i] = uR[i] - uL[i];
+    q2 = q2 + u[i] * u[i];
+    un = un + u[i] * n[i];
+    dun = dun + du[i] * n[i];
+    udu = udu + u[i] * du[i];
+  }
+  const S H = (sL * HL + sR * HR) * wi;
+  const S c2 = (gamma - T(1)) * (H - T(0.5) * q2);
+  const S c = dsqrt(c2);
+  const S rho = sL * sR;
+  const S dp = pR - pL, drho = qR[0] - qL[0];
+  const S ic2 = T(1) / c2;
+  const S a1 = T(0.5) * (dp - rho * c * dun) * ic2;
+  const S a3 = T(0.5) * (dp + rho * c * dun) * ic2;
+  const S a2 = drho - dp * ic2;
+  const S l1 = dabs(un - c) * a1, l2 = dabs(un), l3 = dabs(un + c) * a3;
+  S d[NV];
+  d[0] = l1 + l2 * a2 + l3;
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+    d[1 + i] = l1 * (u[i] - c * n[i]) + l2 * (a2 * u[i] + rho * (du[i] - dun * n[i])) + l3 * (u[i] + c * n[i]);
+  d[NV - 1] = l1 * (H - c * un) + l2 * (a2 * T(0.5) * q2 + rho * (udu - un * dun)) + l3 * (H + c * un);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fn[v] = (T(0.5) * (fL[v] + fR[v]) - T(0.5) * d[v]) * absA;
+}
+
 // Rusanov normal flux times the face area: ((fL.n + fR.n)/2 - lam/2 (qR - qL)) |A|,
 // lam = max(|u.n| + c) over the two sides (the "-" side at a tie).
 template <int ND, typename S, typename T>
@@ -180,6 +255,14 @@ __device__ __forceinline__ void rusanov(const S* qL, const S* qR, const T* n, T 
   const S lam = dmax(lamL, lamR);
 #pragma unroll
   for (int v = 0; v < NV; ++v) Fn[v] = (T(0.5) * (fL[v] + fR[v]) - T(0.5) * lam * (qR[v] - qL[v])) * absA;
+}
+
+// The common inviscid flux of a face: Rusanov (kind 0) or Roe (kind 1).
+template <int ND, typename S, typename T>
+__device__ __forceinline__ void common_flux(int kind, const S* qL, const S* qR, const T* n, T absA, T gamma,
+                                            S* Fn) {
+  if (kind == 1) roe<ND>(qL, qR, n, absA, gamma, Fn);
+  else rusanov<ND>(qL, qR, n, absA, gamma, Fn);
 }
 
 // Viscous flux fv[j][v] from q and its physical gradient G[j][v]:

@@ -95,10 +95,11 @@ __device__ __forceinline__ void flux_adjoint_q(const T* q, const T (*G)[ND + 2],
   }
 }
 
-// (qLb, qRb) += (d Fn / d(qL, qR))^T Fnb for the Rusanov flux (area included).
+// (qLb, qRb) += (d Fn / d(qL, qR))^T Fnb for the common flux of kind `kind`
+// (Rusanov or Roe, area included): one forward-mode column per input.
 template <int ND, typename T>
-__device__ __forceinline__ void rusanov_adjoint(const T* qL, const T* qR, const T* n, T absA, T gamma,
-                                                const T* Fnb, T* qLb, T* qRb) {
+__device__ __forceinline__ void flux_adjoint(int kind, const T* qL, const T* qR, const T* n, T absA, T gamma,
+                                             const T* Fnb, T* qLb, T* qRb) {
   constexpr int NV = ND + 2;
   using D = Dual<T>;
 #pragma unroll 1
@@ -109,7 +110,7 @@ __device__ __forceinline__ void rusanov_adjoint(const T* qL, const T* qR, const 
       a[v] = D{qL[v], k == v ? T(1) : T(0)};
       b[v] = D{qR[v], k == NV + v ? T(1) : T(0)};
     }
-    rusanov<ND>(a, b, n, absA, gamma, Fn);
+    common_flux<ND>(kind, a, b, n, absA, gamma, Fn);
     T acc = T(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc += Fnb[v] * Fn[v].d;
@@ -311,6 +312,7 @@ struct FaceAdjArgs {
   GeoView<T> geo_m, geo_s;
   T gamma, mu, kappa;
   int n, Pm, Ps;
+  int flux;            // common inviscid flux: 0 Rusanov, 1 Roe
   int64_t scratch_base;
 };
 
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(128) face_adj_kernel(FaceAdjArgs<T> a) {
       }
     }
   }
-  rusanov_adjoint<ND>(qM, qS, n, absA, a.gamma, Fnb, qMb, qSb);
+  flux_adjoint<ND>(a.flux, qM, qS, n, absA, a.gamma, Fnb, qMb, qSb);
   T GMb[ND][NV], GSb[ND][NV];
   if (VISC) {
     T qc[NV], cM[ND], cS[ND];
@@ -550,6 +552,7 @@ struct BndAdjArgs {
   T gamma, mu, kappa;
   T qinf[5];
   int n, P, kind;
+  int flux;            // common inviscid flux: 0 Rusanov, 1 Roe
 };
 
 template <typename T, int ND, bool VISC>
@@ -583,7 +586,7 @@ __global__ void __launch_bounds__(128) bnd_adj_kernel(BndAdjArgs<T> a) {
     qMb[v] = VISC ? -fbm[(NV + v) * NFP + t] : T(0);
     qGb[v] = T(0);
   }
-  rusanov_adjoint<ND>(qM, qG, n, absA, a.gamma, Fnb, qMb, qGb);
+  flux_adjoint<ND>(a.flux, qM, qG, n, absA, a.gamma, Fnb, qMb, qGb);
   T GMb[ND][NV];
   if (VISC) {
     T qc[NV], cM[ND];
