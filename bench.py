@@ -299,6 +299,23 @@ def op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=5, names=None):
     return res
 
 
+def roe_ops(m, q, ph, peak_gbs):
+    """The same operators with Roe's common flux instead of Rusanov (the
+    paper's flux): FP64, double-float and FP32 residual and the FP32 exact JVP
+    on the bench workload, graph-replayed as in op_throughput."""
+    import torch
+    from paper_1910_03693_gb300 import FRContext
+    ctx = FRContext(m, gamma=ph["gamma"], mu=ph.get("mu", 0.0), Pr=ph.get("Pr", 0.72), flux="roe")
+    q64 = ctx.pack(torch.from_numpy(q).cuda())
+    ctx.autotune(q64)
+    r = op_throughput(ctx, q64, ctx.n_dof, peak_gbs, reps=10, runs=3,
+                      names=("residual_f64", "residual_df", "residual_f32", "jvp_exact_f32"))
+    out = {k: {"gdof_s": v["gdof_s"], "ms": v["ms"]} for k, v in r.items()}
+    del ctx
+    torch.cuda.empty_cache()
+    return out
+
+
 def mixed_degree_ops(peak_gbs):
     """Mixed-degree workloads (several buckets): FP64 residual and FP32 exact JVP
     throughput with one launch per degree bucket, with the persistent
@@ -545,6 +562,7 @@ def main():
     bf = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype="bf16op")
     f64F = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype=torch.float32, low_above=0.0)
     mixed = mixed_degree_ops(peak) if args.n == 32 else None
+    roe = roe_ops(m, q, ph, peak)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
@@ -567,6 +585,7 @@ def main():
         "roofline": roof,
         "ops": ops,
         "mixed_degree_ops": mixed,
+        "roe_flux_ops": roe,
         "stage_modes": {"exact_f32_jvp_ms": round(total_ms / args.steps, 3),
                         "exact_f32_jvp_final_abs": stats[-1]["norm_final"],
                         "fd_f64": fd, "exact_bf16op_jvp": bf, "exact_f32_jvp_f64_F": f64F},
