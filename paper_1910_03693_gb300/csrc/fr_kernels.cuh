@@ -131,99 +131,9 @@ struct VolCfg {
 // block reaches the barriers (threads beyond epb*NSP only help to synchronise).
 // DIAG: every metric S is diagonal (axis-aligned affine elements): only S[d][d]
 // is read and the metric products reduce to one multiply per component.
-// Traces on axis-aligned boxes (3D, diagonal metrics), by lines: each
-// reference derivative then feeds exactly one component of the physical
-// gradient, so every output is written by the thread that computes it.
-// Phase 1, one thread per element line along each axis: the P values of the
-// line give q at both ends and the normal derivative there (4 outputs a
-// variable from P loads).  Phase 2, one thread per line of a face along one of
-// its two tangential axes: the P face values give the P tangential
-// derivatives.  Same shared-memory layout and outputs as trace_body.
-template <typename T, int P, bool VISC>
-__device__ __forceinline__ void trace_body_lines(const TraceArgs<T>& a, int64_t i0, int epb, unsigned char* smem_raw) {
-  using Sh = Shape<3, P>;
-  constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int le = threadIdx.x / NSP;
-  const int lt = threadIdx.x % NSP;
-  const int64_t i = i0 + le;
-  const bool valid = le < epb && i < a.count;
-  T* sq = sm + le * (NV * NSP + NF * NV * NFP);   // [NV][NSP]
-  T* sqf = sq + NV * NSP;                           // [NF][NV][NFP]
-  const BasisTab<T>& B = a.basis[P];
-  if (valid) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sq[v * NSP + lt] = load_state(a.q, a.state_base + (i * NV + v) * NSP + lt);
-  }
-  __syncthreads();
-  T* out = a.trace + a.trace_base + (valid ? i * NF * (int64_t)a.nvt * NFP : 0);
-  const int64_t e = valid ? a.slot_elem[a.slot_begin + i] : 0;
-  if (valid) {
-    for (int L = lt; L < 3 * NFP; L += NSP) {
-      const int d = L / NFP, t = L % NFP;
-      T cg[2];
-      if (VISC) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-          cg[s] = geo_face(a.geo, e, 2 * d + s, d * 3 + d, t) * geo_face(a.geo, e, 2 * d + s, 3 * 3 + 1, t);
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        T x[P];
-#pragma unroll
-        for (int k = 0; k < P; ++k) x[k] = sq[v * NSP + line_sp<3, P>(d, t, k)];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const int f = 2 * d + s;
-          Acc<T> ex = acc_init(T(0));
-#pragma unroll
-          for (int k = 0; k < P; ++k) acc_madd(ex, B.ext[s][k], x[k]);
-          const T qv = acc_value(ex);
-          out[(f * a.nvt + v) * NFP + t] = qv;
-          if (VISC) {
-            sqf[(f * NV + v) * NFP + t] = qv;
-            Acc<T> dn = acc_init(T(0));
-#pragma unroll
-            for (int k = 0; k < P; ++k) acc_madd(dn, B.dext[s][k], x[k]);
-            out[(f * a.nvt + NV + d * NV + v) * NFP + t] = cg[s] * acc_value(dn);
-          }
-        }
-      }
-    }
-  }
-  if (!VISC) return;
-  __syncthreads();
-  if (!valid) return;
-  for (int L = lt; L < NF * 2 * P; L += NSP) {
-    const int f = L / (2 * P), r = L % (2 * P), which = r / P, line = r % P;
-    const int d = f >> 1;
-    const int j = which == 0 ? (d == 0 ? 1 : 0) : (d == 2 ? 1 : 2);   // the tangential axis
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T* face = sqf + (f * NV + v) * NFP;
-      T x[P];
-#pragma unroll
-      for (int m = 0; m < P; ++m) x[m] = face[which == 0 ? m + P * line : line + P * m];
-#pragma unroll
-      for (int o = 0; o < P; ++o) {
-        const int t = which == 0 ? o + P * line : line + P * o;
-        Acc<T> g = acc_init(T(0));
-#pragma unroll
-        for (int m = 0; m < P; ++m) acc_madd(g, B.D[o][m], x[m]);
-        const T c = geo_face(a.geo, e, f, j * 3 + j, t) * geo_face(a.geo, e, f, 3 * 3 + 1, t);
-        out[(f * a.nvt + NV + j * NV + v) * NFP + t] = c * acc_value(g);
-      }
-    }
-  }
-}
-
 template <typename T, int ND, int P, bool VISC, bool DIAG = false>
 __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, int epb, unsigned char* smem_raw) {
   using Sh = Shape<ND, P>;
-  if constexpr (DIAG && ND == 3) {
-    trace_body_lines<T, P, VISC>(a, i0, epb, smem_raw);
-    return;
-  }
   constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int le = threadIdx.x / NSP;
