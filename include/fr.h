@@ -309,9 +309,7 @@ fr_status fr_filter(fr_ctx* ctx, double* q_dev, double alpha, int32_t p_above, v
  * rounding of the remainder), op 0 a + b, 1 a - b, 2 a * b, 3 a * b + c,
  * 4 a / b, 5 sqrt(a), and the result is written as the FP64 value of its
  * two parts.  b is read for ops 0-4, c for op 3 (else they may be null).
- * Op 6 instead writes a rounded to FP32 by the integer-pipe rounding the
- * Arnoldi update uses for the FP32 copy of its column (IEEE round to nearest
- * even).  Exposed for checking the arithmetic against exact results. */
+ * Exposed for checking the arithmetic against exact rational results. */
 fr_status fr_dfloat_eval(int32_t op, const double* a, const double* b, const double* c, double* out, int64_t n,
                          void* stream);
 

@@ -390,13 +390,12 @@ class FRContext:
         return perm
 
 
-DFLOAT_OPS = {"add": 0, "sub": 1, "mul": 2, "fma": 3, "div": 4, "sqrt": 5, "round_f32": 6}
+DFLOAT_OPS = {"add": 0, "sub": 1, "mul": 2, "fma": 3, "div": 4, "sqrt": 5}
 
 
 def dfloat_eval(op, a, b=None, c=None):
     """One double-float operation of the FR_DF arithmetic, elementwise on FP64
-    CUDA tensors: "add", "sub", "mul", "fma" (a * b + c), "div", "sqrt"; or
-    "round_f32", the integer-pipe FP64 -> FP32 rounding (result as FP64)."""
+    CUDA tensors: "add", "sub", "mul", "fma" (a * b + c), "div", "sqrt"."""
     a = _dev(a, "a")
     out = torch.empty_like(a)
     ptr = lambda t: _ptr(_dev(t, "operand")) if t is not None else None

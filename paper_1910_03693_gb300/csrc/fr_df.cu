@@ -5,7 +5,6 @@
 // device from the FP64 ones the first time they are needed.
 #include <algorithm>
 
-#include "convert.cuh"
 #include "dfloat.cuh"
 #include "fr_launch.h"
 
@@ -94,7 +93,6 @@ __global__ void k_df_eval(int op, const double* a, const double* b, const double
       case 3: r = dfma(x, y, z); break;
       case 4: r = x / y; break;
       case 5: r = dsqrt(x); break;
-      case 6: out[i] = (double)f32_from_f64_rn(a[i]); continue;
       default: r = x; break;
     }
     out[i] = to_double(r);
@@ -106,7 +104,7 @@ using namespace frgb;
 extern "C" fr_status fr_dfloat_eval(int32_t op, const double* a, const double* b, const double* c, double* out,
                                     int64_t n, void* stream) {
   const bool need_b = op >= 0 && op <= 4, need_c = op == 3;
-  if (op < 0 || op > 6 || n < 0 || !a || !out || (need_b && !b) || (need_c && !c)) {
+  if (op < 0 || op > 5 || n < 0 || !a || !out || (need_b && !b) || (need_c && !c)) {
     set_error("fr_dfloat_eval: bad argument");
     return FR_ERR_INVALID;
   }

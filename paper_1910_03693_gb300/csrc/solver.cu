@@ -10,7 +10,6 @@
 #include <cstring>
 #include <vector>
 
-#include "convert.cuh"
 #include "fr_launch.h"
 
 namespace frgb {
@@ -164,13 +163,13 @@ struct Slots {
       p[2 * nw] = x[0];
     }
   }
-  // the same slot rounded to FP32 on the integer pipe (8-byte stores of pairs)
+  // the same slot rounded to FP32 (8-byte stores of pairs)
   __device__ static void store32(float* __restrict__ p, int64_t q, int64_t nw, int64_t n, const double (&x)[2]) {
     if (q < nw) {
-      if (VEC) *reinterpret_cast<float2*>(p + 2 * q) = make_float2(f32_from_f64_rn(x[0]), f32_from_f64_rn(x[1]));
-      else p[q] = f32_from_f64_rn(x[0]);
+      if (VEC) *reinterpret_cast<float2*>(p + 2 * q) = make_float2((float)x[0], (float)x[1]);
+      else p[q] = (float)x[0];
     } else if (VEC && q == nw && (n & 1)) {
-      p[2 * nw] = f32_from_f64_rn(x[0]);
+      p[2 * nw] = (float)x[0];
     }
   }
 };
