@@ -163,15 +163,6 @@ struct Slots {
       p[2 * nw] = x[0];
     }
   }
-  // the same slot rounded to FP32 (8-byte stores of pairs)
-  __device__ static void store32(float* __restrict__ p, int64_t q, int64_t nw, int64_t n, const double (&x)[2]) {
-    if (q < nw) {
-      if (VEC) *reinterpret_cast<float2*>(p + 2 * q) = make_float2((float)x[0], (float)x[1]);
-      else p[q] = (float)x[0];
-    } else if (VEC && q == nw && (n & 1)) {
-      p[2 * nw] = (float)x[0];
-    }
-  }
 };
 
 // Slots handled per thread and loop step: U slots spaced one grid apart, all
@@ -291,8 +282,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
 // block that finishes the norm also stores 1/||w_out|| there (0 for a zero
 // vector) and next_j into *jidx: the scale and index of the next Arnoldi
 // product, set without a round trip through the host (the host computes the
-// same IEEE quotient for its own copy).  With x32, the new column is also
-// written rounded to FP32: the input of the next FP32 Arnoldi product.
+// same IEEE quotient for its own copy).
 template <int KC, bool VEC, typename WT, bool NEG>
 __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __restrict__ V, int64_t ldv, int k,
                                                               const double* __restrict__ raw,
@@ -300,7 +290,7 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
                                                               double* w_out, int64_t n, double* __restrict__ partial,
                                                               double* __restrict__ out, unsigned* __restrict__ ticket,
                                                               double* __restrict__ next_scale, int* __restrict__ jidx,
-                                                              int next_j, float* __restrict__ x32) {
+                                                              int next_j) {
   constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
   using L = Slots<VEC>;
   using LW = WSlots<VEC, WT, NEG>;
@@ -337,7 +327,6 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       L::store(w_out, q0 + u * stride, nw, n, x[u]);
-      if (x32) L::store32(x32, q0 + u * stride, nw, n, x[u]);
       accu[u] = fma(x[u][1], x[u][1], fma(x[u][0], x[u][0], accu[u]));
     }
   }
@@ -470,18 +459,17 @@ __global__ void k_gather_col(const double* __restrict__ V, int64_t ld, const int
     x[i] = (T)src[i] * sc;
 }
 
-// One Arnoldi product of the exact mode into w, in FP64, by the JVP kernels
-// (q traces prepared beforehand) whose volume kernel writes -J x straight
-// into w.  FP64 products: x = v_j = s_j V[j], gathered into a fixed buffer (j
-// read from device memory), so w = -J v_j.  FP32 products: x is the FP32 copy
-// of the stored column u_j = V[j] that the orthogonalisation wrote (the first
-// column's by a cast), so w = -J u_j and the caller applies s_j.  Replayed
-// from a CUDA graph captured on first use and again whenever q, V, w or the
-// timing state changed (the layout and the launch tuning drop it); launched
-// directly when graphs are off or cannot be used.
-static void gather_col(fr_ctx* c, const double* V, int64_t ld, double* x, int64_t n, cudaStream_t s) {
+// One Arnoldi product w = -J(q) v_j of the exact mode, v_j = s_j V[j]: gather
+// into a fixed buffer (j read from device memory), then the JVP kernels (q
+// traces prepared beforehand), whose volume kernel writes -J v_j in FP64
+// straight into w.  Replayed from a CUDA graph captured on first use and again
+// whenever q, V, w or the timing state changed (the layout and the launch
+// tuning drop it); launched directly when graphs are off or cannot be used.
+static void gather_col(fr_ctx* c, int pi, const double* V, int64_t ld, void* x, int64_t n, cudaStream_t s) {
+  const double nb = (double)n * (8 + (pi ? 4 : 8));
   const double* sc = c->d_red + kOutS;
-  FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_gather_col<double><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, sc, x, n));
+  if (pi) FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<float><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, sc, (float*)x, n));
+  else FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<double><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, sc, (double*)x, n));
 }
 
 static void release_graph_timers(fr_ctx* c, int pi) {
@@ -503,10 +491,8 @@ static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double*
   void* x = pi ? (void*)vec32(c, 1) : (void*)vec64(c, 10);
   if (!qptr || !x) return FR_ERR_NOMEM;
   collect_graph_timers(c);
-  // FP64 products gather s_j V[j]; FP32 products read the FP32 copy of the
-  // stored column u_j that the orthogonalisation wrote (the caller scales)
   auto direct = [&](cudaStream_t st) -> fr_status {
-    if (!pi) gather_col(c, V, ld, (double*)x, n, st);
+    gather_col(c, pi, V, ld, x, n, st);
     return launch_jvp_prepared_neg64(c, qptr, x, w, prec, st);
   };
   if (!c->use_graphs || !c->jvp_graph_ok) return direct(s);
@@ -605,11 +591,8 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
 
 // GMRES(m) with x0 = 0.  R0 (optional) = R(q) for the finite-difference mode.
 // b_norm: ||b|| when the caller already has it, else negative.
-// sync_at_end: return only when x is complete (the public call); the stage
-// passes false and lets its next residual overlap the final combination.
 static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0, const double* b, double* x,
-                            const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s, double b_norm = -1.0,
-                            bool sync_at_end = true) {
+                            const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s, double b_norm = -1.0) {
   const int m = o->m;
   const int64_t n = c->n_dof, ld = krylov_ld(c);
   if (m < 1 || m + 1 > kMaxK || o->max_it < 1 || !(o->rtol > 0.0) || o->reorth < 0 || o->reorth > 2) {
@@ -694,20 +677,13 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   // then w_out = w_in - sum s_i^2 raw_i u_i with ||w_out||^2 into N
   // (the update also stores the scale of the new column and the index of
   // the next product on the device: kk is the new column's index)
-  // FP32 exact products read the stored column u_j in FP32 (written by the
-  // update, or cast for the first column) and return -J u_j: the dots, the
-  // norm and the second pass of that step then carry 1/s_j, which the host
-  // multiplies back (the projection itself is scale-free).
-  const bool col32 = exact && op->jv_prec != FR_F64;
-  float* x32 = col32 ? vec32(c, 1) : nullptr;
-  if (col32 && !x32) return FR_ERR_NOMEM;
   auto gs_pass = [&](int kk, const double* w_in, double* w_out, double* raw, int with_norm) {
     FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
                 FR_KC_DISPATCH(kk, vec, grid, k_multidot, double, false, V, ld, kk, w_in, n, part, raw, ticket,
                                with_norm));
-    FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2) + (x32 ? 4.0 * n : 0.0),
+    FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
                 FR_KC_DISPATCH(kk, vec, grid, k_orth_update, double, false, V, ld, kk, raw, sdev, w_in, w_out, n,
-                               part, c->d_red + kOutN, ticket, sdev + kk, c->d_jidx, kk, x32));
+                               part, c->d_red + kOutN, ticket, sdev + kk, c->d_jidx, kk));
   };
   bool first = true;
   while (true) {
@@ -724,7 +700,6 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       break;
     }
     FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(r, 1.0 / beta, V, n));
-    if (col32) vcast_f64_f32(c, V, x32, n, s);
     set_scale(0, 1.0);
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
@@ -740,9 +715,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
         FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(V + (int64_t)j * ld, sh[j], xs, n));
         if ((e = apply_op(c, op, R0, xs, w, s, false)) != FR_OK) return e;
       }
-      // the product was taken of u_j (FP32 path, factor 1/s_j in w) or of v_j = s_j u_j
-      const double sj = col32 ? sh[j] : 1.0;
-      if (pc && (e = precond_apply(c, 1.0, w, op->sigma * sh[j] / sj, V + (int64_t)j * ld, w, s)) != FR_OK) return e;
+      if (pc && (e = precond_apply(c, 1.0, w, op->sigma * sh[j], V + (int64_t)j * ld, w, s)) != FR_OK) return e;
       ++it;
       // classical Gram-Schmidt: one pass (reorth 0), a second pass when the
       // first removed more than half of ||w||^2, ||w_new|| < 0.7 ||w|| (DGKS,
@@ -757,17 +730,16 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       cudaMemcpyAsync(c->h_red, c->d_red + kOutH1, sizeof(double) * 3 * kMaxK, cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
       for (int i = 0; i <= j; ++i) {
-        h[i] = sj * sh[i] * c->h_red[i];
-        h2[i] = ro == 2 ? sj * sh[i] * c->h_red[kMaxK + i] : 0.0;
+        h[i] = sh[i] * c->h_red[i];
+        h2[i] = ro == 2 ? sh[i] * c->h_red[kMaxK + i] : 0.0;
       }
       if (ro == 1 && std::sqrt(c->h_red[2 * kMaxK]) < 0.7 * std::sqrt(c->h_red[kk])) {
         gs_pass(kk, unew, unew, c->d_red + kOutH2, 0);
         cudaMemcpyAsync(c->h_red + kMaxK, c->d_red + kOutH2, sizeof(double) * 2 * kMaxK, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
-        for (int i = 0; i <= j; ++i) h2[i] = sj * sh[i] * c->h_red[kMaxK + i];
+        for (int i = 0; i <= j; ++i) h2[i] = sh[i] * c->h_red[kMaxK + i];
       }
-      const double nrm = std::sqrt(c->h_red[2 * kMaxK]);   // norm of the stored new column
-      const double hn = sj * nrm;
+      const double hn = std::sqrt(c->h_red[2 * kMaxK]);
       for (int i = 0; i <= j; ++i) H[i * m + j] = h[i] + h2[i];
       if (!pc) H[j * m + j] += op->sigma;   // Hessenberg of sigma I - J from that of -J
       H[(j + 1) * m + j] = hn;
@@ -794,7 +766,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       g[j] = cs[j] * g[j];
       res = std::fabs(g[j + 1]);
       k = j + 1;
-      if (nrm != 0.0) sh[j + 1] = 1.0 / nrm;   // the device copy was stored by the update
+      if (hn != 0.0) sh[j + 1] = 1.0 / hn;   // the device copy was stored by the update
       if (res <= o->rtol * beta0 || it >= o->max_it || hn == 0.0) break;
     }
     for (int i = k - 1; i >= 0; --i) {
@@ -820,7 +792,6 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   }
   st->iterations = it;
   st->rel_res = res / beta0;
-  if (!sync_at_end) return cuda_check(cudaGetLastError(), "gmres");
   return cuda_check(cudaStreamSynchronize(s), "gmres");
 }
 
@@ -954,7 +925,7 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
     fr_gmres_stats gs;
     for (int h = 0; h <= o->max_halvings; ++h) {
       op.sigma = inv_wdt + 1.0 / dtau;
-      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s, norm, false)) != FR_OK) return e;
+      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s, norm)) != FR_OK) return e;
       st->gmres_iterations += gs.iterations;
       if (gs.converged) break;
       dtau *= 0.5;
