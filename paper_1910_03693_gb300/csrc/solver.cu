@@ -591,8 +591,11 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
 
 // GMRES(m) with x0 = 0.  R0 (optional) = R(q) for the finite-difference mode.
 // b_norm: ||b|| when the caller already has it, else negative.
+// sync_at_end: return only when x is complete (the public call); the stage
+// passes false and lets its next residual overlap the final combination.
 static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0, const double* b, double* x,
-                            const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s, double b_norm = -1.0) {
+                            const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s, double b_norm = -1.0,
+                            bool sync_at_end = true) {
   const int m = o->m;
   const int64_t n = c->n_dof, ld = krylov_ld(c);
   if (m < 1 || m + 1 > kMaxK || o->max_it < 1 || !(o->rtol > 0.0) || o->reorth < 0 || o->reorth > 2) {
@@ -792,6 +795,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   }
   st->iterations = it;
   st->rel_res = res / beta0;
+  if (!sync_at_end) return cuda_check(cudaGetLastError(), "gmres");
   return cuda_check(cudaStreamSynchronize(s), "gmres");
 }
 
@@ -925,7 +929,7 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
     fr_gmres_stats gs;
     for (int h = 0; h <= o->max_halvings; ++h) {
       op.sigma = inv_wdt + 1.0 / dtau;
-      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s, norm)) != FR_OK) return e;
+      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s, norm, false)) != FR_OK) return e;
       st->gmres_iterations += gs.iterations;
       if (gs.converged) break;
       dtau *= 0.5;
