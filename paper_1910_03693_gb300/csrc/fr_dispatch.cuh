@@ -93,6 +93,15 @@ static inline int epb_for(fr_ctx* c, int prec, int kind, int P) {
   return (t > 0 && t * nsp <= 256) ? t : dflt;
 }
 
+// Elements per tile of the multi-bucket launch: as many whole elements as fill
+// its 256-thread blocks (the tuned per-bucket values size separate launches,
+// whose block is e * n_sp threads; a small one here would leave most of the
+// block idle).
+static inline int epb_multi(int nd, int P) {
+  const int nsp = nsp_of(nd, P);
+  return nsp >= 256 ? 1 : 256 / nsp;
+}
+
 // One launch over all buckets for this precision and kernel kind: the master
 // switch, more than one bucket, and the per-kind choice (the autotuner writes
 // it into the unused P = 0 slot of the table: 0 default = yes, 1 yes, 2 no).
@@ -131,7 +140,7 @@ static const WorkItem* work_items(fr_ctx* c, int prec, int kind, int* n_items) {
   std::vector<std::pair<double, WorkItem>> items;
   for (size_t bi = 0; bi < c->buckets.size(); ++bi) {
     const Bucket& b = c->buckets[bi];
-    const int P = b.p + 1, e = epb_for(c, prec, kind, P);
+    const int P = b.p + 1, e = epb_multi(c->nd, P);
     for (int f = 0; f < b.count; f += e) {
       const int ne = std::min(e, b.count - f);
       items.push_back({ne * element_weight(c->epb_tab[0][0][1], nsp_of(c->nd, P), P), WorkItem{(int32_t)bi, (int32_t)f}});
@@ -203,7 +212,7 @@ static void launch_traces(fr_ctx* c, const T* q, T* trace, cudaStream_t s) {
     size_t smem = 0;
     for (size_t i = 0; i < c->buckets.size(); ++i) {
       const Bucket& b = c->buckets[i];
-      const int P = b.p + 1, e = epb_for(c, prec, 0, P);
+      const int P = b.p + 1, e = epb_multi(ND, P);
       m.b[i] = trace_args<T, ND, VISC>(c, b, q, trace);
       m.P[i] = P;
       m.epb[i] = e;
@@ -292,7 +301,7 @@ static void launch_vols(fr_ctx* c, const T* q, const T* v, T* out, cudaStream_t 
     size_t smem = 0;
     for (size_t i = 0; i < c->buckets.size(); ++i) {
       const Bucket& b = c->buckets[i];
-      const int P = b.p + 1, e = epb_for(c, prec, kind, P);
+      const int P = b.p + 1, e = epb_multi(ND, P);
       m.b[i] = vol_args<T>(c, b, q, v, out, out_neg64, out64);
       m.P[i] = P;
       m.epb[i] = e;
