@@ -319,7 +319,7 @@ def roe_ops(m, q, ph, peak_gbs):
 def mixed_degree_ops(peak_gbs):
     """Mixed-degree workloads (several buckets): FP64 residual and FP32 exact JVP
     throughput with one launch per degree bucket, with the persistent
-    multi-bucket launch under each element-weight model of its tile order
+    multi-bucket launch (both forced) under each element-weight model of its tile order
     (n_sp (p+1), n_sp, n_sp^2, n_sp^3), and after the autotuner.  The cylinder O-grid
     (98,304 curved hexahedra, p 1..4) and the batch of 32 2D vortex instances
     (p 1..5, 8^2..64^2 quads)."""
@@ -338,10 +338,13 @@ def mixed_degree_ops(peak_gbs):
                 t = ctx.autotune(q64)
                 row["autotuned_multi_launch"] = t["multi_launch"]
             else:
-                # tiles ordered by the paper's candidate element weights (slot [0][0][1])
+                # tiles ordered by the paper's candidate element weights (slot [0][0][1]);
+                # the multi-bucket choice forced for every precision and kernel (slot P = 0)
                 tab = [0] * 42
+                for slot in range(0, 42, 7):
+                    tab[slot] = 2 if cfg == "per_bucket" else 1
                 tab[1] = {"multi_w_nsp": 1, "multi_w_nsp2": 2, "multi_w_nsp3": 3}.get(cfg, 0)
-                ctx.set_tuning({"epb": tab, "multi_launch": cfg != "per_bucket"})
+                ctx.set_tuning({"epb": tab, "multi_launch": True})
             r = op_throughput(ctx, q64, N, peak_gbs, reps=10, runs=3, names=("residual_f64", "jvp_exact_f32"))
             row[cfg] = {k: {"gdof_s": v["gdof_s"], "ms": v["ms"]} for k, v in r.items()}
         out[label] = row

@@ -359,12 +359,15 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
  * multi-bucket launch for each kernel, and keeps the fastest; it synchronises `stream` and
  * changes no result beyond rounding order.  fr_tuning_get/fr_tuning_set read
  * and write the table, 2 x 3 x 7 int32 [precision f64,f32][kernel trace,
- * volume residual, volume JVP][P = p+1]: for P >= 2 the elements per CTA,
- * 0 = default (as many whole elements as fit 256 threads; a value whose
- * elements exceed 256 threads also falls back to it); the slot P = 0 holds
- * the multi-bucket choice of that precision and kernel (0 default = one launch
- * over all buckets, 1 the same, 2 one launch per bucket), which
- * FR_TUNE_MULTI_LAUNCH enables; slot [0][0][P = 1] holds the element weight
+ * volume residual, volume JVP][P = p+1]: for P >= 2 the elements per CTA
+ * of the one-launch-per-bucket kernels, 0 = default (as many whole elements
+ * as fit 256 threads; a value whose elements exceed 256 threads also falls
+ * back to it; the multi-bucket launch always fills its 256-thread blocks);
+ * the slot P = 0 holds the multi-bucket choice of that precision and kernel
+ * (0 undecided: one launch over all buckets while the mesh's solution points
+ * fit in 8 full-occupancy waves of the GPU, else one per bucket; 1 one launch
+ * over all buckets; 2 one launch per bucket), which FR_TUNE_MULTI_LAUNCH
+ * enables; slot [0][0][P = 1] holds the element weight
  * that orders the multi-bucket work table (0 n_sp (p+1), 1 n_sp, 2 n_sp^2,
  * 3 n_sp^3: the paper's candidate weights, Sec. 3.2); and the flags below.  fr_tuning_set with table NULL changes only the
  * flags; elements per CTA outside [0, 256], choices outside [0, 2], weight

@@ -102,17 +102,26 @@ static inline int epb_multi(int nd, int P) {
   return nsp >= 256 ? 1 : 256 / nsp;
 }
 
-// One launch over all buckets for this precision and kernel kind: the master
-// switch, more than one bucket, and the per-kind choice (the autotuner writes
-// it into the unused P = 0 slot of the table: 0 default = yes, 1 yes, 2 no).
-static inline bool use_multi(fr_ctx* c, int prec, int kind) {
-  return c->multi_launch && c->buckets.size() > 1 && c->epb_tab[prec][kind][0] != 2;
+static inline unsigned sm_count(fr_ctx* c) {
+  static int n = 0;   // one device per process here; queried once
+  if (n <= 0) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
+  return n > 0 ? (unsigned)n : 152u;
 }
 
-static inline unsigned sm_count(fr_ctx* c) {
-  int n = 0;
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
-  return n > 0 ? (unsigned)n : 152u;
+// One launch over all buckets for this precision and kernel kind: the master
+// switch, more than one bucket, and the per-kind choice (the autotuner writes
+// it into the unused P = 0 slot of the table: 1 yes, 2 no).  Undecided (0):
+// one launch while the mesh's solution points fit in 8 full-occupancy waves
+// (2048 threads per SM), where launches and tails dominate; beyond that each
+// bucket runs alone at its own degree's register footprint (measured: the
+// 4M-DOF vortex batch is faster in one launch, the 18M-DOF cylinder and the
+// 16M-DOF adapted C-grid per bucket).
+static inline bool use_multi(fr_ctx* c, int prec, int kind) {
+  if (!c->multi_launch || c->buckets.size() <= 1) return false;
+  const int choice = c->epb_tab[prec][kind][0];
+  if (choice == 1) return true;
+  if (choice == 2) return false;
+  return c->n_dof / c->nv <= (int64_t)8 * 2048 * sm_count(c);
 }
 
 // Element weight of the multi-bucket work table (tuning slot [0][0][P = 1]):
