@@ -358,7 +358,8 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
  * q64_dev (FP64, state layout, n_dof), then one launch per bucket against the
  * multi-bucket launch for each kernel, and keeps the fastest; it synchronises `stream` and
  * changes no result beyond rounding order.  fr_tuning_get/fr_tuning_set read
- * and write the table, 2 x 3 x 7 int32 [precision f64,f32][kernel trace,
+ * and write the table, 2 x 3 x 7 int32 [precision f64 (also used by the
+ * double-float kernels, same operand size), f32][kernel trace,
  * volume residual, volume JVP][P = p+1]: for P >= 2 the elements per CTA
  * of the one-launch-per-bucket kernels, 0 = default (as many whole elements
  * as fit 256 threads; a value whose elements exceed 256 threads also falls
