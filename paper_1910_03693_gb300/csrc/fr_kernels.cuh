@@ -131,16 +131,51 @@ struct VolCfg {
 // block reaches the barriers (threads beyond epb*NSP only help to synchronise).
 // DIAG: every metric S is diagonal (axis-aligned affine elements): only S[d][d]
 // is read and the metric products reduce to one multiply per component.
+// P consecutive values of shared memory (a line with stride 1): 16- or 8-byte
+// vector loads when the line's length and every offset that places it (the
+// caller's) are multiples of the vector, else scalar loads.
+template <typename T, int P, int W>
+__device__ __forceinline__ void load_contig(const T* p, T (&x)[P]) {
+  constexpr int BYTES = P * (int)sizeof(T);
+  if constexpr (W == 16 && BYTES % 16 == 0) {
+#pragma unroll
+    for (int w = 0; w < BYTES / 16; ++w) {
+      const float4 v = reinterpret_cast<const float4*>(p)[w];
+      memcpy(reinterpret_cast<char*>(&x[0]) + 16 * w, &v, 16);
+    }
+  } else if constexpr (W >= 8 && BYTES % 8 == 0) {
+#pragma unroll
+    for (int w = 0; w < BYTES / 8; ++w) {
+      const float2 v = reinterpret_cast<const float2*>(p)[w];
+      memcpy(reinterpret_cast<char*>(&x[0]) + 8 * w, &v, 8);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < P; ++k) x[k] = p[k];
+  }
+}
+
 template <typename T, int ND, int P, bool VISC, bool DIAG = false>
 __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, int epb, unsigned char* smem_raw) {
   using Sh = Shape<ND, P>;
   constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
+  constexpr int NFPT = NF * NFP;                         // face points of an element
+  constexpr int ITERS = (NFPT + NSP - 1) / NSP;          // face points per thread, at most
+  constexpr int ESTRIDE = NV * NSP + NF * NV * NFP;      // values per element in shared memory
+  // widest vector load every contiguous line start is aligned to (element,
+  // variable and line offsets; the buffer itself is 16-byte aligned)
+  constexpr int SZ = (int)sizeof(T);
+  constexpr int W = ((ESTRIDE * SZ) % 16 == 0 && (NSP * SZ) % 16 == 0 && (NFP * SZ) % 16 == 0 && (P * SZ) % 16 == 0)
+                        ? 16
+                        : (((ESTRIDE * SZ) % 8 == 0 && (NSP * SZ) % 8 == 0 && (NFP * SZ) % 8 == 0 && (P * SZ) % 8 == 0)
+                               ? 8
+                               : 1);
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int le = threadIdx.x / NSP;
   const int lt = threadIdx.x % NSP;
   const int64_t i = i0 + le;
   const bool valid = le < epb && i < a.count;
-  T* sq = sm + le * (NV * NSP + NF * NV * NFP);   // [NV][NSP]
+  T* sq = sm + le * ESTRIDE;                        // [NV][NSP]
   T* sqf = sq + NV * NSP;                           // [NF][NV][NFP]
   const BasisTab<T>& B = a.basis[P];
   if (valid) {
@@ -149,17 +184,35 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
   }
   __syncthreads();
   T* out = a.trace + a.trace_base + (valid ? i * NF * (int64_t)a.nvt * NFP : 0);
+  // the line values give the trace and (NS) the normal derivative at once;
+  // the derivatives wait in registers for the gradient pass
+  T dn[ITERS][NV];
   if (valid) {
-    for (int fp = lt; fp < NF * NFP; fp += NSP) {
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+      const int fp = lt + it * NSP;
+      if (fp >= NFPT) break;
       const int f = fp / NFP, t = fp % NFP, d = f >> 1, s = f & 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
+        T x[P];
+        if (d == 0) load_contig<T, P, W>(sq + v * NSP + line_sp<ND, P>(0, t, 0), x);   // stride 1 along xi
+        else {
+#pragma unroll
+          for (int k = 0; k < P; ++k) x[k] = sq[v * NSP + line_sp<ND, P>(d, t, k)];
+        }
         Acc<T> ac = acc_init(T(0));
 #pragma unroll
-        for (int k = 0; k < P; ++k) acc_madd(ac, B.ext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
+        for (int k = 0; k < P; ++k) acc_madd(ac, B.ext[s][k], x[k]);
         const T acc = acc_value(ac);
         out[(f * a.nvt + v) * NFP + t] = acc;
-        if (VISC) sqf[(f * NV + v) * NFP + t] = acc;
+        if (VISC) {
+          sqf[(f * NV + v) * NFP + t] = acc;
+          Acc<T> an = acc_init(T(0));
+#pragma unroll
+          for (int k = 0; k < P; ++k) acc_madd(an, B.dext[s][k], x[k]);
+          dn[it][v] = acc_value(an);
+        }
       }
     }
   }
@@ -167,8 +220,11 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
   __syncthreads();
   if (!valid) return;
   const int64_t e = a.slot_elem[a.slot_begin + i];
-  for (int fp = lt; fp < NF * NFP; fp += NSP) {
-    const int f = fp / NFP, t = fp % NFP, d = f >> 1, s = f & 1;
+#pragma unroll
+  for (int it = 0; it < ITERS; ++it) {
+    const int fp = lt + it * NSP;
+    if (fp >= NFPT) break;
+    const int f = fp / NFP, t = fp % NFP, d = f >> 1;
     const int ia = t % P, ib = ND == 3 ? t / P : 0;
     const int ta = d == 0 ? 1 : 0;              // first tangential direction
     const int tb = d == 2 ? 1 : 2;              // second (3D)
@@ -181,14 +237,13 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T dq[ND];
+      dq[d] = dn[it][v];
+      const T* face = sqf + (f * NV + v) * NFP;
+      T y[P];
+      load_contig<T, P, W>(face + (ND == 2 ? 0 : P * ib), y);   // the face line along its first axis
       Acc<T> ac = acc_init(T(0));
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc_madd(ac, B.dext[s][k], sq[v * NSP + line_sp<ND, P>(d, t, k)]);
-      dq[d] = acc_value(ac);
-      const T* face = sqf + (f * NV + v) * NFP;
-      ac = acc_init(T(0));
-#pragma unroll
-      for (int m = 0; m < P; ++m) acc_madd(ac, B.D[ia][m], face[ND == 2 ? m : m + P * ib]);
+      for (int m = 0; m < P; ++m) acc_madd(ac, B.D[ia][m], y[m]);
       dq[ta] = acc_value(ac);
       if (ND == 3) {
         ac = acc_init(T(0));
