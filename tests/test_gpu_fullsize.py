@@ -5,7 +5,7 @@ input: elementwise where the oracle computes the full vector in seconds
 (residual, JVP, VJP), by a property that holds at any size otherwise (the
 converged ESDIRK stage solves the oracle's stage equation).  Tolerances are
 those of the small-size tests (FP64 1e-12 of max|R| or of the flux scale,
-1e-11 on curved meshes; FP32 2e-5).
+1e-11 on curved meshes; double-float 2e-10, 2e-9 curved; FP32 2e-5).
 """
 import math
 
@@ -51,6 +51,23 @@ def test_tgv_full_df_residual(built, tgv):
     R = ctx.unpack(ctx.residual(ctx.pack(torch.from_numpy(q).cuda()), double_float=True)).cpu().numpy()
     ok, rel, fs = parity_ok(R, Rref, m, q, 2e-10)
     assert ok, (rel, fs)
+
+
+def test_tgv_full_roe_residual(built, tgv):
+    """Roe's flux at full size: FP64, double-float and FP32 residuals against
+    the oracle's Roe residual (eigenvector matrices and dense solves)."""
+    m, q, ph, _ = tgv
+    ph = dict(ph, flux="roe")
+    Rref = oracle_fr(m, ph).residual(torch.from_numpy(q)).numpy()
+    ctx = gpu_ctx(m, ph, 3, 3)
+    qd = torch.from_numpy(q).cuda()
+    for dtype, tol in ((torch.float64, 1e-12), (torch.float32, 2e-5)):
+        R = ctx.unpack(ctx.residual(ctx.pack(qd, dtype))).cpu().numpy()
+        ok, rel, fs = parity_ok(R, Rref, m, q, tol)
+        assert ok, (str(dtype), rel, fs)
+    R = ctx.unpack(ctx.residual(ctx.pack(qd), double_float=True)).cpu().numpy()
+    ok, rel, fs = parity_ok(R, Rref, m, q, 2e-10)
+    assert ok, ("double-float", rel, fs)
 
 
 def test_tgv_full_fp32_exact_jvp(built, tgv):
@@ -108,6 +125,9 @@ def test_cylinder_full_residual(built):
         R = ctx.unpack(ctx.residual(ctx.pack(qd, dtype))).cpu().numpy()
         ok, rel, fs = parity_ok(R, Rref, m, q, tol)
         assert ok, (str(dtype), rel, fs)
+    R = ctx.unpack(ctx.residual(ctx.pack(qd), double_float=True)).cpu().numpy()   # curved, four buckets
+    ok, rel, fs = parity_ok(R, Rref, m, q, 2e-9)
+    assert ok, ("double-float", rel, fs)
 
 
 def test_naca_full_residual_and_adaptation(built):
