@@ -42,6 +42,13 @@ def small_workloads():
                                               q_inf=cases.free_stream_q(3, vel=vel, mach=0.2)))
     mbat, qb, ph = cases.workload_vortex_batch(5, 3, 9, 1, 5)
     out["vortex_batch_5"] = (mbat, qb, ph)
+    # the highest degree: 3D p = 5 (216 points an element, one element a CTA)
+    # beside p = 4 through p-4/5 mortars, viscous; and 2D p = 5
+    mh = cases.periodic_box(3, 3, 0.0, 1.0, 4)
+    mh = mh.with_p((4 + np.floor(cases.uniform(80, mh.n_elem) * 2)).astype(np.int8))
+    out["box_mixed_p4-5_ns"] = (mh, cases.random_state(mh, 81), dict(gamma=1.4, mu=0.02, Pr=0.71))
+    m5, q5, ph5 = cases.workload_vortex2d(4, 5)
+    out["vortex2d_4x4_p5"] = (m5, q5, ph5)
     return out
 
 
