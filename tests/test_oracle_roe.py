@@ -2,7 +2,8 @@
 independently of its own formulas: Roe's property of the averaged Jacobian
 (taken by automatic differentiation of the flux), the eigenvectors against
 that Jacobian, |A| against a numerical eigendecomposition, consistency,
-upwinding in supersonic flow, and the FR residual's invariants with Roe."""
+upwinding in supersonic flow, the FR residual's invariants with Roe, and
+its linearisation (central-difference step sweep, adjoint identity)."""
 import math
 
 import numpy as np
@@ -176,3 +177,46 @@ def test_roe_differs_from_rusanov():
     Rr = FR(m, Euler(2, G, flux="rusanov")).residual(q)
     Ro = FR(m, Euler(2, G, flux="roe")).residual(q)
     assert float((Rr - Ro).abs().max()) > 1e-3 * float(Rr.abs().max())
+
+
+def _small_roe(nd, mu):
+    if nd == 2:
+        m, q, _ = cases.workload_vortex2d(3, 2)
+        m = m.with_p(np.array([1, 2, 3, 2, 1, 2, 3, 2, 1], dtype=np.int8))
+        q = cases.random_state(m, 2)
+    else:
+        m, q, _ = cases.workload_diff(2, 2)
+    return FR(m, Euler(nd, G, mu, 0.71, flux="roe")), torch.from_numpy(q)
+
+
+@pytest.mark.parametrize("nd,mu", [(2, 0.0), (3, 0.05)])
+def test_roe_jvp_matches_finite_difference_sweep(nd, mu):
+    """The oracle's linearisation of the Roe residual (automatic
+    differentiation through the eigenvector solve) against central
+    differences of the residual itself over a step sweep: the V-curve's
+    minimum below 1e-8."""
+    from oracle import linearize as L
+    fr, q = _small_roe(nd, mu)
+    g = torch.Generator().manual_seed(12)
+    q = q + 1e-3 * q.abs().mean() * (2 * torch.rand(q.numel(), generator=g, dtype=torch.float64) - 1)
+    v = torch.from_numpy(cases.uniform(19, q.numel()) - 0.5) * q.abs().mean()
+    Jv = L.jvp(fr, q, v)
+    errs = {}
+    for k in range(2, 9):
+        eps = 10.0 ** -k
+        fd = (fr.residual(q + eps * v) - fr.residual(q - eps * v)) / (2 * eps)
+        errs[k] = float((fd - Jv).abs().max() / Jv.abs().max())
+    best = min(errs.values())
+    assert best < 1e-8, errs
+    assert errs[2] > 10 * best and errs[8] > 10 * best, errs
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_roe_vjp_dot_product(nd):
+    from oracle import linearize as L
+    fr, q = _small_roe(nd, 0.05)
+    v = torch.from_numpy(cases.uniform(21, q.numel()) - 0.5)
+    w = torch.from_numpy(cases.uniform(22, q.numel()) - 0.5)
+    lhs = float(torch.dot(w, L.jvp(fr, q, v)))
+    rhs = float(torch.dot(L.vjp(fr, q, w), v))
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1.0)
