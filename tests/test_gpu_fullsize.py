@@ -160,7 +160,11 @@ def test_naca_full_residual_and_adaptation(built):
 
 def test_diff_full_vjp_and_dot_product(built):
     """Differentiation workload (24^3, p = 4): FP64 VJP against the oracle's
-    reverse-mode derivative; FP32 <w, Jv> = <J^T w, v>."""
+    reverse-mode derivative; FP32 <w, Jv> = <J^T w, v> up to the FP32 rounding
+    of the two operators.  Each side's error scales with the norms (|w| |Jv|,
+    |v| |J^T w|), not with the inner product itself, which for 8.6M random
+    terms is ~sqrt(N) times smaller; the bound is 1e-5 of the norms' products
+    (the FP32 JVP is ~1e-6 from FP64 in 2-norm)."""
     from oracle import linearize as L
     m, q, ph = cases.workload_diff()
     qg = generic_state(q)
@@ -173,11 +177,15 @@ def test_diff_full_vjp_and_dot_product(built):
     ok, rel, fs = parity_ok(got, ref, m, qg, 1e-12)
     assert ok, (rel, fs)
     q32 = ctx.pack(torch.from_numpy(qg).cuda(), torch.float32)
-    v32 = torch.randn_like(q32)
-    w32 = torch.randn_like(q32)
-    lhs = float(torch.dot(w32.double(), ctx.jvp(q32, v32).double()))
-    rhs = float(torch.dot(ctx.vjp(q32, w32).double(), v32.double()))
-    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+    v32 = ctx.pack(torch.from_numpy(cases.uniform(906, q.size) - 0.5).cuda(), torch.float32)
+    w32 = ctx.pack(torch.from_numpy(cases.uniform(907, q.size) - 0.5).cuda(), torch.float32)
+    Jv = ctx.jvp(q32, v32).double()
+    JTw = ctx.vjp(q32, w32).double()
+    v64, w64 = v32.double(), w32.double()
+    lhs = float(torch.dot(w64, Jv))
+    rhs = float(torch.dot(JTw, v64))
+    bound = float(w64.norm() * Jv.norm() + v64.norm() * JTw.norm())
+    assert abs(lhs - rhs) <= 1e-5 * bound, (lhs, rhs, bound)
 
 
 def test_vortex_batch_full_residual(built):

@@ -37,16 +37,19 @@ def test_vjp_parity(built, name):
 
 
 def test_vjp_dot_product_and_autograd(built):
-    """<w, J v> = <J^T w, v> on the GPU, and torch.autograd through the residual."""
+    """<w, J v> = <J^T w, v> on the GPU in FP64, to 1e-13 of |w| |Jv| + |v| |J^T w|
+    (each side's rounding scales with those norms), and torch.autograd through
+    the residual."""
     from paper_1910_03693_gb300 import autograd_residual
     m, q, ph = WL["diff_3^3_p4_mu0.05"]
     ctx = gpu_ctx(m, ph)
     qs = ctx.pack(torch.from_numpy(q).cuda())
-    v = torch.randn_like(qs)
-    w = torch.randn_like(qs)
-    lhs = float(torch.dot(w, ctx.jvp(qs, v)))
-    rhs = float(torch.dot(ctx.vjp(qs, w), v))
-    assert abs(lhs - rhs) <= 1e-12 * abs(lhs) * 10
+    v = ctx.pack(torch.from_numpy(cases.uniform(908, q.size) - 0.5).cuda())
+    w = ctx.pack(torch.from_numpy(cases.uniform(909, q.size) - 0.5).cuda())
+    Jv, JTw = ctx.jvp(qs, v), ctx.vjp(qs, w)
+    lhs = float(torch.dot(w, Jv))
+    rhs = float(torch.dot(JTw, v))
+    assert abs(lhs - rhs) <= 1e-13 * float(w.norm() * Jv.norm() + v.norm() * JTw.norm()), (lhs, rhs)
     qg = qs.clone().requires_grad_(True)
     R = autograd_residual(ctx, qg)
     (g,) = torch.autograd.grad(R, qg, w)
