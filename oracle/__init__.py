@@ -12,7 +12,7 @@ Modules
   basis      Gauss-Legendre points, Lagrange operators, DG (Radau) correction
              derivatives, Legendre Vandermonde matrices (Sec. 2.2).
   geometry   element maps, metric terms |J| grad(xi_d) at solution and flux
-             points (conservative curl form in 3D).
+             points (cross-product form from the interpolated map).
   physics    Euler / Navier-Stokes fluxes (Sec. 2.1), Rusanov common flux,
              scalar linear advection (for the FR = DG check).
   fr         the FR residual R(q) = -div f with common fluxes, BR2 common
@@ -28,8 +28,9 @@ Modules
              linearized_pseudo_transient_final, ser).
   adapt      spectral-decay indicator (Sec. 3.1), p decision, neighbour
              smoothing, prolongation / projection, bucket order.
-  dg         a direct nodal DG discretisation of linear advection used only
-             to check FR with the DG correction against DG.
+  dg         direct nodal DG discretisations (linear advection; scalar
+             diffusion with the BR2 lifting) used only to check FR with the DG
+             correction against DG.
 
 Readings where the paper is silent are listed in the repository's design notes
 and repeated in each function's docstring.

@@ -3,11 +3,13 @@
 Tensors of one degree-p element group are laid out ``[E, ..., (P,)*nd]`` with
 the spatial axes ordered (zeta, eta, xi): reference direction d lives on tensor
 axis ``-1-d``.  The metric terms are S[d][j] = |J| d(xi_d)/d(x_j) (the
-contravariant vectors scaled by |J|).  In 2D they are the cross-product form
-(S_xi = (y_eta, -x_eta), S_eta = (-y_xi, x_xi)); in 3D the conservative curl
-form J a^i_n = -(curl_xi I(X_l grad_xi X_m))_i of Kopriva (2006), both built from
-the degree-p interpolant of the element map, so that sum_d D_d S_d = 0 holds
-discretely (free-stream preservation).
+contravariant vectors scaled by |J|), in cross-product form from the
+derivatives of the degree-p interpolant X of the element map: in 2D
+S_xi = (y_eta, -x_eta), S_eta = (-y_xi, x_xi); in 3D S_i = dX/dxi_j x dX/dxi_k
+for (i, j, k) cyclic.  The discrete metric identities sum_d D_d S_d = 0, and
+with them free-stream preservation, hold in 2D and for affine and extruded
+hexahedra (every 3D mesh here); general curved hexahedra would need Kopriva's
+(2006) conservative curl form instead.
 """
 import torch
 

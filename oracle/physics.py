@@ -190,3 +190,22 @@ class Advection:
     def common_flux(self, qL, qR, n):
         """The upwind flux (for a scalar the Roe and Rusanov fluxes coincide)."""
         return self.rusanov(qL, qR, n)
+
+
+class Diffusion:
+    """Scalar diffusion dq/dt = mu Lap q (no inviscid flux; viscous flux mu grad q),
+    used only to check the BR2 common gradient against a direct DG-BR2 weak form."""
+
+    def __init__(self, nd, mu):
+        self.nd, self.nv = nd, 1
+        self.mu = float(mu)
+        self.viscous = True
+
+    def flux(self, q):
+        return torch.zeros((q.shape[0], self.nd) + tuple(q.shape[1:]), dtype=q.dtype)
+
+    def common_flux(self, qL, qR, n):
+        return torch.zeros_like(qL)
+
+    def viscous_flux(self, q, G):
+        return self.mu * G
