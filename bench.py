@@ -41,15 +41,34 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# ALU peaks derived from unit counts and the maximum SM clock: 152 SMs x 2 FP64
-# FMA units x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s), and 152 x 128 FP32
-# lanes x 2 x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# Double-float kernels: one algorithmic FMA (2 flops) is one double-float
-# multiply-add of 15 FP32 instructions, so their algorithmic peak is the FP32
-# instruction rate x 2 / 15.
-DF_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 15
+# ALU peaks: measured on the device at the start of the run (fr_fma_rate:
+# independent FMA chains timed with CUDA events); the unit-count values below
+# (SMs x 2 FP64 FMA units or 128 FP32 lanes x 2 flops x 2.07 GHz) are the
+# fallback when the measurement is unavailable.  Double-float kernels: one
+# algorithmic FMA (2 flops) is one double-float multiply-add, 15 FP32
+# instructions (dfma in dfloat.cuh: one product, three FMAs, the six
+# operations of TwoSum, two adds, the three of the final Fast2Sum), so their
+# algorithmic peak is the FP32 instruction rate x 2 / 15.
+DF_FP32_INSTRUCTIONS_PER_FMA = 15
+
+
+def _alu_peaks(measure=True):
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    nominal = {"fp64": sms * 2 * 2 * 2.07e9 / 1e12, "fp32": sms * 128 * 2 * 2.07e9 / 1e12}
+    out = {"sms": sms, "source": "unit counts x 2.07 GHz (fallback)", "fp64": nominal["fp64"],
+           "fp32": nominal["fp32"]}
+    if measure:
+        try:
+            from paper_1910_03693_gb300 import fma_rate
+            out["fp64"] = max(fma_rate(torch.float64, 4096) for _ in range(3))
+            out["fp32"] = max(fma_rate(torch.float32, 65536) for _ in range(3))
+            out["source"] = "measured (fr_fma_rate: 16 independent FMA chains a thread, best of 3)"
+            out["nominal_fp64"], out["nominal_fp32"] = nominal["fp64"], nominal["fp32"]
+        except Exception as e:  # noqa: BLE001
+            out["error"] = str(e)[:200]
+    out["df"] = out["fp32"] / DF_FP32_INSTRUCTIONS_PER_FMA
+    return out
 
 
 def _cpu_model():
@@ -65,16 +84,17 @@ def _cpu_model():
     return platform.processor() or platform.machine()
 
 
-def kernel_roofline(name, launches, ms, nbytes, nflops, hbm_gbs):
-    """Bound, achieved, peak and fraction of one kernel from its algorithmic bytes
-    and operations: the roofline it reaches first decides the bound."""
+def kernel_roofline(name, launches, ms, nbytes, nflops, hbm_gbs, alu_peaks):
+    """Bound, achieved, peak and fraction of one kernel from the bytes and
+    operations its launches count (its own inputs and outputs): the roofline
+    it reaches first decides the bound."""
     t = ms / 1e3
     if name.endswith("_df"):
-        alu_peak, alu = DF_PEAK_TFLOPS, "fp32 (double-float, 15 FP32 instructions per FMA)"
+        alu_peak, alu = alu_peaks["df"], "fp32 (double-float, 15 FP32 instructions per FMA)"
     elif name.endswith("f64"):
-        alu_peak, alu = FP64_PEAK_TFLOPS, "fp64"
+        alu_peak, alu = alu_peaks["fp64"], "fp64"
     else:
-        alu_peak, alu = FP32_PEAK_TFLOPS, "fp32"
+        alu_peak, alu = alu_peaks["fp32"], "fp32"
     t_hbm = nbytes / (hbm_gbs * 1e9)
     t_alu = nflops / (alu_peak * 1e12)
     if t_alu > t_hbm:
@@ -83,6 +103,50 @@ def kernel_roofline(name, launches, ms, nbytes, nflops, hbm_gbs):
                 "alu": alu}
     ach = nbytes / t / 1e9 if t > 0 else 0.0
     return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs}
+
+
+# Algorithmic bytes of one evaluation per unit of state (the survey's
+# measurement section): residual 2 N s (state in, R out), exact JVP and VJP
+# 3 N s (q, v in; Jv out), finite-difference Jv 4 N s; geometry is per-element
+# constants on the bench's affine mesh and negligible.  Intermediate trace and
+# face arrays are not counted: a fully fused product would keep them on chip.
+SURVEY_VECTORS = {"residual": 2, "jvp": 3, "vjp": 3, "fd": 4}
+
+
+def _operator_of(kernel):
+    """(operator, bytes per value) of a library kernel name, or None for kernels
+    outside the residual / JVP (Arnoldi, vector, layout kernels)."""
+    if kernel.endswith("_f32"):
+        s = 4
+    elif kernel.endswith("_f64") or kernel.endswith("_df"):
+        s = 8
+    else:
+        return None
+    if "_jvp_" in kernel:
+        return "jvp", s
+    if "_res_" in kernel:
+        return "residual", s
+    if kernel.startswith("trace_"):   # FP32 traces serve the JVP's tangent in the step
+        return ("jvp" if s == 4 else "residual"), s
+    return None
+
+
+def survey_roofline(kernel, launches, ms, n_dof, hbm_gbs):
+    """The dominant kernel against the HBM roofline with the survey's
+    algorithmic bytes: the bytes of one evaluation of the operator it belongs
+    to (SURVEY_VECTORS x N x s) charged to each of its launches, over its mean
+    launch time."""
+    t = ms / 1e3 / max(launches, 1)
+    ops = _operator_of(kernel)
+    if ops is None:
+        return {"bound": "hbm", "achieved": None, "peak": hbm_gbs, "unit": "GB/s", "frac": None,
+                "bytes_per_launch": None}
+    op, s = ops
+    b = SURVEY_VECTORS[op] * n_dof * s
+    ach = b / t / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
+            "bytes_per_launch": b, "operator": op,
+            "bytes": f"{SURVEY_VECTORS[op]} N s per evaluation of the {op} (N = {n_dof}, s = {s})"}
 
 
 def _csrc_hash():
@@ -481,6 +545,7 @@ def main():
 
     # launch tuning (elements per CTA, multi-bucket launch), untimed set-up
     tuning = ctx.autotune(qn[:N])
+    alu = _alu_peaks()
 
     def step(q_in):
         ctx.indicator(q_in[:N], var=1, eta=eta, eta_max=eta_max)
@@ -531,39 +596,60 @@ def main():
     peak, peak_kind = _peaks()
     kern = max(report, key=lambda k: report[k][1])
     cnt, ms, nbytes, nflops = report[kern]
-    roof = kernel_roofline(kern, cnt, ms, nbytes, nflops, peak)
+    roof = survey_roofline(kern, cnt, ms, N, peak)
+    io = kernel_roofline(kern, cnt, ms, nbytes, nflops, peak, alu)
     roof.update({"kernel": kern, "traffic": _traffic_for(kern), "hbm_peak_source": peak_kind,
-                 "share_of_step": ms / total_ms, "per_launch_ms": ms / cnt})
+                 "share_of_step": ms / total_ms, "per_launch_ms": ms / cnt,
+                 "kernel_io": {"bound": io["bound"], "achieved": io["achieved"], "unit": io["unit"],
+                               "peak": io["peak"], "frac": io["frac"],
+                               "bytes": "the kernel's own inputs and outputs per launch, intermediate "
+                                        "trace and face arrays included"}})
     kernels = {}
     for k, v in sorted(report.items(), key=lambda kv: -kv[1][1]):
-        r = kernel_roofline(k, *v, peak) if (v[2] > 0 or v[3] > 0) else None
+        r = kernel_roofline(k, *v, peak, alu) if (v[2] > 0 or v[3] > 0) else None
         kernels[k] = {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4),
                       "bound": r["bound"] if r else None,
                       "achieved": round(r["achieved"], 2) if r else None,
                       "unit": r["unit"] if r else None, "frac": round(r["frac"], 4) if r else None}
 
-    # end to end through the public API: host canonical state in, host state out
+    # end to end through the public API: every step takes the canonical state
+    # from page-locked host memory through fr_pack (host pointer: the library
+    # copies it in) and returns the stage value to page-locked host memory
+    # through fr_unpack (host pointer), with L2 flushed and the device
+    # synchronised before each step as in the timed region; the evaluations are
+    # this leg's own, counted from its own launches
     out_host = torch.empty(N, dtype=torch.float64).pin_memory()
-    flush.zero_()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    evals_e2e = 0
+    ctx.timing(True)
+    e2e_ms = 0.0
     for _ in range(args.steps):
-        ctx.pack(qn_host.cuda(non_blocking=True), out=qn[:N])
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.pack(qn_host, out=qn[:N])
         step(qn)
-        out_host.copy_(ctx.unpack(qi), non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e = {"value": (N * n_evals * max(world, 1)) / (e2e_ms / 1e3) / 1e9, "unit": "GDOF/s",
-           "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+        ctx.unpack(qi, out=out_host)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    rep_e2e, _ = ctx.timing_report()
+    ctx.timing(False)
+    evals_e2e = sum(v[0] for k, v in rep_e2e.items() if k.startswith("vol_res") or k.startswith("vol_jvp"))
+    e2e_ms, e2e_units = reduce_over_ranks(e2e_ms, N * evals_e2e, dist if world > 1 else None)
+    e2e = {"value": e2e_units / (e2e_ms / 1e3) / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
+           "ms_per_step": e2e_ms / args.steps, "evaluations": evals_e2e,
+           "path": "fr_pack(host pinned) -> step -> fr_unpack(host pinned), L2 flushed per step"}
 
     # per-operator throughput (graph-replayed) and the FP64 finite-difference stage
     ops = op_throughput(ctx, qn[:N], N, peak)
     fd = stage_fd64(ctx, tab, qn, N, R1, opts)
     bf = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype="bf16op")
     f64F = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype=torch.float32, low_above=0.0)
+    roof["frac_alg"] = {k: ops[k]["hbm_frac"] for k in ("jvp_exact_f32", "residual_f32", "residual_df",
+                                                         "residual_f64", "vjp_f32")}
+    roof["frac_alg_note"] = ("survey bytes (residual 2 N s, JVP/VJP 3 N s) over the whole graph-replayed "
+                             "operator's time, against the measured HBM peak")
     mixed = mixed_degree_ops(peak) if args.n == 32 else None
     roe = roe_ops(m, q, ph, peak)
 
@@ -586,6 +672,7 @@ def main():
                   "converged": all(s["converged"] for s in stats),
                   "rel_final": [s["norm_final"] / s["norm0"] for s in stats]},
         "roofline": roof,
+        "alu_peaks_tflops": alu,
         "ops": ops,
         "mixed_degree_ops": mixed,
         "roe_flux_ops": roe,

@@ -144,13 +144,19 @@ fr_status fr_layout(const fr_ctx* ctx, fr_layout_info* info);
 fr_status fr_get_p(const fr_ctx* ctx, int8_t* p_host);
 const char* fr_last_error(void);
 
-/* Canonical FP64 (device) <-> state layout in `prec`. */
-fr_status fr_pack(fr_ctx* ctx, const double* canon_dev, void* q_dev, fr_prec prec, void* stream);
-fr_status fr_unpack(fr_ctx* ctx, const void* q_dev, fr_prec prec, double* canon_dev, void* stream);
+/* Canonical FP64 <-> state layout in `prec`.  The canonical buffer (n_dof
+ * doubles) may be device memory (read or written in place by the layout
+ * kernel) or host memory, page-locked or pageable (copied on `stream` through
+ * a staging vector of the context; with pageable memory the copy completes
+ * before the call returns).  With a host destination, fr_unpack's result is
+ * there once `stream` has reached it. */
+fr_status fr_pack(fr_ctx* ctx, const double* canon_host_or_dev, void* q_dev, fr_prec prec, void* stream);
+fr_status fr_unpack(fr_ctx* ctx, const void* q_dev, fr_prec prec, double* canon_host_or_dev, void* stream);
 
-/* R = R(q) = -div f, Sec. 2.2 Eq. (FR_diff) with Rusanov common inviscid
- * flux, common solution Eq. (com_q) and BR2-type common gradient
- * Eq. (com_grad_q).  q and R are state-layout device buffers of n_dof. */
+/* R = R(q) = -div f, Sec. 2.2 Eq. (FR_diff) with the common inviscid flux
+ * the context was created with (Rusanov, or Roe's Eq. invis_com), common
+ * solution Eq. (com_q) and BR2-type common gradient Eq. (com_grad_q).  q and R
+ * are state-layout device buffers of n_dof in `prec` (FR_DF: FP64 buffers). */
 fr_status fr_residual(fr_ctx* ctx, const void* q_dev, void* R_dev, fr_prec prec, void* stream);
 
 /* Jv ~ dR(q)/dq v.  FR_JV_EXACT: the exact directional derivative.
@@ -163,15 +169,22 @@ fr_status fr_jvp(fr_ctx* ctx, const void* q_dev, const void* v_dev, void* Jv_dev
  * nothing: the same product as fr_jvp(..., FR_F64, FR_JV_FD, eps, ...), with its
  * three work vectors in a device array reserved when the library is loaded
  * (3 x 262,144 doubles, 6 MiB on every device, held until exit).  The paper
- * has no counterpart: this serves callers that may not allocate device memory
- * after set-up (work recorded by global-mode stream capture, loops whose
- * allocator budget is fixed, memory fully reserved by another allocator).
+ * has no counterpart.  It serves callers that cannot call cudaMalloc once
+ * their set-up is done: processes whose device memory is already fully
+ * reserved by another allocator (a framework's caching allocator, say), where
+ * a new allocation would fail, and loops that must not call the allocator at
+ * all, because cudaFree synchronises the whole device and an allocation can
+ * stall behind other work.  Nothing else in the call allocates either: the
+ * work tables of mixed-degree meshes are built when the layout or the tuning
+ * changes (fr_create, p_rebucket, fr_tuning_set, fr_autotune), not on first use.
  * q, v, Jv: FP64 state-layout device buffers of n_dof.  FR_ERR_INVALID when
  * n_dof > 262,144, eps <= 0, or the current device is not the context's.  The
- * first call on each device looks up the array's device address; make that
- * first call before any stream capture begins.  All calls share the array:
- * calls whose GPU work overlaps (other streams or contexts on the device)
- * race on it. */
+ * first call on each device looks up the array's device address (set-up,
+ * once per device, in the runtime's primary context of that device, the only
+ * context supported); make that first call before any stream capture begins.
+ * All calls share the array, which keeps the last call's contents (each call
+ * writes its work vectors before reading them): calls whose GPU work overlaps
+ * (other streams, or other threads on the device) race on it. */
 fr_status fr_jvp_fd_static(fr_ctx* ctx, const double* q_dev, const double* v_dev, double* Jv_dev,
                            double eps, void* stream);
 
@@ -211,9 +224,11 @@ typedef struct {
   double rel_res;
 } fr_gmres_stats;
 
-/* Restarted GMRES(m) from x = 0 in FP64 (classical Gram-Schmidt as
- * opts->reorth says, Givens rotations on the host).  b, x: device FP64,
- * n_dof.  One host synchronisation per Arnoldi iteration. */
+/* Restarted GMRES(m) (Sec. 2.3: the matrix-free Krylov solve of the
+ * linearised pseudo-transient system, Eq. linearized_pseudo_transient_final)
+ * from x = 0 in FP64: classical Gram-Schmidt as opts->reorth says, Givens
+ * rotations on the host.  b, x: device FP64, n_dof.  One host
+ * synchronisation per Arnoldi iteration. */
 fr_status gmres_solve(fr_ctx* ctx, const fr_shifted_op* op, const double* b_dev, double* x_dev,
                       const fr_gmres_opts* opts, fr_gmres_stats* stats, void* stream);
 
@@ -394,6 +409,14 @@ fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);
  * fr_timing call into *launches (optional). */
 fr_status fr_timing(fr_ctx* ctx, int32_t enable);
 fr_status fr_timing_report(fr_ctx* ctx, char* buf, int64_t len, int64_t* launches);
+
+/* Arithmetic peak of the current device, measured (measurement support, no
+ * counterpart in the paper): a kernel of independent FMA chains (16 per
+ * thread, `iters` x 16 FMAs each, 8 warps on every SM x 4 blocks) in FP64
+ * (prec FR_F64) or FP32 (FR_F32), timed with CUDA events on `stream`;
+ * *tflops = 2 x FMAs / time.  Synchronises `stream`.  FR_ERR_INVALID for other
+ * precisions or iters < 1. */
+fr_status fr_fma_rate(fr_prec prec, int64_t iters, double* tflops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -7,4 +7,4 @@ spectral-decay p-adaptation with on-device rebucketing (arXiv:1910.03693,
 Secs. 2-3), as hand-written CUDA kernels for sm_103a behind a C ABI
 (``include/fr.h``).  This Python layer only marshals arguments.
 """
-from .api import FRContext, FRError, autograd_residual, dfloat_eval, esdirk_tableau  # noqa: F401
+from .api import FRContext, FRError, autograd_residual, dfloat_eval, esdirk_tableau, fma_rate  # noqa: F401

@@ -147,15 +147,22 @@ class FRContext:
 
     # ------------------------------------------------------------ conversions
     def pack(self, canon, dtype=torch.float64, out=None):
-        canon = _dev(canon, "canon")
+        """Canonical FP64 vector (CUDA tensor, or a host tensor: page-locked or
+        pageable, copied by the library) -> state layout in ``dtype``."""
+        if not (isinstance(canon, torch.Tensor) and canon.is_contiguous()):
+            raise ValueError("canon must be a contiguous tensor")
         assert canon.dtype == torch.float64 and canon.numel() == self.n_dof
         out = self.empty(dtype) if out is None else _dev(out, "out")
         _check(lib().fr_pack(self.h, _ptr(canon), _ptr(out), _prec(out), _stream()), "fr_pack")
         return out
 
     def unpack(self, q, out=None):
+        """State layout -> canonical FP64 vector; ``out`` may be a CUDA tensor or
+        a host tensor (filled once the current stream reaches the copy)."""
         q = _dev(q, "q")
         out = torch.empty(self.n_dof, dtype=torch.float64, device="cuda") if out is None else out
+        if not (out.dtype == torch.float64 and out.is_contiguous() and out.numel() == self.n_dof):
+            raise ValueError("out must be a contiguous FP64 tensor of n_dof values")
         _check(lib().fr_unpack(self.h, _ptr(q), _prec(q), _ptr(out), _stream()), "fr_unpack")
         return out
 
@@ -402,6 +409,14 @@ def dfloat_eval(op, a, b=None, c=None):
     _check(lib().fr_dfloat_eval(DFLOAT_OPS[op], _ptr(a), ptr(b), ptr(c), _ptr(out), a.numel(), _stream()),
            "fr_dfloat_eval")
     return out
+
+
+def fma_rate(dtype=torch.float64, iters=4096):
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
+    out = C.c_double(0.0)
+    prec = _lib.FR_F64 if dtype == torch.float64 else _lib.FR_F32
+    _check(lib().fr_fma_rate(prec, int(iters), C.byref(out), _stream()), "fr_fma_rate")
+    return out.value
 
 
 def esdirk_tableau(order=3):

@@ -177,16 +177,50 @@ void clear_graphs(fr_ctx* c) {
   }
 }
 
+// Work table of the multi-bucket launch: tiles of epb_multi elements, ordered
+// by decreasing element weight per tile (higher degrees first), bucket order
+// kept among equal weights.  Built on the host and uploaded synchronously.
+fr_status rebuild_work_table(fr_ctx* c) {
+  cudaFree(c->d_work);
+  c->d_work = nullptr;
+  c->n_work = 0;
+  std::vector<std::pair<double, WorkItem>> items;
+  for (size_t bi = 0; bi < c->buckets.size(); ++bi) {
+    const Bucket& b = c->buckets[bi];
+    const int P = b.p + 1, e = epb_multi(c->nd, P);
+    for (int f = 0; f < b.count; f += e) {
+      const int ne = std::min(e, b.count - f);
+      items.push_back({ne * element_weight(c->epb_tab[0][0][1], ipow(P, c->nd), P), WorkItem{(int32_t)bi, (int32_t)f}});
+    }
+  }
+  if (items.empty()) return FR_OK;
+  std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  std::vector<WorkItem> h(items.size());
+  for (size_t i = 0; i < items.size(); ++i) h[i] = items[i].second;
+  void* d = nullptr;
+  if (cudaMalloc(&d, sizeof(WorkItem) * h.size()) != cudaSuccess) {
+    cudaGetLastError();  // out of memory: launches go per bucket instead
+    return FR_ERR_NOMEM;
+  }
+  if (cudaMemcpy(d, h.data(), sizeof(WorkItem) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return cuda_check(cudaGetLastError(), "work table upload");
+  }
+  c->d_work = static_cast<WorkItem*>(d);
+  c->n_work = (int)h.size();
+  return FR_OK;
+}
+
 void clear_work_cache(fr_ctx* c) {
   c->pc_ready = false;   // the layout or the tuning changed: blocks must be rebuilt
-  for (auto& kv : c->work_cache) cudaFree(kv.second.first);
-  c->work_cache.clear();
   clear_graphs(c);
+  rebuild_work_table(c);
 }
 
 fr_status build_layout(fr_ctx* c) {
   const int nd = c->nd, nv = c->nv, nf = c->nf, E = c->E;
-  clear_work_cache(c);
+  c->pc_ready = false;
+  clear_graphs(c);
   // free previous face groups
   for (auto& g : c->fgroups) cudaFree(g.d_recs);
   for (auto& g : c->bgroups) cudaFree(g.d_recs);
@@ -307,6 +341,7 @@ fr_status build_layout(fr_ctx* c) {
     set_error("mortar scratch exceeds its capacity");
     return FR_ERR_INVALID;
   }
+  rebuild_work_table(c);   // a failure leaves no table: launches go per bucket
   return FR_OK;
 }
 
@@ -561,7 +596,10 @@ static void destroy_impl(fr_ctx* c) {
   cudaFree(c->d_nbr);
   for (auto& g : c->fgroups) cudaFree(g.d_recs);
   for (auto& g : c->bgroups) cudaFree(g.d_recs);
-  clear_work_cache(c);
+  clear_graphs(c);
+  cudaFree(c->d_work);
+  c->d_work = nullptr;
+  c->n_work = 0;
   cudaFree(c->d_jidx);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_jidx) cudaFreeHost(c->h_jidx);

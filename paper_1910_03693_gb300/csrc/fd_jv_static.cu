@@ -1,18 +1,23 @@
 // Finite-difference Jacobian-vector product whose three work vectors live in a
 // statically reserved device array, so that the call itself allocates no
-// memory.  Meant for callers that may not allocate device memory once their
-// set-up is done: code that runs while a stream is being captured into a CUDA
-// graph in global capture mode (cudaMalloc is not permitted then), loops with
-// latency or memory-budget rules that forbid allocator calls after start-up,
-// and processes whose device memory is already fully reserved by another
-// allocator (e.g. a framework's caching allocator).
+// memory.  Meant for callers that cannot call cudaMalloc once their set-up is
+// done: processes whose device memory is already fully reserved by another
+// allocator (e.g. a framework's caching allocator), where a new allocation
+// would fail, and loops that must not call the allocator at all, because
+// cudaFree synchronises the whole device and an allocation can stall behind
+// other work.  The residual launches it makes allocate nothing either: the
+// work table of the multi-bucket launch is built when the layout or the
+// tuning changes.
 //
 // The reserved array holds three vectors of at most kStaticFdMaxDof doubles
 // (6 MiB on every device that loads the library, kept until the process
 // exits): R(q), q + eps v and R(q + eps v).  Every call writes each of them
-// before reading it, so nothing has to be cleared between calls.  All calls
-// share the array: two calls whose work overlaps on the GPU (different
-// streams, or different contexts on the same device) race on it.
+// before reading it, so nothing has to be cleared between calls; the array
+// keeps the last call's contents.  All calls share the array: two calls whose
+// work overlaps on the GPU (different streams or threads on the same device)
+// race on it.  The device address is looked up on the first call on each
+// device and cached per device, which is right for the runtime's primary
+// context, the only one supported.
 #include <mutex>
 
 #include "fr_launch.h"

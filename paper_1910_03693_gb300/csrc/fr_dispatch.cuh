@@ -97,11 +97,6 @@ static inline int epb_for(fr_ctx* c, int prec, int kind, int P) {
 // its 256-thread blocks (the tuned per-bucket values size separate launches,
 // whose block is e * n_sp threads; a small one here would leave most of the
 // block idle).
-static inline int epb_multi(int nd, int P) {
-  const int nsp = nsp_of(nd, P);
-  return nsp >= 256 ? 1 : 256 / nsp;
-}
-
 static inline unsigned sm_count(fr_ctx* c) {
   static int n = 0;   // one device per process here; queried once
   if (n <= 0) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
@@ -124,49 +119,14 @@ static inline bool use_multi(fr_ctx* c, int prec, int kind) {
   return c->n_dof / c->nv <= (int64_t)8 * 2048 * sm_count(c);
 }
 
-// Element weight of the multi-bucket work table (tuning slot [0][0][P = 1]):
-// 0 n_sp (p+1) (the default), 1 n_sp, 2 n_sp^2, 3 n_sp^3 -- the paper's
-// candidate element weights for repartitioning (Sec. 3.2), reused as CTA
-// work weights for the order in which the persistent launch takes tiles.
-static inline double element_weight(int model, int nsp, int P) {
-  switch (model) {
-    case 1: return (double)nsp;
-    case 2: return (double)nsp * nsp;
-    case 3: return (double)nsp * nsp * nsp;
-    default: return (double)nsp * P;
-  }
-}
-
-// Work table of the multi-bucket launch: tiles of epb elements, ordered by
-// decreasing weight per tile (higher degrees first), bucket order.
+// Work table of the multi-bucket launch, built when the layout or the tuning
+// changed (rebuild_work_table); never allocated here.  Null when it could not
+// be built: the caller then launches per bucket.
 static const WorkItem* work_items(fr_ctx* c, int prec, int kind, int* n_items) {
-  const int key = prec * 16 + kind;
-  for (auto& kv : c->work_cache)
-    if (kv.first == key) {
-      *n_items = kv.second.second;
-      return (const WorkItem*)kv.second.first;
-    }
-  std::vector<std::pair<double, WorkItem>> items;
-  for (size_t bi = 0; bi < c->buckets.size(); ++bi) {
-    const Bucket& b = c->buckets[bi];
-    const int P = b.p + 1, e = epb_multi(c->nd, P);
-    for (int f = 0; f < b.count; f += e) {
-      const int ne = std::min(e, b.count - f);
-      items.push_back({ne * element_weight(c->epb_tab[0][0][1], nsp_of(c->nd, P), P), WorkItem{(int32_t)bi, (int32_t)f}});
-    }
-  }
-  std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-  std::vector<WorkItem> h(items.size());
-  for (size_t i = 0; i < items.size(); ++i) h[i] = items[i].second;
-  void* d = nullptr;
-  if (cudaMalloc(&d, sizeof(WorkItem) * std::max<size_t>(h.size(), 1)) != cudaSuccess) {
-    cudaGetLastError();  // out of memory: the caller launches per bucket instead
-    return nullptr;
-  }
-  cudaMemcpy(d, h.data(), sizeof(WorkItem) * h.size(), cudaMemcpyHostToDevice);
-  c->work_cache.push_back({key, {d, (int)h.size()}});
-  *n_items = (int)h.size();
-  return (const WorkItem*)d;
+  (void)prec;
+  (void)kind;
+  *n_items = c->n_work;
+  return c->n_work > 0 ? c->d_work : nullptr;
 }
 
 template <typename KernelT>

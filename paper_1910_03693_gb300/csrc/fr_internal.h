@@ -93,6 +93,31 @@ struct BndGroup {
   BndRec* d_recs = nullptr;
 };
 
+// One tile of elements of one bucket: the unit of the multi-bucket launch.
+struct WorkItem {
+  int32_t bucket;   // index into the launch's bucket table
+  int32_t first;    // first element (bucket-local)
+};
+
+// Elements per tile of the multi-bucket launch: as many as fill a 256-thread block.
+inline int epb_multi(int nd, int P) {
+  const int nsp = nd == 2 ? P * P : P * P * P;
+  return nsp >= 256 ? 1 : 256 / nsp;
+}
+
+// Element weight of the multi-bucket work table (tuning slot [0][0][P = 1]):
+// 0 n_sp (p+1) (the default), 1 n_sp, 2 n_sp^2, 3 n_sp^3 -- the paper's
+// candidate element weights for repartitioning (Sec. 3.2), reused as CTA
+// work weights for the order in which the persistent launch takes tiles.
+inline double element_weight(int model, int nsp, int P) {
+  switch (model) {
+    case 1: return (double)nsp;
+    case 2: return (double)nsp * nsp;
+    case 3: return (double)nsp * nsp * nsp;
+    default: return (double)nsp * P;
+  }
+}
+
 struct PhysParams {
   double gamma, mu, Pr, kappa;
   double q_inf[5];
@@ -172,7 +197,7 @@ struct fr_ctx {
   double pc_sigma = 0.0;
   int64_t step_cap = 0;                  // doubles in d_step            // (m+1) * n_dof_cap basis
   int krylov_m = 0;
-  double* d_vec64[12] = {};   // 0-2 FD Jv, 3 Jv, 4-5 GMRES, 6-9 ESDIRK, 10-11 adaptation
+  double* d_vec64[13] = {};   // 0-2 FD Jv, 3 Jv, 4-5 GMRES, 6-9 ESDIRK, 10-11 adaptation, 12 host staging
   float* d_vec32[4] = {};
   double* d_red = nullptr;               // reduction scratch
   int64_t red_cap = 0;
@@ -183,7 +208,11 @@ struct fr_ctx {
   // tables of the multi-bucket launch by (precision, kind)
   int epb_tab[2][3][frgb::kPM + 1] = {};
   bool multi_launch = true;
-  std::vector<std::pair<int, std::pair<void*, int>>> work_cache;
+  // work table of the multi-bucket launch (the same for every precision and
+  // kernel kind), rebuilt eagerly whenever the layout or the weight model
+  // changes, so that no launch ever allocates it
+  frgb::WorkItem* d_work = nullptr;
+  int n_work = 0;
   // CUDA graph of one Arnoldi matrix-vector product -J(q) V[j] (per precision),
   // with the column index read from d_jidx; keyed by the pointers it captured
   cudaGraphExec_t jvp_graph[2] = {nullptr, nullptr};
@@ -211,6 +240,7 @@ struct fr_ctx {
 
 namespace frgb {
 void clear_work_cache(fr_ctx* c);
+fr_status rebuild_work_table(fr_ctx* c);
 void clear_graphs(fr_ctx* c);
 void collect_graph_timers(fr_ctx* c);
 // launchers (kernels_*.cu)

@@ -272,12 +272,6 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs<T> a, int epb) {
   trace_body<T, ND, P, VISC, DIAG>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
 }
 
-// One tile of elements of one bucket: the unit of the multi-bucket launch.
-struct WorkItem {
-  int32_t bucket;   // index into the launch's bucket table
-  int32_t first;    // first element (bucket-local)
-};
-
 constexpr int kMaxBuckets = kMaxDeg + 1;
 
 template <typename T>

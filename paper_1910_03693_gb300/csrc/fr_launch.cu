@@ -83,6 +83,20 @@ __global__ void unpack_kernel(const T* __restrict__ q, double* __restrict__ cano
   }
 }
 
+// Whether a canonical buffer given to fr_pack / fr_unpack is device memory
+// (device or managed allocations, read by the kernels in place) or host memory
+// (page-locked or pageable, copied through the staging vector).
+fr_status canonical_on_device(const void* p, bool* on_device) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    *on_device = false;
+    return FR_OK;
+  }
+  *on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return FR_OK;
+}
+
 fr_status launch_pack(fr_ctx* c, const double* canon, void* q, fr_prec prec, bool unpack, cudaStream_t s) {
   const unsigned g = (unsigned)std::min<int64_t>(c->E, 1 << 20);
   if (!unpack) {
@@ -192,14 +206,35 @@ fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   return FR_OK;
 }
 
-fr_status fr_pack(fr_ctx* c, const double* canon_dev, void* q_dev, fr_prec prec, void* stream) {
-  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) return FR_ERR_INVALID;
-  return launch_pack(c, canon_dev, q_dev, prec, false, (cudaStream_t)stream);
+fr_status fr_pack(fr_ctx* c, const double* canon, void* q_dev, fr_prec prec, void* stream) {
+  if (!c || !canon || !q_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) return FR_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool on_device = false;
+  fr_status st = canonical_on_device(canon, &on_device);
+  if (st != FR_OK) return st;
+  if (on_device) return launch_pack(c, canon, q_dev, prec, false, s);
+  // host buffer (page-locked or pageable): one copy into the staging vector
+  double* stage = vec64(c, kHostStageVec);
+  if (!stage) return FR_ERR_NOMEM;
+  st = cuda_check(cudaMemcpyAsync(stage, canon, sizeof(double) * c->n_dof, cudaMemcpyHostToDevice, s),
+                  "fr_pack: host to device copy");
+  if (st != FR_OK) return st;
+  return launch_pack(c, stage, q_dev, prec, false, s);
 }
 
-fr_status fr_unpack(fr_ctx* c, const void* q_dev, fr_prec prec, double* canon_dev, void* stream) {
-  if (!c || !canon_dev || !q_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) return FR_ERR_INVALID;
-  return launch_pack(c, canon_dev, const_cast<void*>(q_dev), prec, true, (cudaStream_t)stream);
+fr_status fr_unpack(fr_ctx* c, const void* q_dev, fr_prec prec, double* canon, void* stream) {
+  if (!c || !canon || !q_dev || (prec != FR_F64 && prec != FR_F32 && prec != FR_BF16OP)) return FR_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool on_device = false;
+  fr_status st = canonical_on_device(canon, &on_device);
+  if (st != FR_OK) return st;
+  if (on_device) return launch_pack(c, canon, const_cast<void*>(q_dev), prec, true, s);
+  double* stage = vec64(c, kHostStageVec);
+  if (!stage) return FR_ERR_NOMEM;
+  st = launch_pack(c, stage, const_cast<void*>(q_dev), prec, true, s);
+  if (st != FR_OK) return st;
+  return cuda_check(cudaMemcpyAsync(canon, stage, sizeof(double) * c->n_dof, cudaMemcpyDeviceToHost, s),
+                    "fr_unpack: device to host copy");
 }
 
 fr_status fr_residual(fr_ctx* c, const void* q_dev, void* R_dev, fr_prec prec, void* stream) {

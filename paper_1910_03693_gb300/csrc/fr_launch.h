@@ -5,7 +5,11 @@
 
 namespace frgb {
 
-// Device scratch vectors owned by the context, sized n_dof_capacity.
+// Device scratch vectors owned by the context, sized n_dof_capacity (slots
+// 0-2 finite-difference Jv, 3 Jv, 4-5 GMRES, 6-9 ESDIRK, 10-11 adaptation and
+// tuning, 12 staging of host buffers in fr_pack / fr_unpack).
+constexpr int kHostStageVec = 12;
+fr_status canonical_on_device(const void* p, bool* on_device);
 double* vec64(fr_ctx* c, int k);
 float* vec32(fr_ctx* c, int k);
 

@@ -94,13 +94,32 @@ def flux_scale(mesh, q, gamma=1.4):
     return float(fmax * P * P / h_min)
 
 
+class Parity(tuple):
+    """(ok, rel, flux_scaled) with ``legs``: per variable, which bound held
+    ("rel": max|d_v| / max|ref_v|, "flux": max|d_v| / flux scale, or None)."""
+    legs = ()
+
+
 def parity_ok(gpu, ref, mesh, q, tol):
-    """Residual-relative error <= tol, or (where R is small next to the fluxes that
-    cancel in it) flux-scaled error <= tol.  Returns (ok, rel, flux_scaled)."""
-    d = float(np.abs(np.asarray(gpu) - np.asarray(ref)).max())
-    rel = d / max(float(np.abs(ref).max()), 1e-300)
-    fs = d / flux_scale(mesh, q)
-    return (rel <= tol or fs <= tol), rel, fs
+    """Per variable v: max|d_v| / max|ref_v| <= tol, or (where R_v is small next
+    to the fluxes that cancel in it) max|d_v| / flux_scale <= tol.  Returns
+    (ok, rel, flux_scaled) with rel and flux_scaled the worst variable's values
+    and ``.legs`` naming the bound each variable met."""
+    nv = mesh.nd + 2
+    d = np.abs(np.asarray(gpu) - np.asarray(ref)).reshape(-1, nv)
+    r = np.abs(np.asarray(ref)).reshape(-1, nv)
+    fsc = flux_scale(mesh, q)
+    legs, rels, fss = [], [], []
+    for v in range(nv):
+        dv = float(d[:, v].max())
+        rel = dv / max(float(r[:, v].max()), 1e-300)
+        fs = dv / fsc
+        rels.append(rel)
+        fss.append(fs)
+        legs.append("rel" if rel <= tol else ("flux" if fs <= tol else None))
+    out = Parity((all(l is not None for l in legs), max(rels), max(fss)))
+    out.legs = tuple(legs)
+    return out
 
 
 def generic_state(q, seed=77, amp=1e-3):

@@ -112,3 +112,37 @@ def test_nodal_filter_matches_oracle(built, name):
     assert np.abs(got - ref).max() <= 1e-13 * np.abs(q).max()
     low = np.repeat(m.p <= 2, [(int(p) + 1) ** m.nd * m.nv for p in m.p])
     assert np.array_equal(got[low], q[low])
+
+
+@pytest.mark.parametrize("emax", [1.0, 0.7371, 3.1e-5])
+def test_decision_at_thresholds_bit_exact(built, emax):
+    """The degree decision (Sec. 3.1: raise when eta > nu_max eta_max, lower when
+    eta < nu_min eta_max, strict) on eta values planted exactly at the two
+    thresholds and one ulp on either side, the same eta array given to both
+    sides: the new p-map must equal the oracle's bit for bit.  (eta itself
+    agrees to ~1e-15 only: the two sides build their Legendre tables
+    independently and round them differently in the last bit.)"""
+    from oracle import adapt
+    m, q, ph = WL["vortex2d_16x16_p2"]
+    E = m.n_elem
+    nu_max, nu_min = 0.1, 0.001
+    up, dn = nu_max * emax, nu_min * emax
+    cand = [up, np.nextafter(up, np.inf), np.nextafter(up, -np.inf),
+            dn, np.nextafter(dn, np.inf), np.nextafter(dn, -np.inf), emax, 0.0]
+    eta = np.array([cand[(7 * e) % len(cand)] for e in range(E)], dtype=np.float64)
+    eta[E // 2] = emax                       # the maximum is attained
+    p_ref = adapt.limit_jumps(m, adapt.decide(eta, m.p, nu_max, nu_min, 1, 4))
+    ctx = gpu_ctx(m, ph, p_min=1, p_max=4)
+    buf = torch.zeros(ctx.n_dof_capacity, dtype=torch.float64, device="cuda")
+    ctx.pack(torch.from_numpy(q).cuda(), out=buf[:ctx.n_dof])
+    eta_d = torch.from_numpy(eta).cuda()
+    emax_d = torch.tensor([eta.max()], dtype=torch.float64, device="cuda")
+    ctx.rebucket(eta_d, emax_d, buf, nu_max, nu_min, 1, 4)
+    assert np.array_equal(ctx.p_map(), p_ref.astype(np.int8))
+    # the planted ulps decide: up+1ulp raises, up stays, dn-1ulp lowers, dn stays
+    dec = adapt.decide(eta, m.p, nu_max, nu_min, 1, 4)
+    base = int(m.p[0])
+    assert np.all(dec[eta == np.nextafter(up, np.inf)] == base + 1)
+    assert np.all(dec[eta == up] == base)
+    assert np.all(dec[eta == np.nextafter(dn, -np.inf)] == base - 1)
+    assert np.all(dec[eta == dn] == base)
