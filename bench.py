@@ -126,7 +126,7 @@ def _operator_of(kernel):
         return "jvp", s
     if "_res_" in kernel:
         return "residual", s
-    if kernel.startswith("trace_"):   # FP32 traces serve the JVP's tangent in the step
+    if kernel.startswith(("trace_", "ctrace_")):   # FP32 traces serve the JVP's tangent in the step
         return ("jvp" if s == 4 else "residual"), s
     return None
 
@@ -587,7 +587,7 @@ def main():
     ctx.timing(False)
     clocks = sampler.stop()
 
-    n_evals = sum(v[0] for k, v in report.items() if k.startswith("vol_res") or k.startswith("vol_jvp"))
+    n_evals = sum(v[0] for k, v in report.items() if k.startswith(("vol_res", "vol_jvp", "fused_jvp")))
     units = N * n_evals                       # DOF-evaluations over the K steps on this rank
     total_ms, units = reduce_over_ranks(total_ms, units, dist if world > 1 else None)
     value = units / (total_ms / 1e3) / 1e9
@@ -634,7 +634,7 @@ def main():
         e2e_ms += e0.elapsed_time(e1)
     rep_e2e, _ = ctx.timing_report()
     ctx.timing(False)
-    evals_e2e = sum(v[0] for k, v in rep_e2e.items() if k.startswith("vol_res") or k.startswith("vol_jvp"))
+    evals_e2e = sum(v[0] for k, v in rep_e2e.items() if k.startswith(("vol_res", "vol_jvp", "fused_jvp")))
     e2e_ms, e2e_units = reduce_over_ranks(e2e_ms, N * evals_e2e, dist if world > 1 else None)
     e2e = {"value": e2e_units / (e2e_ms / 1e3) / 1e9, "unit": "GDOF/s",
            "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,

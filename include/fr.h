@@ -392,6 +392,11 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
 #define FR_TUNE_GRAPHS 2        /* Arnoldi products replayed from a CUDA graph */
 #define FR_TUNE_DIAG_METRICS 4  /* 3D meshes of axis-aligned affine elements:
                                    kernels that skip the zero metric terms   */
+#define FR_TUNE_FUSED_JVP 8     /* meshes whose faces are all interior and
+                                   conforming (same degree both sides, no
+                                   boundary): the exact JVP as compact traces
+                                   plus one face-and-volume kernel per element
+                                   tile, no face-output array in memory      */
 fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
 fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
 fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);

@@ -217,6 +217,50 @@ void clear_work_cache(fr_ctx* c) {
   rebuild_work_table(c);
 }
 
+// The fused JVP's tables: compact-trace bases of the buckets and, when every
+// face is interior and conforming, the neighbour of every element face with
+// the master / slave assignment of the face records (higher degree, then lower
+// element id, then lower face index).
+static fr_status build_fused_table(fr_ctx* c, const std::vector<int32_t>& elem_slot) {
+  const int nd = c->nd, nf = c->nf, E = c->E;
+  const int ct = c->visc ? 2 * c->nv : c->nv;
+  int64_t cb = 0;
+  std::vector<int> bucket_of_p(kMaxDeg + 1, -1);
+  for (size_t k = 0; k < c->buckets.size(); ++k) {
+    Bucket& b = c->buckets[k];
+    b.ctrace_base = cb;
+    cb += (int64_t)b.count * nf * ct * ipow(b.p + 1, nd - 1);
+    bucket_of_p[b.p] = (int)k;
+  }
+  c->fused_ok = c->bgroups.empty() && cb <= c->trace_cap;
+  for (const auto& g : c->fgroups)
+    if (g.pm != g.ps) c->fused_ok = false;
+  if (!c->fused_ok) return FR_OK;
+  std::vector<FusedNbr> h((size_t)E * nf);
+  for (int s = 0; s < E; ++s) {
+    const int e = c->slot_elem[s];
+    for (int f = 0; f < nf; ++f) {
+      const int n = c->nbr[(size_t)e * nf + f];
+      const int g = c->nbr_face[(size_t)e * nf + f];
+      if (n < 0 || c->p[n] != c->p[e]) {
+        c->fused_ok = false;
+        return FR_OK;
+      }
+      const bool master = e < n || (e == n && f < g);
+      const Bucket& b = c->buckets[bucket_of_p[c->p[n]]];
+      FusedNbr r;
+      r.nloc = elem_slot[n] - b.slot_begin;
+      r.nelem = n;
+      r.g = g;
+      r.code = (int32_t)(uint8_t)c->orient[(size_t)e * nf + f] | (master ? 256 : 0);
+      h[(size_t)s * nf + f] = r;
+    }
+  }
+  if (!c->d_fnbr) FR_CUDA(cudaMalloc(&c->d_fnbr, sizeof(FusedNbr) * (size_t)E * nf));
+  FR_CUDA(cudaMemcpy(c->d_fnbr, h.data(), sizeof(FusedNbr) * h.size(), cudaMemcpyHostToDevice));
+  return FR_OK;
+}
+
 fr_status build_layout(fr_ctx* c) {
   const int nd = c->nd, nv = c->nv, nf = c->nf, E = c->E;
   c->pc_ready = false;
@@ -341,6 +385,7 @@ fr_status build_layout(fr_ctx* c) {
     set_error("mortar scratch exceeds its capacity");
     return FR_ERR_INVALID;
   }
+  FR_TRY(build_fused_table(c, elem_slot));
   rebuild_work_table(c);   // a failure leaves no table: launches go per bucket
   return FR_OK;
 }
@@ -600,6 +645,7 @@ static void destroy_impl(fr_ctx* c) {
   cudaFree(c->d_work);
   c->d_work = nullptr;
   c->n_work = 0;
+  cudaFree(c->d_fnbr);
   cudaFree(c->d_jidx);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_jidx) cudaFreeHost(c->h_jidx);

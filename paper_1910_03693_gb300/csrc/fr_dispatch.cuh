@@ -9,6 +9,7 @@
 
 #include "fr_kernels.cuh"
 #include "fr_launch.h"
+#include "fused_jvp.cuh"
 #include "vjp_kernels.cuh"
 
 namespace frgb {
@@ -377,11 +378,117 @@ static void residual_out64_impl(fr_ctx* c, const T* q, double* R, cudaStream_t s
   launch_vols<T, ND, VISC, 0, DIAG>(c, q, nullptr, nullptr, s, nullptr, R);
 }
 
+// ---------------------------------------------------------------------------
+// Fused JVP (every face interior and conforming): compact traces, then one
+// face-and-volume kernel per bucket
+// ---------------------------------------------------------------------------
+static inline bool fused_jvp_on(const fr_ctx* c) { return c->fused_ok && c->use_fused; }
+
+template <typename T, int ND, int P, bool VISC>
+static void launch_ctrace_p(const CTraceArgs<T>& a, int epb, cudaStream_t s) {
+  const size_t smem = (size_t)epb * (ND + 2) * Shape<ND, P>::NSP * sizeof(T);
+  ctrace_kernel<T, ND, P, VISC><<<nblocks(a.count, epb), epb * Shape<ND, P>::NSP, smem, s>>>(a, epb);
+}
+
+template <typename T, int ND, bool VISC>
+static void launch_ctraces(fr_ctx* c, const T* q, T* out, cudaStream_t s) {
+  constexpr int NV = ND + 2, NF = 2 * ND, CT = VISC ? 2 * NV : NV;
+  for (const auto& b : c->buckets) {
+    const int P = b.p + 1, e = epb_multi(ND, P);
+    CTraceArgs<T> a;
+    a.q = q;
+    a.out = out;
+    a.basis = basis_ptr<T>(c);
+    a.state_base = b.state_base;
+    a.ctrace_base = b.ctrace_base;
+    a.count = b.count;
+    const double nb = (double)b.count * (NV * nsp_of(ND, P) + NF * CT * ipow(P, ND - 1)) * sizeof(T);
+    FR_LAUNCH_B(c, kname<T>("ctrace_f64", "ctrace_f32", "ctrace_df"), s, nb, {
+      switch (P) {
+        case 2: launch_ctrace_p<T, ND, 2, VISC>(a, e, s); break;
+        case 3: launch_ctrace_p<T, ND, 3, VISC>(a, e, s); break;
+        case 4: launch_ctrace_p<T, ND, 4, VISC>(a, e, s); break;
+        case 5: launch_ctrace_p<T, ND, 5, VISC>(a, e, s); break;
+        case 6: launch_ctrace_p<T, ND, 6, VISC>(a, e, s); break;
+      }
+    });
+  }
+}
+
+// Elements per CTA of the fused kernel: as many as fill 256 threads, at most as
+// many as leave shared memory for two CTAs on an SM.
+template <typename T, int ND, int P, bool VISC>
+static int fused_epb() {
+  const size_t per = (size_t)FusedSmem<ND, P, VISC>::PER * sizeof(T);
+  const int by_smem = (int)std::max<size_t>(1, (size_t)(113 * 1024) / per);
+  return std::max(1, std::min(epb_multi(ND, P), by_smem));
+}
+
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+static void launch_fused_p(const FusedArgs<T>& a, cudaStream_t s) {
+  const int epb = fused_epb<T, ND, P, VISC>();
+  const size_t smem = (size_t)epb * FusedSmem<ND, P, VISC>::PER * sizeof(T);
+  auto kern = fused_jvp_kernel<T, ND, P, VISC, DIAG>;
+  static size_t configured = 0;
+  ensure_smem(kern, smem, configured);
+  kern<<<nblocks(a.count, epb), epb * Shape<ND, P>::NSP, smem, s>>>(a, epb);
+}
+
+template <typename T, int ND, bool VISC, bool DIAG>
+static void jvp_fused_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready,
+                           double* neg64) {
+  constexpr int NV = ND + 2, NF = 2 * ND, CT = VISC ? 2 * NV : NV;
+  T* trq = (T*)c->d_trace_q;
+  T* trv = (T*)c->d_trace_v;
+  if (!q_traces_ready) launch_ctraces<T, ND, VISC>(c, q, trq, s);
+  launch_ctraces<T, ND, VISC>(c, v, trv, s);
+  for (const auto& b : c->buckets) {
+    FusedArgs<T> a;
+    a.q = q;
+    a.v = v;
+    a.trq = trq;
+    a.trv = trv;
+    a.out = Jv;
+    a.out_neg64 = neg64;
+    a.nbr = (const FusedNbr*)c->d_fnbr;
+    a.slot_elem = c->d_slot_elem;
+    a.basis = basis_ptr<T>(c);
+    a.geo = geo_view<T>(c, b.p);
+    a.gamma = (T)c->phys.gamma;
+    a.mu = (T)c->phys.mu;
+    a.kappa = (T)c->phys.kappa;
+    a.flux = c->phys.flux;
+    a.state_base = b.state_base;
+    a.ctrace_base = b.ctrace_base;
+    a.count = b.count;
+    a.slot_begin = b.slot_begin;
+    const int P = b.p + 1, NSP = nsp_of(ND, P), NFP = ipow(P, ND - 1);
+    // q and v in; the neighbours' compact traces of q and v; J v out (FP64 when negated)
+    const double nb = (double)b.count * ((2.0 * NV * NSP + 2.0 * NF * CT * NFP) * sizeof(T) +
+                                         (double)NV * NSP * (neg64 ? 8 : sizeof(T)));
+    FR_LAUNCH_B(c, kname<T>("fused_jvp_f64", "fused_jvp_f32", "fused_jvp_df"), s, nb, {
+      switch (P) {
+        case 2: launch_fused_p<T, ND, 2, VISC, DIAG>(a, s); break;
+        case 3: launch_fused_p<T, ND, 3, VISC, DIAG>(a, s); break;
+        case 4: launch_fused_p<T, ND, 4, VISC, DIAG>(a, s); break;
+        case 5: launch_fused_p<T, ND, 5, VISC, DIAG>(a, s); break;
+        case 6: launch_fused_p<T, ND, 6, VISC, DIAG>(a, s); break;
+      }
+    });
+  }
+}
+
 // JVP; with q_traces_ready the traces of q in d_trace_q are reused (q is
 // fixed during one GMRES solve)
 template <typename T, int ND, bool VISC, bool DIAG = false>
 static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready = false,
                      double* neg64 = nullptr) {
+  if constexpr (!is_dfloat<T>::value) {
+    if (fused_jvp_on(c)) {
+      jvp_fused_impl<T, ND, VISC, DIAG>(c, q, v, Jv, s, q_traces_ready, neg64);
+      return;
+    }
+  }
   T* trq = (T*)c->d_trace_q;
   T* trv = (T*)c->d_trace_v;
   if (!q_traces_ready) launch_traces<T, ND, VISC, DIAG>(c, q, trq, s);
@@ -650,7 +757,10 @@ static void run_op_cfg(fr_ctx* c, int op, const void* q, const void* v, void* ou
   if (op == 0) residual_impl<T, ND, VISC, DIAG>(c, qq, oo, s);
   else if (op == 1) jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, oo, s);
   else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);
-  else if (op == 3) launch_traces<T, ND, VISC, DIAG>(c, qq, (T*)c->d_trace_q, s);
+  else if (op == 3) {
+    if (fused_jvp_on(c)) launch_ctraces<T, ND, VISC>(c, qq, (T*)c->d_trace_q, s);
+    else launch_traces<T, ND, VISC, DIAG>(c, qq, (T*)c->d_trace_q, s);
+  }
   else if (op == 5) autotune_impl<T, ND, VISC, DIAG>(c, qq, oo, 3, s);
   else if (op == 6) jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, nullptr, s, true, (double*)out);
   else jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, oo, s, true);

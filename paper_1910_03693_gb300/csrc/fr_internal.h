@@ -81,6 +81,7 @@ struct Bucket {
   int64_t state_base = 0;   // values
   int64_t trace_base = 0;   // values
   int64_t out_base = 0;     // values
+  int64_t ctrace_base = 0;  // values: compact traces of the fused JVP (q and its normal derivative)
 };
 
 struct FaceGroup {
@@ -97,6 +98,14 @@ struct BndGroup {
 struct WorkItem {
   int32_t bucket;   // index into the launch's bucket table
   int32_t first;    // first element (bucket-local)
+};
+
+// Neighbour of one element face for the fused JVP (slot-major, face-minor).
+struct FusedNbr {
+  int32_t nloc;    // the neighbour's bucket-local index (conforming faces: the same bucket)
+  int32_t nelem;   // the neighbour's element id (its geometry)
+  int32_t g;       // the neighbour's face
+  int32_t code;    // bits 0-7: orientation code (this side's point -> the neighbour's); bit 8: this side is the master
 };
 
 // Elements per tile of the multi-bucket launch: as many as fill a 256-thread block.
@@ -213,6 +222,12 @@ struct fr_ctx {
   // changes, so that no launch ever allocates it
   frgb::WorkItem* d_work = nullptr;
   int n_work = 0;
+  // fused JVP: every face interior and conforming (then the exact JVP runs as
+  // compact traces + one face-and-volume kernel); the neighbour of every
+  // element face, slot-major (frgb::FusedNbr)
+  bool fused_ok = false;
+  bool use_fused = true;
+  void* d_fnbr = nullptr;
   // CUDA graph of one Arnoldi matrix-vector product -J(q) V[j] (per precision),
   // with the column index read from d_jidx; keyed by the pointers it captured
   cudaGraphExec_t jvp_graph[2] = {nullptr, nullptr};

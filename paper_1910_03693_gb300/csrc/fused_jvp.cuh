@@ -1,0 +1,483 @@
+// Fused exact JVP (Sec. 2.2 differentiated; the GMRES product of Sec. 2.3) for
+// meshes whose faces are all interior and conforming (the same degree on both
+// sides, no boundary): the Taylor-Green and Fourier-mode boxes, periodic
+// vortices and batches of them.
+//
+// Two passes instead of three:
+//   1. compact traces: q and its reference normal derivative at every face
+//      point (2 NV values, against NV (1 + ND) for the trace-gradient layout),
+//      written once per Newton iteration for q and once per product for v;
+//   2. one kernel per element tile: the element's own traces are rebuilt on
+//      chip from its solution points, the neighbours' compact traces of the
+//      shared faces are gathered from global memory, the tangential
+//      derivatives of both sides are formed from the face traces, and the
+//      common flux, BR2 gradient and lifting are evaluated at every face point
+//      of the element in the master's orientation (master and slave as the
+//      face records define them), so that both sides of a face evaluate the
+//      same expression on the same values and receive exactly opposite fluxes;
+//      the corrected gradient, fluxes, divergence and correction follow from
+//      the face outputs kept in shared memory.
+// No face-output array goes through HBM; the face flux is evaluated twice
+// (once from each side), which costs arithmetic instead of bytes.
+//
+// Layouts: compact traces [slot][face][CT][NFP] (CT = 2 NV for Navier-Stokes:
+// q then the normal derivative; NV for Euler), at a per-bucket base.
+#pragma once
+
+#include "fr_kernels.cuh"
+
+namespace frgb {
+
+// Explicit fused multiply-adds: the compact traces of q are formed by two
+// kernels (the trace pass and, for the element itself, the fused kernel), and
+// both sides of a face must see the same bits.
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <bool VISC, int NV>
+struct CompactWidth {
+  static constexpr int value = VISC ? 2 * NV : NV;
+};
+
+// q and (Navier-Stokes) the reference normal derivative at face point fp of an
+// element staged in shared memory as [NV][NSP].
+template <typename T, int ND, int P, bool VISC>
+__device__ __forceinline__ void trace_point(const T* sq, const BasisTab<T>& B, int fp, T* qf, T* dn) {
+  using Sh = Shape<ND, P>;
+  constexpr int NV = Sh::NV, NSP = Sh::NSP, NFP = Sh::NFP;
+  const int f = fp / NFP, t = fp % NFP, d = f >> 1, s = f & 1;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T x[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) x[k] = sq[v * NSP + line_sp<ND, P>(d, t, k)];
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < P; ++k) acc = xfma(B.ext[s][k], x[k], acc);
+    qf[v] = acc;
+    if (VISC) {
+      T an = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) an = xfma(B.dext[s][k], x[k], an);
+      dn[v] = an;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: compact traces.  One thread per solution point for the load, then
+// per face point.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CTraceArgs {
+  const T* q;
+  T* out;
+  const BasisTab<T>* basis;
+  int64_t state_base, ctrace_base;
+  int count;
+};
+
+template <typename T, int ND, int P, bool VISC>
+__global__ void __launch_bounds__(256) ctrace_kernel(CTraceArgs<T> a, int epb) {
+  using Sh = Shape<ND, P>;
+  constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
+  constexpr int CT = CompactWidth<VISC, NV>::value;
+  constexpr int NFPT = NF * NFP, ITERS = (NFPT + NSP - 1) / NSP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int le = threadIdx.x / NSP, lt = threadIdx.x % NSP;
+  const int64_t i = (int64_t)blockIdx.x * epb + le;
+  const bool valid = le < epb && i < a.count;
+  T* sq = reinterpret_cast<T*>(smem_raw) + le * NV * NSP;
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sq[v * NSP + lt] = a.q[a.state_base + (i * NV + v) * NSP + lt];
+  }
+  __syncthreads();
+  if (!valid) return;
+  const BasisTab<T>& B = a.basis[P];
+  T* out = a.out + a.ctrace_base + i * NF * CT * NFP;
+#pragma unroll
+  for (int it = 0; it < ITERS; ++it) {
+    const int fp = lt + it * NSP;
+    if (fp >= NFPT) break;
+    const int f = fp / NFP, t = fp % NFP;
+    T qf[NV], dn[NV];
+    trace_point<T, ND, P, VISC>(sq, B, fp, qf, dn);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      out[(f * CT + v) * NFP + t] = qf[v];
+      if (VISC) out[(f * CT + NV + v) * NFP + t] = dn[v];
+    }
+  }
+}
+
+// Physical gradient (value and tangent) at point t of face fc from that
+// face's compact traces Xq (of q) and Xv (of v), laid out [CT][NFP]: the
+// normal derivative is stored, the two tangential derivatives differentiate
+// the face trace along its own axes (P terms each), and the face metric terms
+// map reference to physical derivatives.
+template <typename T, int ND, int P, bool DIAG>
+__device__ __forceinline__ void face_grad(const T* Xq, const T* Xv, int fc, int t, const GeoView<T>& geo, int64_t e,
+                                          const BasisTab<T>& B, Dual<T> (*G)[ND + 2]) {
+  constexpr int NV = ND + 2;
+  constexpr int NFP = ND == 2 ? P : P * P;
+  const int dc = fc >> 1;
+  const int ia = t % P, ib = ND == 3 ? t / P : 0;
+  const int ta = dc == 0 ? 1 : 0;
+  const int tb = dc == 2 ? 1 : 2;
+  T Sf[ND][ND];
+#pragma unroll
+  for (int dd = 0; dd < ND; ++dd)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) Sf[dd][j] = (DIAG && dd != j) ? T(0) : geo_face(geo, e, fc, dd * ND + j, t);
+  const T Jinv = geo_face(geo, e, fc, ND * ND + 1, t);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Dual<T> dq[ND];
+    dq[dc] = Dual<T>{Xq[(NV + v) * NFP + t], Xv[(NV + v) * NFP + t]};
+    const T* yq = Xq + v * NFP;
+    const T* yv = Xv + v * NFP;
+    T aq = T(0), av = T(0);
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      aq = xfma(B.D[ia][m], yq[m + P * ib], aq);
+      av = xfma(B.D[ia][m], yv[m + P * ib], av);
+    }
+    dq[ta] = Dual<T>{aq, av};
+    if (ND == 3) {
+      aq = T(0);
+      av = T(0);
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        aq = xfma(B.D[ib][m], yq[ia + P * m], aq);
+        av = xfma(B.D[ib][m], yv[ia + P * m], av);
+      }
+      dq[tb] = Dual<T>{aq, av};
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      Dual<T> g{T(0), T(0)};
+      if (DIAG) {
+        g = Sf[j][j] * dq[j];
+      } else {
+#pragma unroll
+        for (int dd = 0; dd < ND; ++dd) g = g + Sf[dd][j] * dq[dd];
+      }
+      G[j][v] = g * Jinv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: faces and volume of a tile of elements.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FusedArgs {
+  const T* q;           // state (bucket layout)
+  const T* v;           // tangent
+  const T* trq;         // compact traces of q and of v (all buckets)
+  const T* trv;
+  T* out;               // J v in T, or
+  double* out_neg64;    // -J v in FP64 (the Arnoldi vector) when non-null
+  const FusedNbr* nbr;  // [slot][NF]
+  const int32_t* slot_elem;
+  const BasisTab<T>* basis;
+  GeoView<T> geo;
+  T gamma, mu, kappa;
+  int flux;
+  int64_t state_base, ctrace_base;
+  int count, slot_begin;
+};
+
+// Shared memory of one element, in values of T: the state and tangent, the
+// four compact-trace blocks (own q and v, the neighbours' q and v), which the
+// volume fluxes (ND x NV duals a point) reuse once the faces are done, and
+// the face outputs.
+template <int ND, int P, bool VISC>
+struct FusedSmem {
+  static constexpr int NV = ND + 2, NF = 2 * ND;
+  static constexpr int NSP = Shape<ND, P>::NSP, NFP = Shape<ND, P>::NFP;
+  static constexpr int CT = CompactWidth<VISC, NV>::value;
+  static constexpr int TB = NF * CT * NFP;                     // compact traces of one element (q or v)
+  static constexpr int FO = (VISC ? 3 : 1) * NV * NFP;         // face outputs of one face
+  static constexpr int REG = 4 * TB > 2 * ND * NV * NSP ? 4 * TB : 2 * ND * NV * NSP;
+  static constexpr int PER = 2 * NV * NSP + REG + NF * FO;
+};
+
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+__global__ void __launch_bounds__(256, 2) fused_jvp_kernel(FusedArgs<T> a, int epb) {
+  using Sh = Shape<ND, P>;
+  using Sm = FusedSmem<ND, P, VISC>;
+  using S = Dual<T>;
+  constexpr int NV = Sh::NV, NF = Sh::NF, NSP = Sh::NSP, NFP = Sh::NFP;
+  constexpr int CT = Sm::CT, TB = Sm::TB, FO = Sm::FO;
+  constexpr int NFPT = NF * NFP, ITERS = (NFPT + NSP - 1) / NSP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int le = threadIdx.x / NSP, lt = threadIdx.x % NSP;
+  const int64_t i = (int64_t)blockIdx.x * epb + le;
+  const bool valid = le < epb && i < a.count;
+  T* base = reinterpret_cast<T*>(smem_raw) + (int64_t)le * Sm::PER;
+  T* sqq = base;                 // [NV][NSP] own q
+  T* sqv = sqq + NV * NSP;       // [NV][NSP] own v
+  T* Aq = sqv + NV * NSP;        // [NF][CT][NFP] own compact traces of q
+  T* Av = Aq + TB;               //                of v
+  T* Bq = Av + TB;               // [NF][CT][NFP] the neighbour's traces of the shared face (its point order)
+  T* Bv = Bq + TB;
+  T* C = Aq + Sm::REG;           // [NF][FO / NFP][NFP] tangent F~com (then, NS: primal dq, tangent dq)
+  S* sF = reinterpret_cast<S*>(Aq);   // [ND][NV][NSP] volume fluxes, once the faces are done
+  const BasisTab<T>& B = a.basis[P];
+  const int64_t slot = a.slot_begin + i;
+
+  // 1. own state and tangent
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int64_t k = a.state_base + (i * NV + v) * NSP + lt;
+      sqq[v * NSP + lt] = a.q[k];
+      sqv[v * NSP + lt] = a.v[k];
+    }
+  }
+  __syncthreads();
+
+  // 2. own compact traces; the neighbours' traces of the shared faces
+  if (valid) {
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+      const int fp = lt + it * NSP;
+      if (fp >= NFPT) break;
+      const int f = fp / NFP, t = fp % NFP;
+      T qf[NV], dn[NV];
+      trace_point<T, ND, P, VISC>(sqq, B, fp, qf, dn);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Aq[(f * CT + v) * NFP + t] = qf[v];
+        if (VISC) Aq[(f * CT + NV + v) * NFP + t] = dn[v];
+      }
+      trace_point<T, ND, P, VISC>(sqv, B, fp, qf, dn);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Av[(f * CT + v) * NFP + t] = qf[v];
+        if (VISC) Av[(f * CT + NV + v) * NFP + t] = dn[v];
+      }
+    }
+    for (int idx = lt; idx < TB; idx += NSP) {
+      const int f = idx / (CT * NFP), rem = idx % (CT * NFP);
+      const FusedNbr nb = a.nbr[slot * NF + f];
+      const int64_t src = a.ctrace_base + ((int64_t)nb.nloc * NF + nb.g) * CT * NFP + rem;
+      Bq[idx] = a.trq[src];
+      Bv[idx] = a.trv[src];
+    }
+  }
+  __syncthreads();
+
+  // 3. common flux, BR2 gradient and lifting at every face point of the element
+  if (valid) {
+    const int64_t e = a.slot_elem[slot];
+#pragma unroll 1
+    for (int it = 0; it < ITERS; ++it) {
+      const int fp = lt + it * NSP;
+      if (fp >= NFPT) break;
+      const int f = fp / NFP, t = fp % NFP;
+      const FusedNbr nb = a.nbr[slot * NF + f];
+      const int u = orient_map(nb.code & 0xff, t, P, ND);
+      const bool master = (nb.code >> 8) & 1;
+      const int64_t eM = master ? e : (int64_t)nb.nelem, eS = master ? (int64_t)nb.nelem : e;
+      const int fM = master ? f : nb.g, fS = master ? nb.g : f;
+      const int tM = master ? t : u, tS = master ? u : t;
+      const T* XqM = (master ? Aq : Bq) + f * CT * NFP;
+      const T* XvM = (master ? Av : Bv) + f * CT * NFP;
+      const T* XqS = (master ? Bq : Aq) + f * CT * NFP;
+      const T* XvS = (master ? Bv : Av) + f * CT * NFP;
+      S qM[NV], qS[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        qM[v] = S{XqM[v * NFP + tM], XvM[v * NFP + tM]};
+        qS[v] = S{XqS[v * NFP + tS], XvS[v * NFP + tS]};
+      }
+      const int dm = fM >> 1, sm = fM & 1, ss = fS & 1;
+      const T sgm = sm ? T(1) : T(-1);
+      const T absA = geo_face(a.geo, eM, fM, ND * ND + 2 + dm, tM);
+      const T inv_absA = geo_face(a.geo, eM, fM, ND * ND + 2 + ND + dm, tM);
+      T A[ND], n[ND];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        A[j] = sgm * geo_face(a.geo, eM, fM, dm * ND + j, tM);
+        n[j] = A[j] * inv_absA;
+      }
+      S Fn[NV];
+      common_flux<ND>(a.flux, qM, qS, n, absA, a.gamma, Fn);
+      S qc[NV];
+      if (VISC) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qS[v]);
+        const int ds = fS >> 1;
+        T cM[ND], cS[ND];
+        const T gJM = B.dgf[sm] * geo_face(a.geo, eM, fM, ND * ND + 1, tM);
+        const T gJS = B.dgf[ss] * geo_face(a.geo, eS, fS, ND * ND + 1, tS);
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          cM[j] = gJM * geo_face(a.geo, eM, fM, dm * ND + j, tM);
+          cS[j] = gJS * geo_face(a.geo, eS, fS, ds * ND + j, tS);
+        }
+        S GM[ND][NV], GS[ND][NV], Gc[ND][NV];
+        face_grad<T, ND, P, DIAG>(XqM, XvM, fM, tM, a.geo, eM, B, GM);
+        face_grad<T, ND, P, DIAG>(XqS, XvS, fS, tS, a.geo, eS, B, GS);
+        if (DIAG) {
+#pragma unroll
+          for (int j = 0; j < ND; ++j)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Gc[j][v] = T(0.5) * (GM[j][v] + GS[j][v]);
+#pragma unroll
+          for (int j = 0; j < ND; ++j) {
+            if (j != dm) continue;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+              Gc[j][v] = Gc[j][v] + T(0.5) * (cM[j] * (qc[v] - qM[v]) + cS[j] * (qc[v] - qS[v]));
+          }
+          S fr[NV];
+          flux_viscous_row<ND>(qc, Gc, a.gamma, a.mu, a.kappa, dm, fr);
+          T Ad = T(0);
+#pragma unroll
+          for (int j = 0; j < ND; ++j)
+            if (j == dm) Ad = A[j];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Fn[v] = Fn[v] - fr[v] * Ad;
+        } else {
+#pragma unroll
+          for (int j = 0; j < ND; ++j)
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+              Gc[j][v] = T(0.5) * (GM[j][v] + cM[j] * (qc[v] - qM[v]) + GS[j][v] + cS[j] * (qc[v] - qS[v]));
+          S fv[ND][NV];
+          flux_viscous<ND>(qc, Gc, a.gamma, a.mu, a.kappa, fv);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            S acc = szero<S>();
+#pragma unroll
+            for (int j = 0; j < ND; ++j) acc = acc + fv[j][v] * A[j];
+            Fn[v] = Fn[v] - acc;
+          }
+        }
+      }
+      const T sgs = ss ? T(1) : T(-1);
+      T* Cf = C + f * FO;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const S x = master ? sgm * Fn[v] : sgs * (T(0) - Fn[v]);
+        Cf[v * NFP + t] = tangent(x);
+        if (VISC) {
+          const S dq = qc[v] - (master ? qM[v] : qS[v]);
+          Cf[(NV + v) * NFP + t] = value(dq);
+          Cf[(2 * NV + v) * NFP + t] = tangent(dq);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // 4. corrected gradient, fluxes, divergence and correction (as the volume kernel)
+  int idx[3];
+  idx[0] = lt % P;
+  idx[1] = (lt / P) % P;
+  idx[2] = ND == 3 ? lt / (P * P) : 0;
+  T Smt[ND][ND];
+  T Jinv = T(1);
+  if (valid) {
+    const int64_t e = a.slot_elem[slot];
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+      for (int j = 0; j < ND; ++j) Smt[d][j] = (DIAG && d != j) ? T(0) : geo_vol(a.geo, e, d * ND + j, lt);
+    Jinv = geo_vol(a.geo, e, ND * ND + 1, lt);
+    S q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = S{sqq[v * NSP + lt], sqv[v * NSP + lt]};
+    S f[ND][NV];
+    flux_inviscid<ND>(q, a.gamma, f);
+    if (VISC) {
+      S gref[ND][NV];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        const int stride = d == 0 ? 1 : (d == 1 ? P : P * P);
+        const int lb = lt - idx[d] * stride;
+        const int tf = face_pt<ND, P>(d, idx);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          Acc<S> acc = acc_init(szero<S>());
+#pragma unroll
+          for (int k = 0; k < P; ++k)
+            acc_madd(acc, B.D[idx[d]][k], S{sqq[v * NSP + lb + k * stride], sqv[v * NSP + lb + k * stride]});
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const T* Cf = C + (2 * d + s) * FO;
+            acc_madd(acc, B.dg[s][idx[d]], S{Cf[(NV + v) * NFP + tf], Cf[(2 * NV + v) * NFP + tf]});
+          }
+          gref[d][v] = acc_value(acc);
+        }
+      }
+      S G[ND][NV];
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if (DIAG) {
+            G[j][v] = (Smt[j][j] * Jinv) * gref[j][v];
+          } else {
+            S acc = szero<S>();
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc = acc + Smt[d][j] * gref[d][v];
+            G[j][v] = acc * Jinv;
+          }
+        }
+      S fv[ND][NV];
+      flux_viscous<ND>(q, G, a.gamma, a.mu, a.kappa, fv);
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[j][v] = f[j][v] - fv[j][v];
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (DIAG) {
+          sF[(d * NV + v) * NSP + lt] = Smt[d][d] * f[d][v];
+        } else {
+          S acc = szero<S>();
+#pragma unroll
+          for (int j = 0; j < ND; ++j) acc = acc + Smt[d][j] * f[j][v];
+          sF[(d * NV + v) * NSP + lt] = acc;
+        }
+      }
+  }
+  __syncthreads();
+  if (!valid) return;
+  S div[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) div[v] = szero<S>();
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const int stride = d == 0 ? 1 : (d == 1 ? P : P * P);
+    const int lb = lt - idx[d] * stride;
+    const int tf = face_pt<ND, P>(d, idx);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const S* line = sF + (d * NV + v) * NSP + lb;
+      Acc<S> acc = acc_init(szero<S>());
+#pragma unroll
+      for (int k = 0; k < P; ++k) acc_madd(acc, B.Dh[idx[d]][k], line[k * stride]);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) acc_madd(acc, B.dg[s][idx[d]], S{T(0), C[(2 * d + s) * FO + v * NFP + tf]});
+      div[v] = div[v] + acc_value(acc);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const S r = (T(0) - div[v]) * Jinv;
+    const int64_t k = a.state_base + (i * NV + v) * NSP + lt;
+    if (a.out_neg64) a.out_neg64[k] = -(double)tangent(r);
+    else a.out[k] = tangent(r);
+  }
+}
+
+}  // namespace frgb

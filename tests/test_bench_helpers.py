@@ -36,6 +36,7 @@ def test_survey_roofline_charges_the_operator_bytes():
     assert r["operator"] == "residual" and r["bytes_per_launch"] == 2 * N * 8
     assert bench.survey_roofline("arnoldi_dot", 1, 1.0, N, 6800.0)["frac"] is None
     assert bench._operator_of("trace_f32") == ("jvp", 4) and bench._operator_of("trace_f64") == ("residual", 8)
+    assert bench._operator_of("fused_jvp_f32") == ("jvp", 4) and bench._operator_of("ctrace_f32") == ("jvp", 4)
 
 
 def test_double_float_instruction_count_matches_dfma():

@@ -1,0 +1,207 @@
+"""The fused exact JVP (compact traces + one face-and-volume kernel per element
+tile), used when every face of the mesh is interior and conforming.
+
+Checked against the three-pass JVP of the same library (FP64, the same
+arithmetic up to its order: 1e-13), against the oracle's JVP (FP64 1e-12, or
+1e-11 on curved elements; FP32 2e-5), for conservation of the linearised
+operator (both sides of a face receive exactly opposite fluxes), in GMRES
+(the prepared product replayed from a CUDA graph), and on meshes whose
+elements are rotated so that faces meet with non-trivial orientation codes.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import cases
+from helpers import generic_state, gpu_ctx, oracle_fr, parity_ok
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1910_03693_gb300 import build as B
+    B.build()
+    return True
+
+
+def rotate_elements(m, q, elems):
+    """Rotate the reference frame of the given elements by 90 degrees about the
+    zeta axis (new xi = old eta, new eta = -old xi), keeping the physical mesh and
+    state: node and solution-point order, faces, neighbour faces and orientation
+    codes are rewritten.  The elements must not be face neighbours of one
+    another, start with orientation code 0 on every face, and have geometry
+    order 1."""
+    assert m.geom_order == 1
+    nd, nv = m.nd, m.nd + 2
+    P = None
+    nodes = m.nodes.copy()
+    nbr, nbr_face, orient = m.nbr.copy(), m.nbr_face.copy(), m.orient.copy()
+    off = m.offsets()
+    q = np.asarray(q).copy()
+    old_of_new = {0: 2, 1: 3, 2: 1, 3: 0, 4: 4, 5: 5}    # new face -> old face
+    # face point order: new faces 0, 1 flip their first tangential axis; in 3D
+    # faces 4, 5 swap the tangential axes and flip the (new) first one
+    own_code = {0: 2, 1: 2, 2: 0, 3: 0, 4: 3, 5: 3}
+    nbr_code = {0: 2, 1: 2, 2: 0, 3: 0, 4: 5, 5: 5}     # the inverse mapping, seen from the neighbour
+    rot = set(int(e) for e in elems)
+    for e in rot:
+        assert np.all(m.orient[e] == 0)
+        for f in range(2 * nd):
+            assert int(m.nbr[e, f]) not in rot
+        P = int(m.p[e]) + 1
+        # nodes (2 per direction): new (i', j', k) = old (1 - j', i', k)
+        nn = 2
+        for a in range(nn ** nd):
+            i, j = a % nn, (a // nn) % nn
+            k = a // (nn * nn) if nd == 3 else 0
+            src = (1 - j) + nn * i + nn * nn * k
+            nodes[e, a] = m.nodes[e, src]
+        # solution points: new (i', j', k) = old (P-1-j', i', k)
+        blk = q[off[e]:off[e + 1]].reshape(-1, nv)
+        new = blk.copy()
+        for sp in range(P ** nd):
+            i, j = sp % P, (sp // P) % P
+            k = sp // (P * P) if nd == 3 else 0
+            new[sp] = blk[(P - 1 - j) + P * i + P * P * k]
+        q[off[e]:off[e + 1]] = new.reshape(-1)
+        for fn in range(2 * nd):
+            fo = old_of_new[fn]
+            n, g = int(m.nbr[e, fo]), int(m.nbr_face[e, fo])
+            nbr[e, fn], nbr_face[e, fn] = n, g
+            orient[e, fn] = own_code[fn] if nd == 3 else (2 if fn < 2 else 0)
+            nbr_face[n, g] = fn
+            orient[n, g] = nbr_code[fn] if nd == 3 else (2 if fn < 2 else 0)
+    out = cases.Mesh(nd, 1, nodes, nbr, nbr_face, orient, m.p.copy(), m.name + "_rot")
+    cases.check_connectivity(out)
+    return out, q
+
+
+def _sheared_box(p, n=3, mu=0.02):
+    m = cases.periodic_box(3, n, 0.0, 1.0, p)
+    m.nodes = m.nodes.copy()
+    m.nodes[..., 0] += 0.3 * m.nodes[..., 1] + 0.2 * m.nodes[..., 2]     # affine, not axis-aligned
+    return m, cases.random_state(m, 41), dict(gamma=1.4, mu=mu, Pr=0.71)
+
+
+def _curved_box(p):
+    m = cases.periodic_box(3, 3, 0.0, 1.0, p)
+    m.nodes = m.nodes + 0.02 * np.sin(5 * m.nodes[..., ::-1])
+    return m, cases.random_state(m, 42), dict(gamma=1.4, mu=0.01, Pr=0.71)
+
+
+def _workloads():
+    out = {}
+    m, q, ph = cases.workload_vortex2d(16, 2)
+    out["vortex2d_16_p2_euler"] = (m, q, ph)
+    out["vortex2d_16_p2_ns"] = (m, cases.random_state(m, 43), dict(ph, mu=0.02))
+    m, q, ph = cases.workload_tgv(5, 3)
+    out["tgv_5_p3"] = (m, q, ph)
+    m, q, ph = cases.workload_diff(3, 4)
+    out["diff_3_p4_mu0.05"] = (m, q, dict(ph, mu=0.05))
+    out["diff_3_p4_roe"] = (m, q, dict(ph, mu=0.05, flux="roe"))
+    out["sheared_box_p2"] = _sheared_box(2)
+    out["curved_box_p2"] = _curved_box(2)
+    out["box_p5_ns"] = _sheared_box(5, n=2)
+    out["box_p1_ns"] = _sheared_box(1, n=4)
+    mb, qb, ph = cases.workload_vortex_batch(5, 3, 9, 1, 5)
+    out["vortex_batch_5"] = (mb, qb, ph)
+    m, q, ph = cases.workload_vortex2d(6, 3)
+    rot = [e for e in range(m.n_elem) if ((e % 6) + (e // 6)) % 2 == 0]
+    mr, qr = rotate_elements(m, cases.random_state(m, 44), rot)
+    out["vortex2d_rotated_ns"] = (mr, qr, dict(ph, mu=0.02))
+    m, q, ph = _sheared_box(2, n=4)
+    rot = [e for e in range(m.n_elem) if ((e % 4) + (e // 4) % 4 + e // 16) % 2 == 0]
+    mr, qr = rotate_elements(m, q, rot)
+    out["sheared_box_rotated"] = (mr, qr, ph)
+    return out
+
+
+WL = _workloads()
+
+
+def _jvp(ctx, q, v, dtype, fused):
+    t = ctx.tuning()
+    t["fused_jvp"] = fused
+    ctx.set_tuning(t)
+    ctx.timing(True)
+    qs = ctx.pack(torch.from_numpy(q).cuda(), dtype)
+    vs = ctx.pack(torch.from_numpy(v).cuda(), dtype)
+    J = ctx.unpack(ctx.jvp(qs, vs)).cpu().numpy()
+    rep, _ = ctx.timing_report()
+    ctx.timing(False)
+    return J, rep
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_fused_jvp_parity(built, name):
+    from oracle import linearize as L
+    m, q, ph = WL[name]
+    q = generic_state(q)
+    v = cases.uniform(911, q.size) - 0.5
+    ctx = gpu_ctx(m, ph)
+    Jf, rep = _jvp(ctx, q, v, torch.float64, True)
+    assert rep.get("fused_jvp_f64", (0,))[0] > 0, rep.keys()          # the fused kernels ran
+    J3, rep3 = _jvp(ctx, q, v, torch.float64, False)
+    assert "fused_jvp_f64" not in rep3
+    assert np.abs(Jf - J3).max() <= 1e-13 * np.abs(J3).max()
+    Jref = L.jvp(oracle_fr(m, ph), torch.from_numpy(q), torch.from_numpy(v)).numpy()
+    tol = 1e-11 if name.startswith("curved") else 1e-12
+    ok, rel, fs = parity_ok(Jf, Jref, m, q, tol)
+    assert ok, (name, rel, fs)
+    J32, rep32 = _jvp(ctx, q, v, torch.float32, True)
+    assert rep32.get("fused_jvp_f32", (0,))[0] > 0
+    ok, rel, fs = parity_ok(J32, Jref, m, q, 2e-5)
+    assert ok, (name, "f32", rel, fs)
+
+
+@pytest.mark.parametrize("name", ["tgv_5_p3", "vortex2d_rotated_ns", "sheared_box_rotated", "diff_3_p4_roe"])
+def test_fused_jvp_conserves(built, name):
+    """On a periodic mesh sum_sp w|J| (J v)_var = 0 to round-off for every
+    variable: the two sides of every face receive exactly opposite fluxes."""
+    m, q, ph = WL[name]
+    q = generic_state(q)
+    v = cases.uniform(912, q.size) - 0.5
+    ctx = gpu_ctx(m, ph)
+    J, _ = _jvp(ctx, q, v, torch.float64, True)
+    W = oracle_fr(m, ph).quadrature_weights().numpy()
+    nv = m.nd + 2
+    tot = (W * J).reshape(-1, nv).sum(0)
+    scale = np.abs(W * J).reshape(-1, nv).sum(0)
+    assert np.all(np.abs(tot) <= 1e-13 * scale), (tot, scale)
+
+
+def test_mixed_degree_mesh_uses_three_passes(built):
+    """Mortar faces make the mesh ineligible: the three-pass kernels run."""
+    m, q, ph = cases.workload_vortex2d(8, 2)
+    m = m.with_p((1 + np.floor(cases.uniform(71, m.n_elem) * 3)).astype(np.int8))
+    m = m.with_p(cases.limit_jumps_down(m, m.p))
+    q = cases.random_state(m, 45)
+    ctx = gpu_ctx(m, ph)
+    _, rep = _jvp(ctx, q, cases.uniform(913, q.size) - 0.5, torch.float64, True)
+    assert "fused_jvp_f64" not in rep and rep.get("face_jvp_f64", (0,))[0] > 0
+
+
+@pytest.mark.parametrize("jv", [torch.float32, torch.float64])
+def test_fused_gmres_matches_three_pass(built, jv):
+    """GMRES with the prepared fused product (traces of q once, the product
+    replayed from a CUDA graph) against GMRES with the three-pass product."""
+    m, q, ph = WL["diff_3_p4_mu0.05"]
+    q = generic_state(q)
+    ctx = gpu_ctx(m, ph)
+    q64 = ctx.pack(torch.from_numpy(q).cuda())
+    b = ctx.pack(torch.from_numpy(cases.uniform(914, q.size) - 0.5).cuda())
+    out = {}
+    for fused in (True, False):
+        t = ctx.tuning()
+        t["fused_jvp"] = fused
+        ctx.set_tuning(t)
+        x, st = ctx.gmres(q64, b, sigma=50.0, mode="exact", jv_dtype=jv, m=30, rtol=1e-6, max_it=200)
+        assert st["converged"], st
+        out[fused] = (x.cpu().numpy(), st["iterations"])
+    assert abs(out[True][1] - out[False][1]) <= (0 if jv == torch.float64 else 2)
+    x0 = out[False][0]
+    tol = 1e-9 if jv == torch.float64 else 1e-4
+    assert np.abs(out[True][0] - x0).max() <= tol * np.abs(x0).max()
