@@ -69,7 +69,7 @@ def _grad_gpu(ctx, qg, W, nd, dtype):
     q = ctx.pack(torch.from_numpy(qg).cuda(), dtype).requires_grad_(True)
     phi = _phi_gpu(ctx, q, Wst, sel, nd)
     (g,) = torch.autograd.grad(phi, q)
-    return float(phi), ctx.unpack(g).cpu().numpy()
+    return float(phi.detach()), ctx.unpack(g).cpu().numpy()
 
 
 def test_functional_gradient_fp64_matches_oracle(diff):
@@ -100,12 +100,12 @@ def test_functional_gradient_fp32_matches_oracle(diff):
 
 def test_functional_directional_fd_sweep(diff):
     """<grad Phi, v> from the GPU's VJP against central differences of the GPU's
-    own Phi (FP64) for h = 1e-2 .. 1e-8.  The error is measured against
+    own Phi (FP64) for h = 1e-2 .. 1e-11.  The error is measured against
     ||grad Phi|| ||v||, the scale of the inner product's terms: for a random
     direction the inner product itself is ~sqrt(N) smaller, and the rounding
     of Phi would otherwise hide the curve.  Its minimum is below 1e-8 and both
-    ends of the sweep are at least 10 times above it (the V-curve: truncation
-    falling as h^2, rounding rising as 1/h)."""
+    arms rise at least 10 times above it (the V-curve: truncation falling as
+    h^2 from h = 1e-2, rounding rising as 1/h below h = 1e-9)."""
     m, qg, ph, ctx, W, _, _ = diff
     nd = m.nd
     sel = _state_selectors(ctx, nd)
@@ -117,11 +117,11 @@ def test_functional_directional_fd_sweep(diff):
     scale = float(g.norm() * v.norm())
     errs = {}
     with torch.no_grad():
-        for k in range(2, 9):
+        for k in range(2, 12):
             h = 10.0 ** -k
             fp = float(_phi_gpu(ctx, q.detach() + h * v, Wst, sel, nd))
             fm = float(_phi_gpu(ctx, q.detach() - h * v, Wst, sel, nd))
             errs[k] = abs((fp - fm) / (2 * h) - d_exact) / scale
     best = min(errs.values())
     assert best <= 1e-8, errs
-    assert errs[2] >= 10 * best and errs[8] >= 10 * best, errs
+    assert errs[2] >= 10 * best and max(errs[10], errs[11]) >= 10 * best, errs

@@ -157,7 +157,7 @@ def test_graph_arnoldi_matches_direct(built, works, name, jv_dtype):
             x, st = ctx.gmres(qs, b, sigma, mode="exact", jv_dtype=jv_dtype, rtol=1e-6, m=12, max_it=60)
             if timing:
                 rep, launches = ctx.timing_report()
-                n_vol = sum(v[0] for k, v in rep.items() if k.startswith("vol_jvp"))
+                n_vol = sum(v[0] for k, v in rep.items() if k.startswith(("vol_jvp", "fused_jvp")))
                 n_buckets = len(set(int(p) for p in ctx.p_map()))
                 per = 1 if (n_buckets == 1 or ctx.tuning()["multi_launch"]) else n_buckets
                 assert n_vol >= per * st["iterations"], (n_vol, st["iterations"], graphs)
