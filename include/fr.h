@@ -333,10 +333,12 @@ fr_status fr_dfloat_eval(int32_t op, const double* a, const double* b, const dou
  * sigma I - dR/dq(q).  fr_precond_build reads the blocks off the exact FP32
  * JVP at q64_dev (FP64 state layout) with unit vectors, probing the elements
  * of one colour of a distance-1 colouring of the face graph together, and
- * inverts each by Gauss-Jordan elimination with partial pivoting in FP32; it
- * synchronises `stream`.  Blocks of more than 144 DOFs (3D p >= 3) are not
- * stored: those elements are preconditioned by 1/sigma.  Storage: the sum of
- * the squared block sizes in floats.  FR_ERR_NONFINITE on a singular block.
+ * inverts each by Gauss-Jordan elimination with partial pivoting in FP32
+ * (blocks of up to 144 DOFs in shared memory; larger ones, 3D p >= 3 with 320,
+ * 625 or 1080 DOFs, by a blocked elimination on the block in global memory:
+ * panels of 32 pivots, then one rank-32 update of the other columns); it
+ * synchronises `stream`.  Storage: the sum of the squared block sizes in
+ * floats (32^3 elements at p = 3: 13.4 GB).  FR_ERR_NONFINITE on a singular block.
  * Rebucketing or retuning invalidates the blocks.  fr_precond_apply: z =
  * M^-1 w (FP64 state layout, z may alias w).  fr_precond_release frees the
  * block storage. */

@@ -10,8 +10,9 @@
 //    product per colour and local DOF index;
 //  * each block sigma I - J_ee is inverted in shared memory by Gauss-Jordan
 //    elimination with partial pivoting (FP32), and stored column-major.
-// Blocks larger than kPcMax DOFs (3D p >= 3) do not fit the elimination in
-// shared memory; those elements are preconditioned by 1/sigma.
+// Blocks of up to kPcSmem DOFs are inverted with [A | I] in shared memory;
+// larger ones (3D p >= 3: 320, 625 and 1080 DOFs) by a blocked in-place
+// Gauss-Jordan elimination on the block in global memory (below).
 // Apply: z_e = M_e^-1 (a w_e + b u_e), FP32 arithmetic on FP64 vectors.
 #include <algorithm>
 #include <cmath>
@@ -22,7 +23,10 @@
 
 namespace frgb {
 
-constexpr int kPcMax = 144;   // largest block inverted (2 x 144^2 floats in shared memory)
+constexpr int kPcSmem = 144;   // largest block inverted in shared memory (2 x 144^2 floats)
+constexpr int kPcMax = 1080;   // largest block stored: 3D p = 5 (5 x 216 DOFs)
+constexpr int kPanel = 32;     // columns eliminated together by the blocked inversion
+constexpr int kTile = 32;      // columns of one tile of the blocked update
 
 static inline int nsp_host(int nd, int p) { return nd == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1); }
 
@@ -137,6 +141,229 @@ __global__ void k_pc_invert(float* __restrict__ B, const int64_t* __restrict__ p
   }
 }
 
+// In-place inverse of one nb x nb block per CTA (column-major in global
+// memory) by Gauss-Jordan elimination with partial pivoting, blocked by
+// panels of kPanel columns: each panel is eliminated in shared memory (pivot
+// search over the rows not yet used, row swaps, scaling, elimination from
+// every other row), and its kPanel pivots then reach every other column at
+// once as the panel's row permutation followed by the rank-kPanel update
+// A[:, j] += (panel - I) A[K, j]; the row swaps are undone as column swaps at
+// the end.  The block moves through global memory (L2) once per panel, and the
+// nb^3 multiply-adds of the inversion are register-tiled in the update.  A
+// zero pivot sets *status and leaves the block unfinished.
+// Shared memory: the panel [nb][kPanel + 1], the panel's row order idx[nb],
+// the pivot rows perm[nb], the pivot column fcol[nb], the pivot row rk[kPanel],
+// the tile's panel rows X[kPanel][kTile + 1] and permuted rows [2 kPanel][kTile].
+__global__ void __launch_bounds__(512) k_pc_invert_blocked(float* __restrict__ B, const int64_t* __restrict__ pc_off,
+                                                           int slot_begin, int nb, int* __restrict__ status) {
+  extern __shared__ __align__(16) float sm[];
+  constexpr int LD = kPanel + 1;
+  float* Pn = sm;                                   // [nb][LD]
+  float* fcol = Pn + (size_t)nb * LD;               // [nb]
+  float* X = fcol + nb;                             // [kPanel][kTile + 1]
+  float* Y = X + kPanel * (kTile + 1);              // [2 kPanel][kTile]
+  float* rk = Y + 2 * kPanel * kTile;               // [kPanel]
+  int* idx = reinterpret_cast<int*>(rk + kPanel);   // [nb]
+  int* perm = idx + nb;                             // [nb]
+  __shared__ float pv[16];
+  __shared__ int pr[16];
+  __shared__ int piv;
+  const int s = slot_begin + blockIdx.x;
+  const int64_t off = pc_off[s];
+  if (off < 0) return;
+  float* A = B + off;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int kb = 0; kb < nb; kb += kPanel) {
+    const int nk = min(kPanel, nb - kb);
+    // panel in shared memory; its row order starts as the identity
+    for (int t = tid; t < nb * nk; t += nt) {
+      const int c = t / nb, r = t % nb;
+      Pn[r * LD + c] = A[(int64_t)(kb + c) * nb + r];
+    }
+    for (int r = tid; r < nb; r += nt) idx[r] = r;
+    __syncthreads();
+    for (int kl = 0; kl < nk; ++kl) {
+      const int k = kb + kl;
+      // pivot: the row r >= k with the largest |Pn[r][kl]| (lowest row at a tie)
+      float best = -1.0f;
+      int br = k;
+      for (int r = k + tid; r < nb; r += nt) {
+        const float a = fabsf(Pn[r * LD + kl]);
+        if (a > best) {
+          best = a;
+          br = r;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (ob > best || (ob == best && orr < br)) {
+          best = ob;
+          br = orr;
+        }
+      }
+      if (lane == 0) {
+        pv[warp] = best;
+        pr[warp] = br;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float b0 = pv[0];
+        int r0 = pr[0];
+        for (int q = 1; q < nw; ++q)
+          if (pv[q] > b0 || (pv[q] == b0 && pr[q] < r0)) {
+            b0 = pv[q];
+            r0 = pr[q];
+          }
+        piv = (b0 > 0.0f) ? r0 : -1;
+        if (piv < 0) atomicExch(status, 1);
+        else perm[k] = r0;
+      }
+      __syncthreads();
+      const int p = piv;
+      if (p < 0) return;   // singular block: reported through status
+      if (p != k) {
+        for (int c = tid; c < nk; c += nt) {
+          const float a = Pn[k * LD + c];
+          Pn[k * LD + c] = Pn[p * LD + c];
+          Pn[p * LD + c] = a;
+        }
+        if (tid == 0) {
+          const int t0 = idx[k];
+          idx[k] = idx[p];
+          idx[p] = t0;
+        }
+      }
+      __syncthreads();
+      const float inv = 1.0f / Pn[k * LD + kl];
+      for (int r = tid; r < nb; r += nt) fcol[r] = Pn[r * LD + kl];
+      for (int c = tid; c < nk; c += nt) rk[c] = c == kl ? inv : Pn[k * LD + c] * inv;
+      __syncthreads();
+      for (int t = tid; t < nb * nk; t += nt) {
+        const int r = t / nk, c = t % nk;
+        if (r == k) Pn[r * LD + c] = rk[c];
+        else if (c == kl) Pn[r * LD + c] = -fcol[r] * inv;
+        else Pn[r * LD + c] -= fcol[r] * rk[c];
+      }
+      __syncthreads();
+    }
+    // the eliminated panel back to global memory
+    for (int t = tid; t < nb * nk; t += nt) {
+      const int c = t / nb, r = t % nb;
+      A[(int64_t)(kb + c) * nb + r] = Pn[r * LD + c];
+    }
+    // every other column j: rows permuted as the panel's were, then
+    // A[:, j] += (Pn - I_K) A[K, j]
+    const int tx = tid % (kTile / 4), ty = tid / (kTile / 4), nty = nt / (kTile / 4);
+    for (int j0 = 0; j0 < nb; j0 += kTile) {
+      // columns j0 .. j0 + kTile - 1 that lie outside the panel
+      __syncthreads();
+      // (a) row permutation of the tile: the rows that can have moved are the
+      // panel rows and their pivot rows (all reads before any write)
+      for (int t = tid; t < 2 * nk * kTile; t += nt) {
+        const int ri = t / kTile, c = t % kTile, j = j0 + c;
+        const int r = ri < nk ? kb + ri : perm[kb + ri - nk];
+        if (j < nb && (j < kb || j >= kb + nk)) Y[ri * kTile + c] = A[(int64_t)j * nb + idx[r]];
+      }
+      __syncthreads();
+      for (int t = tid; t < 2 * nk * kTile; t += nt) {
+        const int ri = t / kTile, c = t % kTile, j = j0 + c;
+        const int r = ri < nk ? kb + ri : perm[kb + ri - nk];
+        if (j < nb && (j < kb || j >= kb + nk)) A[(int64_t)j * nb + r] = Y[ri * kTile + c];
+      }
+      __syncthreads();
+      // (b) the panel rows of the tile
+      for (int t = tid; t < nk * kTile; t += nt) {
+        const int k = t / kTile, c = t % kTile, j = j0 + c;
+        X[k * (kTile + 1) + c] = (j < nb && (j < kb || j >= kb + nk)) ? A[(int64_t)j * nb + kb + k] : 0.0f;
+      }
+      __syncthreads();
+      // (c) rank-nk update, four rows x four columns a thread per step
+      for (int r0 = ty; r0 < nb; r0 += 4 * nty) {
+        float acc[4][4];
+        int rows[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          rows[m] = r0 + m * nty;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[m][c] = 0.0f;
+        }
+        for (int k = 0; k < nk; ++k) {
+          float x[4], w[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) x[c] = X[k * (kTile + 1) + tx * 4 + c];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int r = rows[m];
+            w[m] = r < nb ? Pn[r * LD + k] - (r == kb + k ? 1.0f : 0.0f) : 0.0f;
+          }
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[m][c] = fmaf(w[m], x[c], acc[m][c]);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int r = rows[m];
+          if (r >= nb) continue;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int j = j0 + tx * 4 + c;
+            if (j < nb && (j < kb || j >= kb + nk)) A[(int64_t)j * nb + r] += acc[m][c];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // undo the row swaps as column swaps, last pivot first
+  for (int k = nb - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int r = tid; r < nb; r += nt) {
+        const float a = A[(int64_t)k * nb + r];
+        A[(int64_t)k * nb + r] = A[(int64_t)p * nb + r];
+        A[(int64_t)p * nb + r] = a;
+      }
+    __syncthreads();
+  }
+}
+
+static size_t pc_blocked_smem(int nb) {
+  return sizeof(float) * ((size_t)nb * (kPanel + 1) + nb + kPanel * (kTile + 1) + 2 * kPanel * kTile + kPanel) +
+         sizeof(int) * 2 * (size_t)nb;
+}
+
+// z_e = M_e^-1 (a w_e + b u_e) for blocks of more than 256 rows: one CTA per
+// element, the rows strided over its threads (coalesced column-major reads).
+__global__ void __launch_bounds__(256) k_pc_apply_big(const float* __restrict__ B, const int64_t* __restrict__ pc_off,
+                                                      const int64_t* __restrict__ state_off, int slot_begin, int nb,
+                                                      double a, const double* w, double b,
+                                                      const double* __restrict__ u, double* z, double inv_sigma) {
+  extern __shared__ __align__(16) float xs[];   // [nb]
+  const int s = slot_begin + blockIdx.x;
+  const int64_t base = state_off[s], off = pc_off[s];
+  double xv[kPcMax / 256 + 1];
+  int nr = 0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x, ++nr) {
+    xv[nr] = a * w[base + i] + (u ? b * u[base + i] : 0.0);
+    xs[i] = (float)xv[nr];
+  }
+  __syncthreads();
+  nr = 0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x, ++nr) {
+    if (off < 0) {
+      z[base + i] = xv[nr] * inv_sigma;
+      continue;
+    }
+    const float* Bc = B + off;
+    float acc = 0.0f;
+    for (int j = 0; j < nb; ++j) acc = fmaf(Bc[(int64_t)j * nb + i], xs[j], acc);
+    z[base + i] = (double)acc;
+  }
+}
+
 // z_e = M_e^-1 (a w_e + b u_e); epb elements per CTA, one thread per row.
 // Elements without a stored block (pc_off < 0): z_e = (a w_e + b u_e) / sigma.
 __global__ void k_pc_apply(const float* __restrict__ B, const int64_t* __restrict__ pc_off,
@@ -227,7 +454,7 @@ fr_status fr_precond_build(fr_ctx* c, const double* q64_dev, double sigma, void*
         total += (int64_t)nb * nb;
       }
     }
-    if (nb <= kPcMax) kmax = std::max(kmax, nb);
+    if (nb <= kPcMax && b.count > 0) kmax = std::max(kmax, nb);
   }
   if (!c->d_pc_off && cudaMalloc(&c->d_pc_off, sizeof(int64_t) * E) != cudaSuccess) return FR_ERR_NOMEM;
   if (!c->d_slot_color && cudaMalloc(&c->d_slot_color, sizeof(int32_t) * E) != cudaSuccess) return FR_ERR_NOMEM;
@@ -281,10 +508,18 @@ fr_status fr_precond_build(fr_ctx* c, const double* q64_dev, double sigma, void*
   for (const auto& b : c->buckets) {
     const int nb = nv * nsp_host(nd, b.p);
     if (nb > kPcMax || b.count == 0) continue;
-    const size_t smem = sizeof(float) * 2 * (size_t)nb * nb;
-    cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    FR_LAUNCH(c, "precond_build", s,
-              k_pc_invert<<<b.count, 256, smem, s>>>(c->d_pc, c->d_pc_off, b.slot_begin, nb, c->d_pc_status));
+    if (nb <= kPcSmem) {
+      const size_t smem = sizeof(float) * 2 * (size_t)nb * nb;
+      cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      FR_LAUNCH(c, "precond_build", s,
+                k_pc_invert<<<b.count, 256, smem, s>>>(c->d_pc, c->d_pc_off, b.slot_begin, nb, c->d_pc_status));
+    } else {
+      const size_t smem = pc_blocked_smem(nb);
+      cudaFuncSetAttribute(k_pc_invert_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      FR_LAUNCH(c, "precond_build", s,
+                k_pc_invert_blocked<<<b.count, 512, smem, s>>>(c->d_pc, c->d_pc_off, b.slot_begin, nb,
+                                                               c->d_pc_status));
+    }
   }
   int status = 0;
   cudaMemcpyAsync(&status, c->d_pc_status, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -329,10 +564,17 @@ fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const do
                                                                         a, w, b, u, z, 1.0 / c->pc_sigma));
       continue;
     }
-    const int epb = nb >= 256 ? 1 : 256 / nb;
+    const double bytes = (double)bk.count * nb * (24.0 + 4.0 * nb);
+    if (nb > 256) {
+      FR_LAUNCH_B(c, "precond_apply", s, bytes,
+                  k_pc_apply_big<<<bk.count, 256, sizeof(float) * nb, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
+                                                                           bk.slot_begin, nb, a, w, b, u, z,
+                                                                           1.0 / c->pc_sigma));
+      continue;
+    }
+    const int epb = 256 / nb;
     const int threads = epb * nb;
     const unsigned grid = (unsigned)((bk.count + epb - 1) / epb);
-    const double bytes = (double)bk.count * nb * (24.0 + 4.0 * nb);
     FR_LAUNCH_B(c, "precond_apply", s, bytes,
                 k_pc_apply<<<grid, threads, sizeof(float) * threads, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
                                                                           bk.slot_begin, bk.count, nb, epb, a, w, b,
