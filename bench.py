@@ -417,10 +417,34 @@ def mixed_degree_ops(peak_gbs):
     return out
 
 
-def stage_fd64(ctx, tab, qn, N, R1, opts, **over):
+def stage_fd64(ctx, tab, qn, N, R1, opts, tuning=None, precond_sigma=None, **over):
     """The same ESDIRK3 stage in another product mode, timed once after one
-    untimed solve: by default mode (A), FP64 finite-difference Jv."""
+    untimed solve: by default mode (A), FP64 finite-difference Jv.  ``tuning``
+    overrides launch choices for the run (restored after it);
+    ``precond_sigma``: element-Jacobi blocks built at q^n with that shift before
+    the stage (the build timed apart)."""
     import torch
+    saved = ctx.tuning()
+    if tuning:
+        t = dict(saved)
+        t["epb"] = list(saved["epb"])
+        for k, v in tuning.items():
+            if k == "epb":
+                for i, x in v.items():
+                    t["epb"][i] = x
+            else:
+                t[k] = v
+        ctx.set_tuning(t)
+    build_ms = None
+    if precond_sigma is not None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ctx.precond_build(qn[:N], precond_sigma)
+        e1.record()
+        torch.cuda.synchronize()
+        build_ms = round(e0.elapsed_time(e1), 3)
+        over = dict(over, precond=True)
     o = dict(opts, mode="fd", jv_dtype=torch.float64, low_above=0.0)
     o.update(over)
     qi = torch.empty(N, dtype=torch.float64, device="cuda")
@@ -435,10 +459,16 @@ def stage_fd64(ctx, tab, qn, N, R1, opts, **over):
         st = ctx.esdirk_stage(tab, 2, DT, qn[:N], [R1, R2, None, None], qi, **o)
         e1.record()
         torch.cuda.synchronize()
-    return {"ms": round(e0.elapsed_time(e1), 3), "newton": st["newton"], "gmres": st["gmres"],
-            "converged": st["converged"], "rel_final": st["norm_final"] / st["norm0"],
-            "norm_final": st["norm_final"], "F_evals_low": st["low_evaluations"],
-            "F_evals_f64": st["f64_evaluations"]}
+    out = {"ms": round(e0.elapsed_time(e1), 3), "newton": st["newton"], "gmres": st["gmres"],
+           "converged": st["converged"], "rel_final": st["norm_final"] / st["norm0"],
+           "norm_final": st["norm_final"], "F_evals_low": st["low_evaluations"],
+           "F_evals_f64": st["f64_evaluations"]}
+    if build_ms is not None:
+        out["precond_build_ms"] = build_ms
+        ctx.precond_release()
+    if tuning:
+        ctx.set_tuning(saved)
+    return out
 
 
 def run_timesteps(args):
@@ -646,6 +676,13 @@ def main():
     fd = stage_fd64(ctx, tab, qn, N, R1, opts)
     bf = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype="bf16op")
     f64F = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype=torch.float32, low_above=0.0)
+    same = dict(mode="exact", jv_dtype=torch.float32)
+    # the Arnoldi dots with FP64 FMAs instead of double-float; the fused JVP
+    # kernels forced; the element-Jacobi preconditioner (blocks at q^n with the
+    # shift 1/(w dt) + 1/dtau_max, 320-DOF blocks inverted on the device)
+    f64dots = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"df_arnoldi": False}, **same)
+    fusedst = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 1}}, **same)
+    pcst = stage_fd64(ctx, tab, qn, N, R1, opts, precond_sigma=1.0 / (tab[1][1] * DT) + 1.0 / DT, **same)
     roof["frac_alg"] = {k: ops[k]["hbm_frac"] for k in ("jvp_exact_f32", "residual_f32", "residual_df",
                                                          "residual_f64", "vjp_f32")}
     roof["frac_alg_note"] = ("survey bytes (residual 2 N s, JVP/VJP 3 N s) over the whole graph-replayed "
@@ -678,7 +715,9 @@ def main():
         "roe_flux_ops": roe,
         "stage_modes": {"exact_f32_jvp_ms": round(total_ms / args.steps, 3),
                         "exact_f32_jvp_final_abs": stats[-1]["norm_final"],
-                        "fd_f64": fd, "exact_bf16op_jvp": bf, "exact_f32_jvp_f64_F": f64F},
+                        "fd_f64": fd, "exact_bf16op_jvp": bf, "exact_f32_jvp_f64_F": f64F,
+                        "exact_f32_jvp_fp64_arnoldi_dots": f64dots, "exact_f32_fused_jvp": fusedst,
+                        "exact_f32_jvp_element_jacobi": pcst},
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clocks,

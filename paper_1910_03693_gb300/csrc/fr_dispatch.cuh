@@ -382,7 +382,15 @@ static void residual_out64_impl(fr_ctx* c, const T* q, double* R, cudaStream_t s
 // Fused JVP (every face interior and conforming): compact traces, then one
 // face-and-volume kernel per bucket
 // ---------------------------------------------------------------------------
-static inline bool fused_jvp_on(const fr_ctx* c) { return c->fused_ok && c->use_fused; }
+// The fused JVP runs when the mesh allows it, the flag enables it and the
+// tuning slot [precision][volume JVP][P = 1] chooses it (1 fused, 2 three
+// passes, 0 undecided = three passes): fr_autotune times both and keeps the
+// faster (measured on the Taylor-Green box, the fused kernel moves half the
+// bytes but is bound by instruction issue and is the slower of the two).
+template <typename T>
+static inline bool fused_jvp_on(const fr_ctx* c) {
+  return c->fused_ok && c->use_fused && c->epb_tab[prec_row<T>()][2][1] == 1;
+}
 
 template <typename T, int ND, int P, bool VISC>
 static void launch_ctrace_p(const CTraceArgs<T>& a, int epb, cudaStream_t s) {
@@ -484,7 +492,7 @@ template <typename T, int ND, bool VISC, bool DIAG = false>
 static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready = false,
                      double* neg64 = nullptr) {
   if constexpr (!is_dfloat<T>::value) {
-    if (fused_jvp_on(c)) {
+    if (fused_jvp_on<T>(c)) {
       jvp_fused_impl<T, ND, VISC, DIAG>(c, q, v, Jv, s, q_traces_ready, neg64);
       return;
     }
@@ -746,6 +754,20 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
   const float t_default = time_best(reps + 2, s, both);
   if (t_tuned <= t_default) std::memcpy(c->epb_tab[prec], tuned, sizeof(tuned));
   clear_work_cache(c);
+  // fused JVP against the three passes (meshes whose faces are all interior
+  // and conforming), with the launch configuration just kept
+  if constexpr (!is_dfloat<T>::value) {
+    if (c->fused_ok && c->use_fused) {
+      float t[2];
+      for (int m = 0; m < 2; ++m) {
+        c->epb_tab[prec][2][1] = m == 0 ? 1 : 2;
+        clear_graphs(c);
+        t[m] = time_best(reps + 2, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });
+      }
+      c->epb_tab[prec][2][1] = t[0] < t[1] ? 1 : 2;
+      clear_work_cache(c);
+    }
+  }
 }
 
 // One operation for one (dimension, viscosity, metric) configuration.
@@ -758,7 +780,7 @@ static void run_op_cfg(fr_ctx* c, int op, const void* q, const void* v, void* ou
   else if (op == 1) jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, oo, s);
   else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);
   else if (op == 3) {
-    if (fused_jvp_on(c)) launch_ctraces<T, ND, VISC>(c, qq, (T*)c->d_trace_q, s);
+    if (fused_jvp_on<T>(c)) launch_ctraces<T, ND, VISC>(c, qq, (T*)c->d_trace_q, s);
     else launch_traces<T, ND, VISC, DIAG>(c, qq, (T*)c->d_trace_q, s);
   }
   else if (op == 5) autotune_impl<T, ND, VISC, DIAG>(c, qq, oo, 3, s);

@@ -276,6 +276,129 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
   grid_sum<KC + 1>(o, with_norm ? k + 1 : k, partial, out, ticket);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float dot products of the Arnoldi process.  On GB300 the FP64 pipe
+// issues 2 FMAs a clock per SM while HBM delivers about 2.7 values a clock per
+// SM, so a dot product with one FP64 FMA per value cannot reach the memory
+// bound.  Here every FP64 value is split into two FP32 numbers by integer
+// operations on its bit pattern, and the products are accumulated as
+// double-float sums (error-free transformations on the FP32 pipe: the exact
+// product of the high parts through the FMA, the two cross terms, Knuth's
+// TwoSum and Dekker's Fast2Sum); each thread's sum is converted to FP64 once,
+// and the grid reduction stays FP64.
+// ---------------------------------------------------------------------------
+
+// x = hi + lo: hi holds x's leading 24 significant bits (truncated), lo the
+// FP32 rounding of the exact remainder (its 29 trailing bits), so that
+// |x - hi - lo| <= 2^-48 |x| for |x| >= 2^-83 (below, the remainder falls into
+// FP32's subnormal range: absolute error under 2^-149).  Built from the bit
+// pattern by integer operations, an int-to-float conversion and exact
+// power-of-two scalings: no FP64 instruction.  |x| < 2^-126 gives (0, 0);
+// |x| >= 2^128 gives the FP32 rounding of x.
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const int e = (int)((hw >> 20) & 0x7FF);
+  const unsigned sign = hw & 0x80000000u;
+  if (e < 897) {
+    hi = 0.0f;
+    lo = 0.0f;
+    return;
+  }
+  if (e > 1150) {
+    hi = __double2float_rn(x);
+    lo = 0.0f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  // remainder m29 2^(e - 1075), scaled in two exact steps that stay in range
+  // (2^(e - 1011) then 2^-64, or 2^(e - 1139) then 2^64)
+  const float m = __uint2float_rn(lw & 0x1FFFFFFFu);
+  float r;
+  if (e <= 1100) r = __fmul_rn(__fmul_rn(m, __uint_as_float((unsigned)(e - 1011 + 127) << 23)), __uint_as_float(63u << 23));
+  else r = __fmul_rn(__fmul_rn(m, __uint_as_float((unsigned)(e - 1139 + 127) << 23)), __uint_as_float(191u << 23));
+  lo = sign ? -r : r;
+}
+
+// (S, E) += a * b, a = (ah, al), b = (bh, bl): the exact product of the high
+// parts and the two cross terms (the product of the low parts, 2^-46 of ab,
+// is dropped), added with TwoSum and renormalised with Fast2Sum
+__device__ __forceinline__ void df_madd(float& S, float& E, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float pe = __fmaf_rn(ah, bh, -p);
+  pe = __fmaf_rn(ah, bl, pe);
+  pe = __fmaf_rn(al, bh, pe);
+  const float s = __fadd_rn(S, p);
+  const float bb = __fsub_rn(s, S);
+  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float u = __fadd_rn(t, __fadd_rn(E, pe));
+  S = __fadd_rn(s, u);
+  E = __fsub_rn(u, __fsub_rn(S, s));
+}
+
+// out[kk] = V[kk]^T w for kk < k (and ||w||^2 with with_norm), as k_multidot,
+// accumulated in double-float arithmetic.  w is FP64 (WT, NEG as k_multidot,
+// only double / false are instantiated).
+template <int KC, bool VEC, typename WT, bool NEG>
+__global__ void __launch_bounds__(kRedThreads) k_multidot_df(const double* __restrict__ V, int64_t ldv, int k,
+                                                              const WT* __restrict__ w, int64_t n,
+                                                              double* __restrict__ partial, double* __restrict__ out,
+                                                              unsigned* __restrict__ ticket, int with_norm) {
+  static_assert(sizeof(WT) == 8 && !NEG, "FP64 vectors only");
+  constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
+  using L = Slots<VEC>;
+  float S[KC + 1], E[KC + 1];
+#pragma unroll
+  for (int kk = 0; kk <= KC; ++kk) S[kk] = E[kk] = 0.0f;
+  const int64_t nw = n / L::W, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t last = nw + ((VEC && (n & 1)) ? 0 : -1);
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 <= last; q0 += U * stride) {
+    double wv[U][2];
+    float wh[U][2], wl[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      L::load(w, q0 + u * stride, nw, n, wv[u]);
+      split_df(wv[u][0], wh[u][0], wl[u][0]);
+      split_df(wv[u][1], wh[u][1], wl[u][1]);
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < KC; c0 += CH) {
+      if (c0 < k) {
+        double vv[U][CH][2];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (c0 + t < k) L::load_stream(V + (c0 + t) * ldv, q0 + u * stride, nw, n, vv[u][t]);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+          if (c0 + t < k) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                float vh, vl;
+                split_df(vv[u][t][h], vh, vl);
+                df_madd(S[c0 + t], E[c0 + t], vh, vl, wh[u][h], wl[u][h]);
+              }
+          }
+      }
+    }
+    if (with_norm) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) df_madd(S[KC], E[KC], wh[u][h], wl[u][h], wh[u][h], wl[u][h]);
+    }
+  }
+  double o[KC + 1];
+#pragma unroll
+  for (int kk = 0; kk <= KC; ++kk) o[kk] = (double)S[kk] + (double)E[kk];
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) o[kk] = kk < k ? o[kk] : o[KC];
+  grid_sum<KC + 1>(o, with_norm ? k + 1 : k, partial, out, ticket);
+}
+
 // w_out = w_in - sum_kk s_kk^2 raw[kk] V[kk] (the stored columns V[kk] scaled
 // by s_kk are the orthonormal basis, raw[kk] = V[kk]^T w_in); out[0] =
 // ||w_out||^2.  w_out may be w_in (in place, FP64).  With next_scale, the
@@ -681,9 +804,14 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   // (the update also stores the scale of the new column and the index of
   // the next product on the device: kk is the new column's index)
   auto gs_pass = [&](int kk, const double* w_in, double* w_out, double* raw, int with_norm) {
-    FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
-                FR_KC_DISPATCH(kk, vec, grid, k_multidot, double, false, V, ld, kk, w_in, n, part, raw, ticket,
-                               with_norm));
+    if (c->df_arnoldi)
+      FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
+                  FR_KC_DISPATCH(kk, vec, grid, k_multidot_df, double, false, V, ld, kk, w_in, n, part, raw, ticket,
+                                 with_norm));
+    else
+      FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
+                  FR_KC_DISPATCH(kk, vec, grid, k_multidot, double, false, V, ld, kk, w_in, n, part, raw, ticket,
+                                 with_norm));
     FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
                 FR_KC_DISPATCH(kk, vec, grid, k_orth_update, double, false, V, ld, kk, raw, sdev, w_in, w_out, n,
                                part, c->d_red + kOutN, ticket, sdev + kk, c->d_jidx, kk));

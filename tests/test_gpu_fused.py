@@ -122,10 +122,18 @@ def _workloads():
 WL = _workloads()
 
 
-def _jvp(ctx, q, v, dtype, fused):
+def _choose(ctx, fused):
+    """Force the fused kernels (or the three passes) in both precisions: the
+    flag and the tuning slot [precision][volume JVP][P = 1]."""
     t = ctx.tuning()
-    t["fused_jvp"] = fused
+    t["fused_jvp"] = True
+    for prec in (0, 1):
+        t["epb"][prec * 21 + 2 * 7 + 1] = 1 if fused else 2
     ctx.set_tuning(t)
+
+
+def _jvp(ctx, q, v, dtype, fused):
+    _choose(ctx, fused)
     ctx.timing(True)
     qs = ctx.pack(torch.from_numpy(q).cuda(), dtype)
     vs = ctx.pack(torch.from_numpy(v).cuda(), dtype)
@@ -195,9 +203,7 @@ def test_fused_gmres_matches_three_pass(built, jv):
     b = ctx.pack(torch.from_numpy(cases.uniform(914, q.size) - 0.5).cuda())
     out = {}
     for fused in (True, False):
-        t = ctx.tuning()
-        t["fused_jvp"] = fused
-        ctx.set_tuning(t)
+        _choose(ctx, fused)
         x, st = ctx.gmres(q64, b, sigma=50.0, mode="exact", jv_dtype=jv, m=30, rtol=1e-6, max_it=200)
         assert st["converged"], st
         out[fused] = (x.cpu().numpy(), st["iterations"])
@@ -205,3 +211,18 @@ def test_fused_gmres_matches_three_pass(built, jv):
     x0 = out[False][0]
     tol = 1e-9 if jv == torch.float64 else 1e-4
     assert np.abs(out[True][0] - x0).max() <= tol * np.abs(x0).max()
+
+
+def test_fused_choice_defaults_to_three_passes_and_autotune_decides(built):
+    """Undecided, the exact JVP runs the three passes; fr_autotune times both
+    kernels' products and records its choice in the tuning slot."""
+    m, q, ph = WL["tgv_5_p3"]
+    ctx = gpu_ctx(m, ph)
+    ctx.timing(True)
+    qs = ctx.pack(torch.from_numpy(q).cuda(), torch.float32)
+    ctx.jvp(qs, qs)
+    rep, _ = ctx.timing_report()
+    ctx.timing(False)
+    assert "fused_jvp_f32" not in rep and rep.get("vol_jvp_f32", (0,))[0] > 0
+    t = ctx.autotune(ctx.pack(torch.from_numpy(q).cuda()))
+    assert t["epb"][21 + 2 * 7 + 1] in (1, 2) and t["epb"][2 * 7 + 1] in (1, 2)

@@ -134,3 +134,27 @@ def test_esdirk3_stage_matches_oracle(built, mode, jv_dtype, low_above, low_prec
     assert np.abs(qg - qo.numpy()).max() <= 1e-6 * dq
     assert abs(st["newton"] - so["newton"]) <= 2
     assert torch.allclose(R2, ctx.residual(qi), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("jv", [torch.float64, torch.float32])
+def test_double_float_arnoldi_matches_fp64(built, jv):
+    """The Arnoldi dot products in double-float arithmetic (the default: FP64
+    values split into FP32 pairs, error-free products and sums on the FP32
+    pipe, about 1e-14 of |u| |w|) against FP64 FMAs: the same iteration count
+    and the same solution to 1e-9 (FP64 products) or 1e-5 (FP32 products)."""
+    m, q, ph = WL["diff_3^3_p4_mu0.05"]
+    ctx = gpu_ctx(m, ph)
+    qs = ctx.pack(torch.from_numpy(generic_state(q)).cuda())
+    b = ctx.pack(torch.from_numpy(cases.uniform(915, q.size) - 0.5).cuda())
+    out = {}
+    for df in (True, False):
+        t = ctx.tuning()
+        t["df_arnoldi"] = df
+        ctx.set_tuning(t)
+        x, st = ctx.gmres(qs, b, 40.0, mode="exact", jv_dtype=jv, m=30, rtol=1e-8, max_it=300)
+        assert st["converged"], (df, st)
+        out[df] = (x.cpu().numpy(), st["iterations"])
+    assert abs(out[True][1] - out[False][1]) <= 1, (out[True][1], out[False][1])
+    tol = 1e-9 if jv == torch.float64 else 1e-5
+    x0 = out[False][0]
+    assert np.abs(out[True][0] - x0).max() <= tol * np.abs(x0).max()
