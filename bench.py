@@ -677,11 +677,15 @@ def main():
     bf = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype="bf16op")
     f64F = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype=torch.float32, low_above=0.0)
     same = dict(mode="exact", jv_dtype=torch.float32)
-    # the Arnoldi dots with FP64 FMAs instead of double-float; the fused JVP
-    # kernels forced; the element-Jacobi preconditioner (blocks at q^n with the
-    # shift 1/(w dt) + 1/dtau_max, 320-DOF blocks inverted on the device)
-    f64dots = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"df_arnoldi": False}, **same)
+    # (FP64 F throughout, so that they compare with exact_f32_jvp_f64_F) the
+    # Arnoldi dots in double-float arithmetic; each of the three exact-JVP
+    # kernel choices forced (fused, trace-gradient and compact three passes);
+    # the element-Jacobi preconditioner (blocks at q^n with the shift
+    # 1/(w dt) + 1/dtau_max, 320-DOF blocks inverted on the device)
+    f64dots = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"df_arnoldi": True}, **same)
     fusedst = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 1}}, **same)
+    classic = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 2}}, **same)
+    compact = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 3}}, **same)
     pcst = stage_fd64(ctx, tab, qn, N, R1, opts, precond_sigma=1.0 / (tab[1][1] * DT) + 1.0 / DT, **same)
     roof["frac_alg"] = {k: ops[k]["hbm_frac"] for k in ("jvp_exact_f32", "residual_f32", "residual_df",
                                                          "residual_f64", "vjp_f32")}
@@ -702,7 +706,9 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "launch": {"epb_p3": {k: tuning["epb"][i * 7 + 4] for i, k in enumerate(
                        ("trace_f64", "vol_res_f64", "vol_jvp_f64", "trace_f32", "vol_res_f32", "vol_jvp_f32"))},
-                       "arnoldi_graph": tuning["graphs"]}},
+                       "arnoldi_graph": tuning["graphs"],
+                       "jvp_kernels_f32": {0: "compact three passes (undecided)", 1: "fused", 2: "trace-gradient three passes",
+                                           3: "compact three passes"}[tuning["epb"][21 + 2 * 7 + 1]]}},
         "stage": {"newton": [s["newton"] for s in stats], "gmres": [s["gmres"] for s in stats],
                   "F_evals_low": [s["low_evaluations"] for s in stats],
                   "F_evals_f64": [s["f64_evaluations"] for s in stats],
@@ -716,7 +722,8 @@ def main():
         "stage_modes": {"exact_f32_jvp_ms": round(total_ms / args.steps, 3),
                         "exact_f32_jvp_final_abs": stats[-1]["norm_final"],
                         "fd_f64": fd, "exact_bf16op_jvp": bf, "exact_f32_jvp_f64_F": f64F,
-                        "exact_f32_jvp_fp64_arnoldi_dots": f64dots, "exact_f32_fused_jvp": fusedst,
+                        "exact_f32_jvp_double_float_arnoldi_dots": f64dots, "exact_f32_fused_jvp": fusedst,
+                        "exact_f32_trace_gradient_jvp": classic, "exact_f32_compact_jvp": compact,
                         "exact_f32_jvp_element_jacobi": pcst},
         "kernels": kernels,
         "gpu_launches": launches,

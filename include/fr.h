@@ -388,9 +388,11 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
  * enables; slot [0][0][P = 1] holds the element weight
  * that orders the multi-bucket work table (0 n_sp (p+1), 1 n_sp, 2 n_sp^2,
  * 3 n_sp^3: the paper's candidate weights, Sec. 3.2); slot [prec][2][P = 1]
- * chooses the exact JVP's kernels where FR_TUNE_FUSED_JVP allows the fused
- * ones (0 undecided: three passes, 1 fused, 2 three passes; fr_autotune
- * times both); and the flags below.  fr_tuning_set with table NULL changes only the
+ * chooses the exact JVP's kernels where FR_TUNE_FUSED_JVP allows the
+ * compact-trace ones (every face interior and conforming): 1 the fused
+ * face-and-volume kernel, 2 the trace-gradient three passes, 3 (and 0,
+ * undecided) the compact three passes; fr_autotune times the three; and the
+ * flags below.  fr_tuning_set with table NULL changes only the
  * flags; elements per CTA outside [0, 256], choices outside [0, 2], weight
  * models outside [0, 3] or unknown flag bits give FR_ERR_INVALID. */
 #define FR_TUNE_MULTI_LAUNCH 1  /* one persistent launch over all degree buckets */
@@ -399,13 +401,15 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
                                    kernels that skip the zero metric terms   */
 #define FR_TUNE_FUSED_JVP 8     /* meshes whose faces are all interior and
                                    conforming (same degree both sides, no
-                                   boundary): the exact JVP as compact traces
-                                   plus one face-and-volume kernel per element
-                                   tile, no face-output array in memory      */
+                                   boundary): the exact JVP from compact
+                                   traces (q and its normal derivative), as
+                                   three passes or as one face-and-volume
+                                   kernel per element tile (tuning slot)     */
 #define FR_TUNE_DF_ARNOLDI 16   /* GMRES: the Arnoldi dot products accumulated
                                    in double-float arithmetic on the FP32 pipe
                                    (FP64 vectors and grid reduction; about
-                                   1e-14 of |u| |w| from the FP64 dots)      */
+                                   1e-14 of |u| |w| from the FP64 dots); off
+                                   by default: measured no faster           */
 fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
 fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
 fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);

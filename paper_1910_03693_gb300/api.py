@@ -220,7 +220,7 @@ class FRContext:
         tab = (C.c_int32 * 42)(*[int(x) for x in t["epb"]]) if "epb" in t else None
         flags = ((1 if t.get("multi_launch", True) else 0) | (2 if t.get("graphs", True) else 0) |
                  (4 if t.get("diag_metrics", True) else 0) | (8 if t.get("fused_jvp", True) else 0) |
-                 (16 if t.get("df_arnoldi", True) else 0))
+                 (16 if t.get("df_arnoldi", False) else 0))
         _check(lib().fr_tuning_set(self.h, tab, flags), "fr_tuning_set")
 
     # ---------------------------------------------------------- instrumentation

@@ -391,6 +391,13 @@ template <typename T>
 static inline bool fused_jvp_on(const fr_ctx* c) {
   return c->fused_ok && c->use_fused && c->epb_tab[prec_row<T>()][2][1] == 1;
 }
+// The compact three-pass JVP (compact traces, the compact face kernel, the
+// volume kernel) on the same meshes: slot value 3, and the undecided default.
+template <typename T>
+static inline bool compact_jvp_on(const fr_ctx* c) {
+  const int ch = c->epb_tab[prec_row<T>()][2][1];
+  return c->fused_ok && c->use_fused && (ch == 3 || ch == 0);
+}
 
 template <typename T, int ND, int P, bool VISC>
 static void launch_ctrace_p(const CTraceArgs<T>& a, int epb, cudaStream_t s) {
@@ -486,6 +493,57 @@ static void jvp_fused_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_
   }
 }
 
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+static void launch_cface_p(const CFaceArgs<T>& a, cudaStream_t s) {
+  constexpr int NFP = ND == 2 ? P : P * P;
+  constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;
+  cface_kernel<T, ND, P, VISC, DIAG><<<nblocks(a.n, FB), FB * NFP, 0, s>>>(a);
+}
+
+template <typename T, int ND, bool VISC, bool DIAG>
+static void jvp_compact_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready,
+                             double* neg64) {
+  constexpr int NV = ND + 2, CT = VISC ? 2 * NV : NV;
+  T* trq = (T*)c->d_trace_q;
+  T* trv = (T*)c->d_trace_v;
+  if (!q_traces_ready) launch_ctraces<T, ND, VISC>(c, q, trq, s);
+  launch_ctraces<T, ND, VISC>(c, v, trv, s);
+  for (const auto& g : c->fgroups) {
+    const Bucket* bk = nullptr;
+    for (const auto& b : c->buckets)
+      if (b.p == g.pm) bk = &b;
+    if (!bk) continue;
+    CFaceArgs<T> a;
+    a.recs = g.d_recs;
+    a.trq = trq;
+    a.trv = trv;
+    a.fout = (T*)c->d_fout;
+    a.elem_slot = c->d_elem_slot;
+    a.basis = basis_ptr<T>(c);
+    a.geo = geo_view<T>(c, g.pm);
+    a.gamma = (T)c->phys.gamma;
+    a.mu = (T)c->phys.mu;
+    a.kappa = (T)c->phys.kappa;
+    a.flux = c->phys.flux;
+    a.n = g.n;
+    a.slot_begin = bk->slot_begin;
+    a.ctrace_base = bk->ctrace_base;
+    const int P = g.pm + 1, NFP = ipow(P, ND - 1);
+    // both sides' compact traces of q and v in; both sides' face outputs out
+    const double nb = (double)g.n * NFP * (4.0 * CT + 2.0 * (VISC ? 3 : 1) * NV) * sizeof(T);
+    FR_LAUNCH_B(c, kname<T>("cface_jvp_f64", "cface_jvp_f32", "cface_jvp_df"), s, nb, {
+      switch (P) {
+        case 2: launch_cface_p<T, ND, 2, VISC, DIAG>(a, s); break;
+        case 3: launch_cface_p<T, ND, 3, VISC, DIAG>(a, s); break;
+        case 4: launch_cface_p<T, ND, 4, VISC, DIAG>(a, s); break;
+        case 5: launch_cface_p<T, ND, 5, VISC, DIAG>(a, s); break;
+        case 6: launch_cface_p<T, ND, 6, VISC, DIAG>(a, s); break;
+      }
+    });
+  }
+  launch_vols<T, ND, VISC, 1, DIAG>(c, q, v, Jv, s, neg64);
+}
+
 // JVP; with q_traces_ready the traces of q in d_trace_q are reused (q is
 // fixed during one GMRES solve)
 template <typename T, int ND, bool VISC, bool DIAG = false>
@@ -494,6 +552,10 @@ static void jvp_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, b
   if constexpr (!is_dfloat<T>::value) {
     if (fused_jvp_on<T>(c)) {
       jvp_fused_impl<T, ND, VISC, DIAG>(c, q, v, Jv, s, q_traces_ready, neg64);
+      return;
+    }
+    if (compact_jvp_on<T>(c)) {
+      jvp_compact_impl<T, ND, VISC, DIAG>(c, q, v, Jv, s, q_traces_ready, neg64);
       return;
     }
   }
@@ -758,13 +820,18 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
   // and conforming), with the launch configuration just kept
   if constexpr (!is_dfloat<T>::value) {
     if (c->fused_ok && c->use_fused) {
-      float t[2];
-      for (int m = 0; m < 2; ++m) {
-        c->epb_tab[prec][2][1] = m == 0 ? 1 : 2;
+      float best = 1e30f;
+      int choice = 2;
+      for (int m = 1; m <= 3; ++m) {   // 1 fused, 2 trace-gradient three passes, 3 compact three passes
+        c->epb_tab[prec][2][1] = m;
         clear_graphs(c);
-        t[m] = time_best(reps + 2, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });
+        const float t = time_best(reps + 2, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });
+        if (t < best) {
+          best = t;
+          choice = m;
+        }
       }
-      c->epb_tab[prec][2][1] = t[0] < t[1] ? 1 : 2;
+      c->epb_tab[prec][2][1] = choice;
       clear_work_cache(c);
     }
   }
@@ -780,7 +847,7 @@ static void run_op_cfg(fr_ctx* c, int op, const void* q, const void* v, void* ou
   else if (op == 1) jvp_impl<T, ND, VISC, DIAG>(c, qq, vv, oo, s);
   else if (op == 2) vjp_impl<T, ND, VISC>(c, qq, vv, oo, s);
   else if (op == 3) {
-    if (fused_jvp_on<T>(c)) launch_ctraces<T, ND, VISC>(c, qq, (T*)c->d_trace_q, s);
+    if (fused_jvp_on<T>(c) || compact_jvp_on<T>(c)) launch_ctraces<T, ND, VISC>(c, qq, (T*)c->d_trace_q, s);
     else launch_traces<T, ND, VISC, DIAG>(c, qq, (T*)c->d_trace_q, s);
   }
   else if (op == 5) autotune_impl<T, ND, VISC, DIAG>(c, qq, oo, 3, s);

@@ -237,7 +237,7 @@ struct fr_ctx {
   bool graph_timers_live[2] = {false, false};   // a replay's timers are not yet accumulated
   bool use_graphs = true;
   bool use_diag = true;
-  bool df_arnoldi = true;     // Arnoldi dot products in double-float arithmetic (FP32 pipe)
+  bool df_arnoldi = false;    // Arnoldi dot products in double-float arithmetic (FP32 pipe)
   cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
   bool jvp_graph_ok = true;
   int* d_jidx = nullptr;

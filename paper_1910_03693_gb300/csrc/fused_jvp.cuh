@@ -481,3 +481,160 @@ __global__ void __launch_bounds__(256, 2) fused_jvp_kernel(FusedArgs<T> a, int e
 }
 
 }  // namespace frgb
+
+namespace frgb {
+
+// ---------------------------------------------------------------------------
+// Compact three-pass JVP (meshes whose faces are all interior and conforming):
+// compact traces, then this face kernel, then the ordinary volume kernel.  A
+// CTA takes FB faces of one group; both sides' compact traces of q and of v
+// (4 blocks of CT x NFP values a face) are staged in shared memory, each
+// thread forms both sides' physical gradients at its face point from them
+// (face_grad: the stored normal derivative, the tangential ones differentiate
+// the face trace) and evaluates the common flux, the BR2 gradient and the
+// lifting once per face, writing the face outputs of both sides as the
+// trace-gradient face kernel does.  Against that kernel the traces move 2 NV
+// instead of NV (1 + ND) values a face point.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CFaceArgs {
+  const FaceRec* recs;
+  const T* trq;             // compact traces of q and v
+  const T* trv;
+  T* fout;
+  const int32_t* elem_slot; // slot of each element
+  const BasisTab<T>* basis;
+  GeoView<T> geo;
+  T gamma, mu, kappa;
+  int flux;
+  int n;                    // faces in the group
+  int slot_begin;           // the group's bucket
+  int64_t ctrace_base;
+};
+
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+__global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
+  using S = Dual<T>;
+  constexpr int NV = ND + 2, NF = 2 * ND;
+  constexpr int NFP = ND == 2 ? P : P * P;
+  constexpr int CT = CompactWidth<VISC, NV>::value;
+  constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;    // faces a CTA
+  constexpr int BLK = CT * NFP;
+  __shared__ T sh[FB][4][BLK];                        // master q, master v, slave q, slave v
+  __shared__ int64_t soff[FB][2];
+  const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
+  const int64_t fidx = (int64_t)blockIdx.x * FB + lf;
+  const bool valid = lf < FB && fidx < a.n;
+  FaceRec r{};
+  if (valid) {
+    r = a.recs[fidx];
+    if (t == 0) {
+      soff[lf][0] = a.ctrace_base + ((int64_t)(a.elem_slot[r.me] - a.slot_begin) * NF + r.mf) * BLK;
+      soff[lf][1] = a.ctrace_base + ((int64_t)(a.elem_slot[r.se] - a.slot_begin) * NF + r.sf) * BLK;
+    }
+  }
+  __syncthreads();
+  // stage the four blocks of every face of the CTA (all threads, coalesced)
+  const int64_t nf_here = min((int64_t)FB, (int64_t)a.n - (int64_t)blockIdx.x * FB);
+  for (int k = threadIdx.x; k < nf_here * 4 * BLK; k += blockDim.x) {
+    const int f = k / (4 * BLK), rem = k % (4 * BLK), w = rem / BLK, o = rem % BLK;
+    const T* src = (w & 1) ? a.trv : a.trq;
+    sh[f][w][o] = src[soff[f][w >> 1] + o];
+  }
+  __syncthreads();
+  if (!valid) return;
+  const BasisTab<T>& B = a.basis[P];
+  const int dm = r.mf >> 1, sm = r.mf & 1, ds = r.sf >> 1, ss = r.sf & 1;
+  const int u = orient_map(r.orient, t, P, ND);
+  const T* XqM = sh[lf][0];
+  const T* XvM = sh[lf][1];
+  const T* XqS = sh[lf][2];
+  const T* XvS = sh[lf][3];
+  S qM[NV], qS[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    qM[v] = S{XqM[v * NFP + t], XvM[v * NFP + t]};
+    qS[v] = S{XqS[v * NFP + u], XvS[v * NFP + u]};
+  }
+  const T sgm = sm ? T(1) : T(-1);
+  const T absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + dm, t);
+  const T inv_absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + ND + dm, t);
+  T A[ND], n[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    A[j] = sgm * geo_face(a.geo, r.me, r.mf, dm * ND + j, t);
+    n[j] = A[j] * inv_absA;
+  }
+  S Fn[NV];
+  common_flux<ND>(a.flux, qM, qS, n, absA, a.gamma, Fn);
+  S qc[NV];
+  if (VISC) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qS[v]);
+    T cM[ND], cS[ND];
+    const T gJM = B.dgf[sm] * geo_face(a.geo, r.me, r.mf, ND * ND + 1, t);
+    const T gJS = B.dgf[ss] * geo_face(a.geo, r.se, r.sf, ND * ND + 1, u);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      cM[j] = gJM * geo_face(a.geo, r.me, r.mf, dm * ND + j, t);
+      cS[j] = gJS * geo_face(a.geo, r.se, r.sf, ds * ND + j, u);
+    }
+    S GM[ND][NV], GS[ND][NV], Gc[ND][NV];
+    face_grad<T, ND, P, DIAG>(XqM, XvM, r.mf, t, a.geo, r.me, B, GM);
+    face_grad<T, ND, P, DIAG>(XqS, XvS, r.sf, u, a.geo, r.se, B, GS);
+    if (DIAG) {
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Gc[j][v] = T(0.5) * (GM[j][v] + GS[j][v]);
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        if (j != dm) continue;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          Gc[j][v] = Gc[j][v] + T(0.5) * (cM[j] * (qc[v] - qM[v]) + cS[j] * (qc[v] - qS[v]));
+      }
+      S fr[NV];
+      flux_viscous_row<ND>(qc, Gc, a.gamma, a.mu, a.kappa, dm, fr);
+      T Ad = T(0);
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+        if (j == dm) Ad = A[j];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fn[v] = Fn[v] - fr[v] * Ad;
+    } else {
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          Gc[j][v] = T(0.5) * (GM[j][v] + cM[j] * (qc[v] - qM[v]) + GS[j][v] + cS[j] * (qc[v] - qS[v]));
+      S fv[ND][NV];
+      flux_viscous<ND>(qc, Gc, a.gamma, a.mu, a.kappa, fv);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        S acc = szero<S>();
+#pragma unroll
+        for (int j = 0; j < ND; ++j) acc = acc + fv[j][v] * A[j];
+        Fn[v] = Fn[v] - acc;
+      }
+    }
+  }
+  // face outputs of both sides (transformed common flux tangent; primal and tangent dq)
+  T* om = a.fout + r.mo;
+  T* os = a.fout + r.so;
+  const T sgs = ss ? T(1) : T(-1);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    om[v * NFP + t] = tangent(sgm * Fn[v]);
+    os[v * NFP + u] = tangent(sgs * (T(0) - Fn[v]));
+    if (VISC) {
+      const S dM = qc[v] - qM[v], dS = qc[v] - qS[v];
+      om[(NV + v) * NFP + t] = value(dM);
+      om[(2 * NV + v) * NFP + t] = tangent(dM);
+      os[(NV + v) * NFP + u] = value(dS);
+      os[(2 * NV + v) * NFP + u] = tangent(dS);
+    }
+  }
+}
+
+}  // namespace frgb

@@ -122,18 +122,23 @@ def _workloads():
 WL = _workloads()
 
 
-def _choose(ctx, fused):
-    """Force the fused kernels (or the three passes) in both precisions: the
-    flag and the tuning slot [precision][volume JVP][P = 1]."""
+MODES = {"fused": 1, "classic": 2, "compact": 3}
+KERNEL = {"fused": "fused_jvp", "classic": "face_jvp", "compact": "cface_jvp"}
+
+
+def _choose(ctx, mode):
+    """Force the exact JVP's kernels in both precisions: the fused
+    face-and-volume kernel, the trace-gradient three passes or the compact
+    three passes (the flag and the tuning slot [precision][volume JVP][P = 1])."""
     t = ctx.tuning()
     t["fused_jvp"] = True
     for prec in (0, 1):
-        t["epb"][prec * 21 + 2 * 7 + 1] = 1 if fused else 2
+        t["epb"][prec * 21 + 2 * 7 + 1] = MODES[mode]
     ctx.set_tuning(t)
 
 
-def _jvp(ctx, q, v, dtype, fused):
-    _choose(ctx, fused)
+def _jvp(ctx, q, v, dtype, mode):
+    _choose(ctx, mode)
     ctx.timing(True)
     qs = ctx.pack(torch.from_numpy(q).cuda(), dtype)
     vs = ctx.pack(torch.from_numpy(v).cuda(), dtype)
@@ -145,35 +150,40 @@ def _jvp(ctx, q, v, dtype, fused):
 
 @pytest.mark.parametrize("name", list(WL))
 def test_fused_jvp_parity(built, name):
+    """The fused and the compact three-pass JVPs against the trace-gradient
+    three passes (FP64, 1e-13) and the oracle (FP64 1e-12 / 1e-11 curved;
+    FP32 2e-5), with the kernels of each choice checked to have run."""
     from oracle import linearize as L
     m, q, ph = WL[name]
     q = generic_state(q)
     v = cases.uniform(911, q.size) - 0.5
     ctx = gpu_ctx(m, ph)
-    Jf, rep = _jvp(ctx, q, v, torch.float64, True)
-    assert rep.get("fused_jvp_f64", (0,))[0] > 0, rep.keys()          # the fused kernels ran
-    J3, rep3 = _jvp(ctx, q, v, torch.float64, False)
-    assert "fused_jvp_f64" not in rep3
-    assert np.abs(Jf - J3).max() <= 1e-13 * np.abs(J3).max()
+    J3, rep3 = _jvp(ctx, q, v, torch.float64, "classic")
+    assert "fused_jvp_f64" not in rep3 and "cface_jvp_f64" not in rep3
     Jref = L.jvp(oracle_fr(m, ph), torch.from_numpy(q), torch.from_numpy(v)).numpy()
     tol = 1e-11 if name.startswith("curved") else 1e-12
-    ok, rel, fs = parity_ok(Jf, Jref, m, q, tol)
-    assert ok, (name, rel, fs)
-    J32, rep32 = _jvp(ctx, q, v, torch.float32, True)
-    assert rep32.get("fused_jvp_f32", (0,))[0] > 0
-    ok, rel, fs = parity_ok(J32, Jref, m, q, 2e-5)
-    assert ok, (name, "f32", rel, fs)
+    for mode in ("fused", "compact"):
+        J, rep = _jvp(ctx, q, v, torch.float64, mode)
+        assert rep.get(KERNEL[mode] + "_f64", (0,))[0] > 0, (mode, rep.keys())
+        assert np.abs(J - J3).max() <= 1e-13 * np.abs(J3).max(), mode
+        ok, rel, fs = parity_ok(J, Jref, m, q, tol)
+        assert ok, (name, mode, rel, fs)
+        J32, rep32 = _jvp(ctx, q, v, torch.float32, mode)
+        assert rep32.get(KERNEL[mode] + "_f32", (0,))[0] > 0
+        ok, rel, fs = parity_ok(J32, Jref, m, q, 2e-5)
+        assert ok, (name, mode, "f32", rel, fs)
 
 
+@pytest.mark.parametrize("mode", ["fused", "compact"])
 @pytest.mark.parametrize("name", ["tgv_5_p3", "vortex2d_rotated_ns", "sheared_box_rotated", "diff_3_p4_roe"])
-def test_fused_jvp_conserves(built, name):
+def test_fused_jvp_conserves(built, name, mode):
     """On a periodic mesh sum_sp w|J| (J v)_var = 0 to round-off for every
     variable: the two sides of every face receive exactly opposite fluxes."""
     m, q, ph = WL[name]
     q = generic_state(q)
     v = cases.uniform(912, q.size) - 0.5
     ctx = gpu_ctx(m, ph)
-    J, _ = _jvp(ctx, q, v, torch.float64, True)
+    J, _ = _jvp(ctx, q, v, torch.float64, mode)
     W = oracle_fr(m, ph).quadrature_weights().numpy()
     nv = m.nd + 2
     tot = (W * J).reshape(-1, nv).sum(0)
@@ -188,34 +198,38 @@ def test_mixed_degree_mesh_uses_three_passes(built):
     m = m.with_p(cases.limit_jumps_down(m, m.p))
     q = cases.random_state(m, 45)
     ctx = gpu_ctx(m, ph)
-    _, rep = _jvp(ctx, q, cases.uniform(913, q.size) - 0.5, torch.float64, True)
-    assert "fused_jvp_f64" not in rep and rep.get("face_jvp_f64", (0,))[0] > 0
+    for mode in ("fused", "compact"):
+        _, rep = _jvp(ctx, q, cases.uniform(913, q.size) - 0.5, torch.float64, mode)
+        assert "fused_jvp_f64" not in rep and "cface_jvp_f64" not in rep
+        assert rep.get("face_jvp_f64", (0,))[0] > 0
 
 
 @pytest.mark.parametrize("jv", [torch.float32, torch.float64])
 def test_fused_gmres_matches_three_pass(built, jv):
-    """GMRES with the prepared fused product (traces of q once, the product
-    replayed from a CUDA graph) against GMRES with the three-pass product."""
+    """GMRES with the prepared fused and compact products (compact traces of q
+    once, the product replayed from a CUDA graph) against GMRES with the
+    trace-gradient three passes."""
     m, q, ph = WL["diff_3_p4_mu0.05"]
     q = generic_state(q)
     ctx = gpu_ctx(m, ph)
     q64 = ctx.pack(torch.from_numpy(q).cuda())
     b = ctx.pack(torch.from_numpy(cases.uniform(914, q.size) - 0.5).cuda())
     out = {}
-    for fused in (True, False):
-        _choose(ctx, fused)
+    for mode in ("classic", "fused", "compact"):
+        _choose(ctx, mode)
         x, st = ctx.gmres(q64, b, sigma=50.0, mode="exact", jv_dtype=jv, m=30, rtol=1e-6, max_it=200)
-        assert st["converged"], st
-        out[fused] = (x.cpu().numpy(), st["iterations"])
-    assert abs(out[True][1] - out[False][1]) <= (0 if jv == torch.float64 else 2)
-    x0 = out[False][0]
+        assert st["converged"], (mode, st)
+        out[mode] = (x.cpu().numpy(), st["iterations"])
+    x0 = out["classic"][0]
     tol = 1e-9 if jv == torch.float64 else 1e-4
-    assert np.abs(out[True][0] - x0).max() <= tol * np.abs(x0).max()
+    for mode in ("fused", "compact"):
+        assert abs(out[mode][1] - out["classic"][1]) <= (0 if jv == torch.float64 else 2), mode
+        assert np.abs(out[mode][0] - x0).max() <= tol * np.abs(x0).max(), mode
 
 
-def test_fused_choice_defaults_to_three_passes_and_autotune_decides(built):
-    """Undecided, the exact JVP runs the three passes; fr_autotune times both
-    kernels' products and records its choice in the tuning slot."""
+def test_default_choice_and_autotune(built):
+    """Undecided, the exact JVP on an eligible mesh runs the compact three
+    passes; fr_autotune times the three choices and records one in the slot."""
     m, q, ph = WL["tgv_5_p3"]
     ctx = gpu_ctx(m, ph)
     ctx.timing(True)
@@ -223,6 +237,6 @@ def test_fused_choice_defaults_to_three_passes_and_autotune_decides(built):
     ctx.jvp(qs, qs)
     rep, _ = ctx.timing_report()
     ctx.timing(False)
-    assert "fused_jvp_f32" not in rep and rep.get("vol_jvp_f32", (0,))[0] > 0
+    assert rep.get("cface_jvp_f32", (0,))[0] > 0 and rep.get("vol_jvp_f32", (0,))[0] > 0
     t = ctx.autotune(ctx.pack(torch.from_numpy(q).cuda()))
-    assert t["epb"][21 + 2 * 7 + 1] in (1, 2) and t["epb"][2 * 7 + 1] in (1, 2)
+    assert t["epb"][21 + 2 * 7 + 1] in (1, 2, 3) and t["epb"][2 * 7 + 1] in (1, 2, 3)

@@ -138,9 +138,9 @@ def test_esdirk3_stage_matches_oracle(built, mode, jv_dtype, low_above, low_prec
 
 @pytest.mark.parametrize("jv", [torch.float64, torch.float32])
 def test_double_float_arnoldi_matches_fp64(built, jv):
-    """The Arnoldi dot products in double-float arithmetic (the default: FP64
-    values split into FP32 pairs, error-free products and sums on the FP32
-    pipe, about 1e-14 of |u| |w|) against FP64 FMAs: the same iteration count
+    """The Arnoldi dot products in double-float arithmetic (FP64 values split
+    into FP32 pairs, error-free products and sums on the FP32 pipe, about
+    1e-14 of |u| |w|) against FP64 FMAs (the default): the same iteration count
     and the same solution to 1e-9 (FP64 products) or 1e-5 (FP32 products)."""
     m, q, ph = WL["diff_3^3_p4_mu0.05"]
     ctx = gpu_ctx(m, ph)
