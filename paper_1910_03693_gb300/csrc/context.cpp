@@ -233,6 +233,10 @@ static fr_status build_fused_table(fr_ctx* c, const std::vector<int32_t>& elem_s
     bucket_of_p[b.p] = (int)k;
   }
   c->fused_ok = c->bgroups.empty() && cb <= c->trace_cap;
+  // the compact face kernel finds a block at the trace-gradient offset scaled
+  // by ct / nvt: true when every bucket's compact base is its trace base so scaled
+  for (const auto& b : c->buckets)
+    if (b.trace_base % c->nvt != 0 || b.trace_base / c->nvt * ct != b.ctrace_base) c->fused_ok = false;
   for (const auto& g : c->fgroups)
     if (g.pm != g.ps) c->fused_ok = false;
   if (!c->fused_ok) return FR_OK;

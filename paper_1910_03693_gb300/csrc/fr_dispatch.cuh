@@ -509,16 +509,11 @@ static void jvp_compact_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStrea
   if (!q_traces_ready) launch_ctraces<T, ND, VISC>(c, q, trq, s);
   launch_ctraces<T, ND, VISC>(c, v, trv, s);
   for (const auto& g : c->fgroups) {
-    const Bucket* bk = nullptr;
-    for (const auto& b : c->buckets)
-      if (b.p == g.pm) bk = &b;
-    if (!bk) continue;
     CFaceArgs<T> a;
     a.recs = g.d_recs;
     a.trq = trq;
     a.trv = trv;
     a.fout = (T*)c->d_fout;
-    a.elem_slot = c->d_elem_slot;
     a.basis = basis_ptr<T>(c);
     a.geo = geo_view<T>(c, g.pm);
     a.gamma = (T)c->phys.gamma;
@@ -526,8 +521,7 @@ static void jvp_compact_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStrea
     a.kappa = (T)c->phys.kappa;
     a.flux = c->phys.flux;
     a.n = g.n;
-    a.slot_begin = bk->slot_begin;
-    a.ctrace_base = bk->ctrace_base;
+    a.nvt = c->nvt;
     const int P = g.pm + 1, NFP = ipow(P, ND - 1);
     // both sides' compact traces of q and v in; both sides' face outputs out
     const double nb = (double)g.n * NFP * (4.0 * CT + 2.0 * (VISC ? 3 : 1) * NV) * sizeof(T);

@@ -117,20 +117,23 @@ __global__ void __launch_bounds__(256) ctrace_kernel(CTraceArgs<T> a, int epb) {
 // the face trace along its own axes (P terms each), and the face metric terms
 // map reference to physical derivatives.
 template <typename T, int ND, int P, bool DIAG>
-__device__ __forceinline__ void face_grad(const T* Xq, const T* Xv, int fc, int t, const GeoView<T>& geo, int64_t e,
-                                          const BasisTab<T>& B, Dual<T> (*G)[ND + 2]) {
+__device__ __forceinline__ void face_metric(const GeoView<T>& geo, int64_t e, int fc, int t, T (&Sf)[ND][ND], T& Jinv) {
+#pragma unroll
+  for (int dd = 0; dd < ND; ++dd)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) Sf[dd][j] = (DIAG && dd != j) ? T(0) : geo_face(geo, e, fc, dd * ND + j, t);
+  Jinv = geo_face(geo, e, fc, ND * ND + 1, t);
+}
+
+template <typename T, int ND, int P, bool DIAG>
+__device__ __forceinline__ void face_grad_m(const T* Xq, const T* Xv, int fc, int t, const T (&Sf)[ND][ND], T Jinv,
+                                            const BasisTab<T>& B, Dual<T> (*G)[ND + 2]) {
   constexpr int NV = ND + 2;
   constexpr int NFP = ND == 2 ? P : P * P;
   const int dc = fc >> 1;
   const int ia = t % P, ib = ND == 3 ? t / P : 0;
   const int ta = dc == 0 ? 1 : 0;
   const int tb = dc == 2 ? 1 : 2;
-  T Sf[ND][ND];
-#pragma unroll
-  for (int dd = 0; dd < ND; ++dd)
-#pragma unroll
-    for (int j = 0; j < ND; ++j) Sf[dd][j] = (DIAG && dd != j) ? T(0) : geo_face(geo, e, fc, dd * ND + j, t);
-  const T Jinv = geo_face(geo, e, fc, ND * ND + 1, t);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     Dual<T> dq[ND];
@@ -166,6 +169,15 @@ __device__ __forceinline__ void face_grad(const T* Xq, const T* Xv, int fc, int 
       G[j][v] = g * Jinv;
     }
   }
+}
+
+// The same with the metric terms read here.
+template <typename T, int ND, int P, bool DIAG>
+__device__ __forceinline__ void face_grad(const T* Xq, const T* Xv, int fc, int t, const GeoView<T>& geo, int64_t e,
+                                          const BasisTab<T>& B, Dual<T> (*G)[ND + 2]) {
+  T Sf[ND][ND], Jinv;
+  face_metric<T, ND, P, DIAG>(geo, e, fc, t, Sf, Jinv);
+  face_grad_m<T, ND, P, DIAG>(Xq, Xv, fc, t, Sf, Jinv, B, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,14 +514,12 @@ struct CFaceArgs {
   const T* trq;             // compact traces of q and v
   const T* trv;
   T* fout;
-  const int32_t* elem_slot; // slot of each element
   const BasisTab<T>* basis;
   GeoView<T> geo;
   T gamma, mu, kappa;
   int flux;
   int n;                    // faces in the group
-  int slot_begin;           // the group's bucket
-  int64_t ctrace_base;
+  int nvt;                  // components of the trace-gradient layout (its offsets scale to compact ones)
 };
 
 template <typename T, int ND, int P, bool VISC, bool DIAG>
@@ -521,31 +531,48 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
   constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;    // faces a CTA
   constexpr int BLK = CT * NFP;
   __shared__ T sh[FB][4][BLK];                        // master q, master v, slave q, slave v
-  __shared__ int64_t soff[FB][2];
   const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
   const int64_t fidx = (int64_t)blockIdx.x * FB + lf;
   const bool valid = lf < FB && fidx < a.n;
   FaceRec r{};
+  const BasisTab<T>& B = a.basis[P];
+  int dm = 0, sm = 0, ds = 0, ss = 0, u = 0;
+  T absA = T(0), inv_absA = T(0), SfM[ND][ND], SfS[ND][ND], JiM = T(0), JiS = T(0);
+  T rowM[ND], rowS[ND];   // area-vector rows S[dm][:] (master, at t) and S[ds][:] (slave, at u)
   if (valid) {
     r = a.recs[fidx];
-    if (t == 0) {
-      soff[lf][0] = a.ctrace_base + ((int64_t)(a.elem_slot[r.me] - a.slot_begin) * NF + r.mf) * BLK;
-      soff[lf][1] = a.ctrace_base + ((int64_t)(a.elem_slot[r.se] - a.slot_begin) * NF + r.sf) * BLK;
+    // compact trace blocks of the two sides: on a conforming mesh the compact
+    // offset is the trace-gradient one scaled by CT / nvt
+    const int64_t om = r.mt / a.nvt * CT, osl = r.st / a.nvt * CT;
+    T buf[4][CT];
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+      buf[0][c] = a.trq[om + c * NFP + t];
+      buf[1][c] = a.trv[om + c * NFP + t];
+      buf[2][c] = a.trq[osl + c * NFP + t];
+      buf[3][c] = a.trv[osl + c * NFP + t];
     }
-  }
-  __syncthreads();
-  // stage the four blocks of every face of the CTA (all threads, coalesced)
-  const int64_t nf_here = min((int64_t)FB, (int64_t)a.n - (int64_t)blockIdx.x * FB);
-  for (int k = threadIdx.x; k < nf_here * 4 * BLK; k += blockDim.x) {
-    const int f = k / (4 * BLK), rem = k % (4 * BLK), w = rem / BLK, o = rem % BLK;
-    const T* src = (w & 1) ? a.trv : a.trq;
-    sh[f][w][o] = src[soff[f][w >> 1] + o];
+    dm = r.mf >> 1;
+    sm = r.mf & 1;
+    ds = r.sf >> 1;
+    ss = r.sf & 1;
+    u = orient_map(r.orient, t, P, ND);
+    absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + dm, t);
+    inv_absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + ND + dm, t);
+    face_metric<T, ND, P, DIAG>(a.geo, r.me, r.mf, t, SfM, JiM);
+    face_metric<T, ND, P, DIAG>(a.geo, r.se, r.sf, u, SfS, JiS);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      rowM[j] = geo_face(a.geo, r.me, r.mf, dm * ND + j, t);
+      rowS[j] = geo_face(a.geo, r.se, r.sf, ds * ND + j, u);
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int c = 0; c < CT; ++c) sh[lf][w][c * NFP + t] = buf[w][c];
   }
   __syncthreads();
   if (!valid) return;
-  const BasisTab<T>& B = a.basis[P];
-  const int dm = r.mf >> 1, sm = r.mf & 1, ds = r.sf >> 1, ss = r.sf & 1;
-  const int u = orient_map(r.orient, t, P, ND);
   const T* XqM = sh[lf][0];
   const T* XvM = sh[lf][1];
   const T* XqS = sh[lf][2];
@@ -557,12 +584,10 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
     qS[v] = S{XqS[v * NFP + u], XvS[v * NFP + u]};
   }
   const T sgm = sm ? T(1) : T(-1);
-  const T absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + dm, t);
-  const T inv_absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + ND + dm, t);
   T A[ND], n[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    A[j] = sgm * geo_face(a.geo, r.me, r.mf, dm * ND + j, t);
+    A[j] = sgm * rowM[j];
     n[j] = A[j] * inv_absA;
   }
   S Fn[NV];
@@ -572,16 +597,16 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qS[v]);
     T cM[ND], cS[ND];
-    const T gJM = B.dgf[sm] * geo_face(a.geo, r.me, r.mf, ND * ND + 1, t);
-    const T gJS = B.dgf[ss] * geo_face(a.geo, r.se, r.sf, ND * ND + 1, u);
+    const T gJM = B.dgf[sm] * JiM;
+    const T gJS = B.dgf[ss] * JiS;
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
-      cM[j] = gJM * geo_face(a.geo, r.me, r.mf, dm * ND + j, t);
-      cS[j] = gJS * geo_face(a.geo, r.se, r.sf, ds * ND + j, u);
+      cM[j] = gJM * rowM[j];
+      cS[j] = gJS * rowS[j];
     }
     S GM[ND][NV], GS[ND][NV], Gc[ND][NV];
-    face_grad<T, ND, P, DIAG>(XqM, XvM, r.mf, t, a.geo, r.me, B, GM);
-    face_grad<T, ND, P, DIAG>(XqS, XvS, r.sf, u, a.geo, r.se, B, GS);
+    face_grad_m<T, ND, P, DIAG>(XqM, XvM, r.mf, t, SfM, JiM, B, GM);
+    face_grad_m<T, ND, P, DIAG>(XqS, XvS, r.sf, u, SfS, JiS, B, GS);
     if (DIAG) {
 #pragma unroll
       for (int j = 0; j < ND; ++j)
