@@ -131,16 +131,25 @@ def _operator_of(kernel):
     return None
 
 
-def survey_roofline(kernel, launches, ms, n_dof, hbm_gbs):
+def survey_roofline(kernel, launches, ms, n_dof, hbm_gbs, nbytes=None):
     """The dominant kernel against the HBM roofline with the survey's
-    algorithmic bytes: the bytes of one evaluation of the operator it belongs
-    to (SURVEY_VECTORS x N x s) charged to each of its launches, over its mean
-    launch time."""
+    algorithmic bytes: for a kernel of the residual or the JVP, the bytes of
+    one evaluation of its operator (SURVEY_VECTORS x N x s) charged to each of
+    its launches; for the Arnoldi and vector kernels, whose algorithmic bytes
+    the survey counts vector by vector (8 bytes a value read or written),
+    the bytes their launches count (``nbytes``, over all launches); over the
+    mean launch time."""
     t = ms / 1e3 / max(launches, 1)
     ops = _operator_of(kernel)
     if ops is None:
-        return {"bound": "hbm", "achieved": None, "peak": hbm_gbs, "unit": "GB/s", "frac": None,
-                "bytes_per_launch": None}
+        if not nbytes:
+            return {"bound": "hbm", "achieved": None, "peak": hbm_gbs, "unit": "GB/s", "frac": None,
+                    "bytes_per_launch": None}
+        b = nbytes / max(launches, 1)
+        ach = b / t / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
+                "bytes_per_launch": b, "operator": "arnoldi/vector",
+                "bytes": "8 bytes a vector value read or written (the survey's Arnoldi count)"}
     op, s = ops
     b = SURVEY_VECTORS[op] * n_dof * s
     ach = b / t / 1e9
@@ -626,7 +635,7 @@ def main():
     peak, peak_kind = _peaks()
     kern = max(report, key=lambda k: report[k][1])
     cnt, ms, nbytes, nflops = report[kern]
-    roof = survey_roofline(kern, cnt, ms, N, peak)
+    roof = survey_roofline(kern, cnt, ms, N, peak, nbytes)
     io = kernel_roofline(kern, cnt, ms, nbytes, nflops, peak, alu)
     roof.update({"kernel": kern, "traffic": _traffic_for(kern), "hbm_peak_source": peak_kind,
                  "share_of_step": ms / total_ms, "per_launch_ms": ms / cnt,

@@ -35,6 +35,8 @@ def test_survey_roofline_charges_the_operator_bytes():
     r = bench.survey_roofline("vol_res_df", 1, 1.0, N, 6800.0)
     assert r["operator"] == "residual" and r["bytes_per_launch"] == 2 * N * 8
     assert bench.survey_roofline("arnoldi_dot", 1, 1.0, N, 6800.0)["frac"] is None
+    r = bench.survey_roofline("arnoldi_update", 2, 1.0, N, 6800.0, nbytes=2 * 8 * 3 * N)   # 0.5 ms a launch
+    assert r["bytes_per_launch"] == 8 * 3 * N and r["achieved"] == pytest.approx(8 * 3 * N / 0.5e-3 / 1e9)
     assert bench._operator_of("trace_f32") == ("jvp", 4) and bench._operator_of("trace_f64") == ("residual", 8)
     assert bench._operator_of("fused_jvp_f32") == ("jvp", 4) and bench._operator_of("ctrace_f32") == ("jvp", 4)
 
