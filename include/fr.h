@@ -410,6 +410,10 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
                                    (FP64 vectors and grid reduction; about
                                    1e-14 of |u| |w| from the FP64 dots); off
                                    by default: measured no faster           */
+#define FR_TUNE_ARNOLDI_RUNS 32 /* GMRES: the Arnoldi dots and updates read each
+                                   column in runs of 4 x 512 contiguous bytes a
+                                   warp (the default; off: one 512-byte segment
+                                   a warp, the segments one grid apart)      */
 fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
 fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
 fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);

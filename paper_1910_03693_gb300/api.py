@@ -207,20 +207,20 @@ class FRContext:
 
     def tuning(self):
         """{"epb": 42 ints [prec][kernel][P], "multi_launch": bool, "graphs": bool, "diag_metrics": bool,
-        "fused_jvp": bool, "df_arnoldi": bool}"""
+        "fused_jvp": bool, "df_arnoldi": bool, "arnoldi_runs": bool}"""
         tab = (C.c_int32 * 42)()
         fl = C.c_int32(0)
         _check(lib().fr_tuning_get(self.h, tab, C.byref(fl)), "fr_tuning_get")
         return {"epb": [int(x) for x in tab], "multi_launch": bool(fl.value & 1), "graphs": bool(fl.value & 2),
                 "diag_metrics": bool(fl.value & 4), "fused_jvp": bool(fl.value & 8),
-                "df_arnoldi": bool(fl.value & 16)}
+                "df_arnoldi": bool(fl.value & 16), "arnoldi_runs": bool(fl.value & 32)}
 
     def set_tuning(self, t):
         """Set what `tuning()` returns; a missing "epb" keeps the table, missing switches default to on."""
         tab = (C.c_int32 * 42)(*[int(x) for x in t["epb"]]) if "epb" in t else None
         flags = ((1 if t.get("multi_launch", True) else 0) | (2 if t.get("graphs", True) else 0) |
                  (4 if t.get("diag_metrics", True) else 0) | (8 if t.get("fused_jvp", True) else 0) |
-                 (16 if t.get("df_arnoldi", False) else 0))
+                 (16 if t.get("df_arnoldi", False) else 0) | (32 if t.get("arnoldi_runs", True) else 0))
         _check(lib().fr_tuning_set(self.h, tab, flags), "fr_tuning_set")
 
     # ---------------------------------------------------------- instrumentation

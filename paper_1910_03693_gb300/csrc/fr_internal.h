@@ -238,6 +238,7 @@ struct fr_ctx {
   bool use_graphs = true;
   bool use_diag = true;
   bool df_arnoldi = false;    // Arnoldi dot products in double-float arithmetic (FP32 pipe)
+  int arnoldi_map = 1;        // slot walk of the Arnoldi reductions (0 grid-strided, 1 warp runs)
   cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
   bool jvp_graph_ok = true;
   int* d_jidx = nullptr;

@@ -180,13 +180,14 @@ fr_status fr_tuning_get(const fr_ctx* c, int32_t* table, int32_t* flags) {
   if (flags)
     *flags = (c->multi_launch ? FR_TUNE_MULTI_LAUNCH : 0) | (c->use_graphs ? FR_TUNE_GRAPHS : 0) |
              (c->use_diag ? FR_TUNE_DIAG_METRICS : 0) | (c->use_fused ? FR_TUNE_FUSED_JVP : 0) |
-             (c->df_arnoldi ? FR_TUNE_DF_ARNOLDI : 0);
+             (c->df_arnoldi ? FR_TUNE_DF_ARNOLDI : 0) | (c->arnoldi_map == 1 ? FR_TUNE_ARNOLDI_RUNS : 0);
   return FR_OK;
 }
 
 fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   if (!c) return FR_ERR_INVALID;
-  if (flags & ~(FR_TUNE_MULTI_LAUNCH | FR_TUNE_GRAPHS | FR_TUNE_DIAG_METRICS | FR_TUNE_FUSED_JVP | FR_TUNE_DF_ARNOLDI)) {
+  if (flags & ~(FR_TUNE_MULTI_LAUNCH | FR_TUNE_GRAPHS | FR_TUNE_DIAG_METRICS | FR_TUNE_FUSED_JVP | FR_TUNE_DF_ARNOLDI |
+                FR_TUNE_ARNOLDI_RUNS)) {
     set_error("fr_tuning_set: unknown flag bits");
     return FR_ERR_INVALID;
   }
@@ -204,6 +205,7 @@ fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   c->use_diag = (flags & FR_TUNE_DIAG_METRICS) != 0;
   c->use_fused = (flags & FR_TUNE_FUSED_JVP) != 0;
   c->df_arnoldi = (flags & FR_TUNE_DF_ARNOLDI) != 0;
+  c->arnoldi_map = (flags & FR_TUNE_ARNOLDI_RUNS) != 0 ? 1 : 0;
   c->diag = c->diag_mesh && c->use_diag;
   clear_work_cache(c);
   return FR_OK;

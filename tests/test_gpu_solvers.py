@@ -158,3 +158,25 @@ def test_double_float_arnoldi_matches_fp64(built, jv):
     tol = 1e-9 if jv == torch.float64 else 1e-5
     x0 = out[False][0]
     assert np.abs(out[True][0] - x0).max() <= tol * np.abs(x0).max()
+
+
+def test_arnoldi_slot_walks_agree(built):
+    """The Arnoldi dots and updates with each warp reading runs of 4 x 512 bytes
+    of every column (the default) and with single 512-byte segments one grid
+    apart: the same iteration count and the same solution to 1e-12 (only the
+    order of the partial sums differs)."""
+    m, q, ph = WL["tgv_5^3_p3"]
+    ctx = gpu_ctx(m, ph)
+    qs = ctx.pack(torch.from_numpy(generic_state(q)).cuda())
+    b = ctx.pack(torch.from_numpy(cases.uniform(916, q.size) - 0.5).cuda())
+    out = {}
+    for runs in (True, False):
+        t = ctx.tuning()
+        t["arnoldi_runs"] = runs
+        ctx.set_tuning(t)
+        x, st = ctx.gmres(qs, b, 60.0, mode="exact", jv_dtype=torch.float64, m=20, rtol=1e-10, max_it=200,
+                          reorth=1)
+        assert st["converged"], (runs, st)
+        out[runs] = (x.cpu().numpy(), st["iterations"])
+    assert out[True][1] == out[False][1]
+    assert np.abs(out[True][0] - out[False][0]).max() <= 1e-12 * np.abs(out[False][0]).max()
