@@ -414,6 +414,11 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
                                    column in runs of 4 x 512 contiguous bytes a
                                    warp (the default; off: one 512-byte segment
                                    a warp, the segments one grid apart)      */
+#define FR_TUNE_TMA_FACES 64    /* the compact face kernel's shared-memory tiles
+                                   filled by bulk asynchronous copies (TMA),
+                                   double-buffered in a persistent walk, where
+                                   every block is a multiple of 16 bytes (the
+                                   default; off: loads by the threads)       */
 fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
 fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
 fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);
@@ -431,6 +436,12 @@ fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);
  * fr_timing call into *launches (optional). */
 fr_status fr_timing(fr_ctx* ctx, int32_t enable);
 fr_status fr_timing_report(fr_ctx* ctx, char* buf, int64_t len, int64_t* launches);
+
+/* Device status word of the context (no counterpart in the paper): kernels
+ * whose waits are bounded set bit 0 when a wait gives up (the compact face
+ * kernel's wait for its bulk copies) and return instead of hanging.
+ * Synchronises the device; *status receives the word, cleared when `clear`. */
+fr_status fr_device_status(fr_ctx* ctx, int32_t* status, int32_t clear);
 
 /* Arithmetic peak of the current device, measured (measurement support, no
  * counterpart in the paper): a kernel of independent FMA chains (16 per

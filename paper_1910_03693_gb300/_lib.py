@@ -116,6 +116,7 @@ SIGNATURES = {
     "fr_filter": [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p],
     "fr_dfloat_eval": [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
     "fr_fma_rate": [C.c_int, C.c_int64, C.POINTER(C.c_double), C.c_void_p],
+    "fr_device_status": [C.c_void_p, C.POINTER(C.c_int32), C.c_int32],
 }
 
 

@@ -207,23 +207,31 @@ class FRContext:
 
     def tuning(self):
         """{"epb": 42 ints [prec][kernel][P], "multi_launch": bool, "graphs": bool, "diag_metrics": bool,
-        "fused_jvp": bool, "df_arnoldi": bool, "arnoldi_runs": bool}"""
+        "fused_jvp": bool, "df_arnoldi": bool, "arnoldi_runs": bool, "tma_faces": bool}"""
         tab = (C.c_int32 * 42)()
         fl = C.c_int32(0)
         _check(lib().fr_tuning_get(self.h, tab, C.byref(fl)), "fr_tuning_get")
         return {"epb": [int(x) for x in tab], "multi_launch": bool(fl.value & 1), "graphs": bool(fl.value & 2),
                 "diag_metrics": bool(fl.value & 4), "fused_jvp": bool(fl.value & 8),
-                "df_arnoldi": bool(fl.value & 16), "arnoldi_runs": bool(fl.value & 32)}
+                "df_arnoldi": bool(fl.value & 16), "arnoldi_runs": bool(fl.value & 32),
+                "tma_faces": bool(fl.value & 64)}
 
     def set_tuning(self, t):
         """Set what `tuning()` returns; a missing "epb" keeps the table, missing switches default to on."""
         tab = (C.c_int32 * 42)(*[int(x) for x in t["epb"]]) if "epb" in t else None
         flags = ((1 if t.get("multi_launch", True) else 0) | (2 if t.get("graphs", True) else 0) |
                  (4 if t.get("diag_metrics", True) else 0) | (8 if t.get("fused_jvp", True) else 0) |
-                 (16 if t.get("df_arnoldi", False) else 0) | (32 if t.get("arnoldi_runs", True) else 0))
+                 (16 if t.get("df_arnoldi", False) else 0) | (32 if t.get("arnoldi_runs", True) else 0) |
+                 (64 if t.get("tma_faces", True) else 0))
         _check(lib().fr_tuning_set(self.h, tab, flags), "fr_tuning_set")
 
     # ---------------------------------------------------------- instrumentation
+    def device_status(self, clear=True):
+        """The context's device status word (bit 0: a bounded wait gave up)."""
+        v = C.c_int32(0)
+        _check(lib().fr_device_status(self.h, C.byref(v), 1 if clear else 0), "fr_device_status")
+        return int(v.value)
+
     def timing(self, enable=True):
         _check(lib().fr_timing(self.h, 1 if enable else 0), "fr_timing")
 

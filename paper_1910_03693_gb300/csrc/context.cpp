@@ -607,6 +607,8 @@ static fr_status create_impl(const fr_mesh_desc* m, const fr_physics* ph, const 
   FR_CUDA(cudaMalloc(&c->d_state_off, sizeof(int64_t) * E));
   FR_CUDA(cudaMalloc(&c->d_slot_p, E));
   FR_CUDA(cudaMalloc(&c->d_nbr, sizeof(int32_t) * E * nf));
+  FR_CUDA(cudaMalloc(&c->d_status, sizeof(int)));
+  FR_CUDA(cudaMemset(c->d_status, 0, sizeof(int)));
   FR_CUDA(cudaMemcpy(c->d_nbr, c->nbr.data(), sizeof(int32_t) * E * nf, cudaMemcpyHostToDevice));
   return build_layout(c);
 }
@@ -650,6 +652,7 @@ static void destroy_impl(fr_ctx* c) {
   c->d_work = nullptr;
   c->n_work = 0;
   cudaFree(c->d_fnbr);
+  cudaFree(c->d_status);
   cudaFree(c->d_jidx);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_jidx) cudaFreeHost(c->h_jidx);

@@ -494,9 +494,23 @@ static void jvp_fused_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_
 }
 
 template <typename T, int ND, int P, bool VISC, bool DIAG>
-static void launch_cface_p(const CFaceArgs<T>& a, cudaStream_t s) {
+static void launch_cface_p(fr_ctx* c, const CFaceArgs<T>& a, cudaStream_t s) {
+  constexpr int NV = ND + 2;
   constexpr int NFP = ND == 2 ? P : P * P;
   constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;
+  constexpr int CT = VISC ? 2 * NV : NV;
+  // staged by bulk copies in FP32 where every block is a multiple of 16 bytes
+  // and a warp holds the tile's faces (3D p = 1, 3, 5); the two buffers then
+  // stay within the 48 KB of static shared memory
+  if constexpr (std::is_same<T, float>::value && (CT * NFP * (int)sizeof(T)) % 16 == 0 && FB <= 32 &&
+                2 * FB * 4 * CT * NFP * (int)sizeof(T) <= 48 * 1024) {
+    if (c->use_tma) {
+      const int ntiles = (a.n + FB - 1) / FB;
+      const unsigned grid = (unsigned)std::max(1, std::min(ntiles, 4 * (int)sm_count(c)));
+      cface_tma_kernel<T, ND, P, VISC, DIAG><<<grid, FB * NFP, 0, s>>>(a, c->d_status);
+      return;
+    }
+  }
   cface_kernel<T, ND, P, VISC, DIAG><<<nblocks(a.n, FB), FB * NFP, 0, s>>>(a);
 }
 
@@ -527,11 +541,11 @@ static void jvp_compact_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStrea
     const double nb = (double)g.n * NFP * (4.0 * CT + 2.0 * (VISC ? 3 : 1) * NV) * sizeof(T);
     FR_LAUNCH_B(c, kname<T>("cface_jvp_f64", "cface_jvp_f32", "cface_jvp_df"), s, nb, {
       switch (P) {
-        case 2: launch_cface_p<T, ND, 2, VISC, DIAG>(a, s); break;
-        case 3: launch_cface_p<T, ND, 3, VISC, DIAG>(a, s); break;
-        case 4: launch_cface_p<T, ND, 4, VISC, DIAG>(a, s); break;
-        case 5: launch_cface_p<T, ND, 5, VISC, DIAG>(a, s); break;
-        case 6: launch_cface_p<T, ND, 6, VISC, DIAG>(a, s); break;
+        case 2: launch_cface_p<T, ND, 2, VISC, DIAG>(c, a, s); break;
+        case 3: launch_cface_p<T, ND, 3, VISC, DIAG>(c, a, s); break;
+        case 4: launch_cface_p<T, ND, 4, VISC, DIAG>(c, a, s); break;
+        case 5: launch_cface_p<T, ND, 5, VISC, DIAG>(c, a, s); break;
+        case 6: launch_cface_p<T, ND, 6, VISC, DIAG>(c, a, s); break;
       }
     });
   }

@@ -239,6 +239,8 @@ struct fr_ctx {
   bool use_diag = true;
   bool df_arnoldi = false;    // Arnoldi dot products in double-float arithmetic (FP32 pipe)
   int arnoldi_map = 1;        // slot walk of the Arnoldi reductions (0 grid-strided, 1 warp runs)
+  bool use_tma = true;        // compact face kernel staged by bulk asynchronous copies where it can be
+  int* d_status = nullptr;    // device status word: bit 0, a bounded wait of a kernel gave up
   cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
   bool jvp_graph_ok = true;
   int* d_jidx = nullptr;

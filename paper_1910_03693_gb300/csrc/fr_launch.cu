@@ -152,6 +152,18 @@ fr_status fr_timing_report(fr_ctx* c, char* buf, int64_t len, int64_t* launches)
   return FR_OK;
 }
 
+fr_status fr_device_status(fr_ctx* c, int32_t* status, int32_t clear) {
+  if (!c || !status) return FR_ERR_INVALID;
+  int v = 0;
+  fr_status st = cuda_check(cudaDeviceSynchronize(), "fr_device_status");
+  if (st != FR_OK) return st;
+  st = cuda_check(cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "fr_device_status");
+  if (st != FR_OK) return st;
+  if (clear) cudaMemset(c->d_status, 0, sizeof(int));
+  *status = v;
+  return FR_OK;
+}
+
 fr_status fr_autotune(fr_ctx* c, const double* q64_dev, void* stream) {
   if (!c || !q64_dev) {
     set_error("fr_autotune: null argument");
@@ -180,14 +192,15 @@ fr_status fr_tuning_get(const fr_ctx* c, int32_t* table, int32_t* flags) {
   if (flags)
     *flags = (c->multi_launch ? FR_TUNE_MULTI_LAUNCH : 0) | (c->use_graphs ? FR_TUNE_GRAPHS : 0) |
              (c->use_diag ? FR_TUNE_DIAG_METRICS : 0) | (c->use_fused ? FR_TUNE_FUSED_JVP : 0) |
-             (c->df_arnoldi ? FR_TUNE_DF_ARNOLDI : 0) | (c->arnoldi_map == 1 ? FR_TUNE_ARNOLDI_RUNS : 0);
+             (c->df_arnoldi ? FR_TUNE_DF_ARNOLDI : 0) | (c->arnoldi_map == 1 ? FR_TUNE_ARNOLDI_RUNS : 0) |
+             (c->use_tma ? FR_TUNE_TMA_FACES : 0);
   return FR_OK;
 }
 
 fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   if (!c) return FR_ERR_INVALID;
   if (flags & ~(FR_TUNE_MULTI_LAUNCH | FR_TUNE_GRAPHS | FR_TUNE_DIAG_METRICS | FR_TUNE_FUSED_JVP | FR_TUNE_DF_ARNOLDI |
-                FR_TUNE_ARNOLDI_RUNS)) {
+                FR_TUNE_ARNOLDI_RUNS | FR_TUNE_TMA_FACES)) {
     set_error("fr_tuning_set: unknown flag bits");
     return FR_ERR_INVALID;
   }
@@ -206,6 +219,7 @@ fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   c->use_fused = (flags & FR_TUNE_FUSED_JVP) != 0;
   c->df_arnoldi = (flags & FR_TUNE_DF_ARNOLDI) != 0;
   c->arnoldi_map = (flags & FR_TUNE_ARNOLDI_RUNS) != 0 ? 1 : 0;
+  c->use_tma = (flags & FR_TUNE_TMA_FACES) != 0;
   c->diag = c->diag_mesh && c->use_diag;
   clear_work_cache(c);
   return FR_OK;

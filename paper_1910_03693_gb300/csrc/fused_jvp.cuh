@@ -522,61 +522,43 @@ struct CFaceArgs {
   int nvt;                  // components of the trace-gradient layout (its offsets scale to compact ones)
 };
 
-template <typename T, int ND, int P, bool VISC, bool DIAG>
-__global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
-  using S = Dual<T>;
-  constexpr int NV = ND + 2, NF = 2 * ND;
-  constexpr int NFP = ND == 2 ? P : P * P;
-  constexpr int CT = CompactWidth<VISC, NV>::value;
-  constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;    // faces a CTA
-  constexpr int BLK = CT * NFP;
-  __shared__ T sh[FB][4][BLK];                        // master q, master v, slave q, slave v
-  const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
-  const int64_t fidx = (int64_t)blockIdx.x * FB + lf;
-  const bool valid = lf < FB && fidx < a.n;
-  FaceRec r{};
-  const BasisTab<T>& B = a.basis[P];
-  int dm = 0, sm = 0, ds = 0, ss = 0, u = 0;
-  T absA = T(0), inv_absA = T(0), SfM[ND][ND], SfS[ND][ND], JiM = T(0), JiS = T(0);
-  T rowM[ND], rowS[ND];   // area-vector rows S[dm][:] (master, at t) and S[ds][:] (slave, at u)
-  if (valid) {
-    r = a.recs[fidx];
-    // compact trace blocks of the two sides: on a conforming mesh the compact
-    // offset is the trace-gradient one scaled by CT / nvt
-    const int64_t om = r.mt / a.nvt * CT, osl = r.st / a.nvt * CT;
-    T buf[4][CT];
+// Geometry of one face point read ahead of the staged traces (the master's
+// area vector and |S|, both sides' metric terms for their gradients).
+template <typename T, int ND>
+struct CFaceGeo {
+  T absA, inv_absA, JiM, JiS;
+  T SfM[ND][ND], SfS[ND][ND];
+  T rowM[ND], rowS[ND];
+  int u;
+};
+
+template <typename T, int ND, int P, bool DIAG>
+__device__ __forceinline__ void cface_geo(const CFaceArgs<T>& a, const FaceRec& r, int t, CFaceGeo<T, ND>& g) {
+  const int dm = r.mf >> 1, ds = r.sf >> 1;
+  g.u = orient_map(r.orient, t, P, ND);
+  g.absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + dm, t);
+  g.inv_absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + ND + dm, t);
+  face_metric<T, ND, P, DIAG>(a.geo, r.me, r.mf, t, g.SfM, g.JiM);
+  face_metric<T, ND, P, DIAG>(a.geo, r.se, r.sf, g.u, g.SfS, g.JiS);
 #pragma unroll
-    for (int c = 0; c < CT; ++c) {
-      buf[0][c] = a.trq[om + c * NFP + t];
-      buf[1][c] = a.trv[om + c * NFP + t];
-      buf[2][c] = a.trq[osl + c * NFP + t];
-      buf[3][c] = a.trv[osl + c * NFP + t];
-    }
-    dm = r.mf >> 1;
-    sm = r.mf & 1;
-    ds = r.sf >> 1;
-    ss = r.sf & 1;
-    u = orient_map(r.orient, t, P, ND);
-    absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + dm, t);
-    inv_absA = geo_face(a.geo, r.me, r.mf, ND * ND + 2 + ND + dm, t);
-    face_metric<T, ND, P, DIAG>(a.geo, r.me, r.mf, t, SfM, JiM);
-    face_metric<T, ND, P, DIAG>(a.geo, r.se, r.sf, u, SfS, JiS);
-#pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      rowM[j] = geo_face(a.geo, r.me, r.mf, dm * ND + j, t);
-      rowS[j] = geo_face(a.geo, r.se, r.sf, ds * ND + j, u);
-    }
-#pragma unroll
-    for (int w = 0; w < 4; ++w)
-#pragma unroll
-      for (int c = 0; c < CT; ++c) sh[lf][w][c * NFP + t] = buf[w][c];
+  for (int j = 0; j < ND; ++j) {
+    g.rowM[j] = geo_face(a.geo, r.me, r.mf, dm * ND + j, t);
+    g.rowS[j] = geo_face(a.geo, r.se, r.sf, ds * ND + j, g.u);
   }
-  __syncthreads();
-  if (!valid) return;
-  const T* XqM = sh[lf][0];
-  const T* XvM = sh[lf][1];
-  const T* XqS = sh[lf][2];
-  const T* XvS = sh[lf][3];
+}
+
+// Common flux, BR2 gradient and lifting at point t of one face from its four
+// staged compact blocks (master q, master v, slave q, slave v), written as the
+// face outputs of both sides.
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+__device__ __forceinline__ void cface_point(const CFaceArgs<T>& a, const FaceRec& r, int t, const CFaceGeo<T, ND>& g,
+                                            const T* XqM, const T* XvM, const T* XqS, const T* XvS) {
+  using S = Dual<T>;
+  constexpr int NV = ND + 2;
+  constexpr int NFP = ND == 2 ? P : P * P;
+  const BasisTab<T>& B = a.basis[P];
+  const int dm = r.mf >> 1, sm = r.mf & 1, ss = r.sf & 1;
+  const int u = g.u;
   S qM[NV], qS[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -587,26 +569,26 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
   T A[ND], n[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    A[j] = sgm * rowM[j];
-    n[j] = A[j] * inv_absA;
+    A[j] = sgm * g.rowM[j];
+    n[j] = A[j] * g.inv_absA;
   }
   S Fn[NV];
-  common_flux<ND>(a.flux, qM, qS, n, absA, a.gamma, Fn);
+  common_flux<ND>(a.flux, qM, qS, n, g.absA, a.gamma, Fn);
   S qc[NV];
   if (VISC) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) qc[v] = T(0.5) * (qM[v] + qS[v]);
     T cM[ND], cS[ND];
-    const T gJM = B.dgf[sm] * JiM;
-    const T gJS = B.dgf[ss] * JiS;
+    const T gJM = B.dgf[sm] * g.JiM;
+    const T gJS = B.dgf[ss] * g.JiS;
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
-      cM[j] = gJM * rowM[j];
-      cS[j] = gJS * rowS[j];
+      cM[j] = gJM * g.rowM[j];
+      cS[j] = gJS * g.rowS[j];
     }
     S GM[ND][NV], GS[ND][NV], Gc[ND][NV];
-    face_grad_m<T, ND, P, DIAG>(XqM, XvM, r.mf, t, SfM, JiM, B, GM);
-    face_grad_m<T, ND, P, DIAG>(XqS, XvS, r.sf, u, SfS, JiS, B, GS);
+    face_grad_m<T, ND, P, DIAG>(XqM, XvM, r.mf, t, g.SfM, g.JiM, B, GM);
+    face_grad_m<T, ND, P, DIAG>(XqS, XvS, r.sf, u, g.SfS, g.JiS, B, GS);
     if (DIAG) {
 #pragma unroll
       for (int j = 0; j < ND; ++j)
@@ -644,7 +626,6 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
       }
     }
   }
-  // face outputs of both sides (transformed common flux tangent; primal and tangent dq)
   T* om = a.fout + r.mo;
   T* os = a.fout + r.so;
   const T sgs = ss ? T(1) : T(-1);
@@ -659,6 +640,162 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
       os[(NV + v) * NFP + u] = value(dS);
       os[(2 * NV + v) * NFP + u] = tangent(dS);
     }
+  }
+}
+
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+__global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
+  constexpr int NV = ND + 2;
+  constexpr int NFP = ND == 2 ? P : P * P;
+  constexpr int CT = CompactWidth<VISC, NV>::value;
+  constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;    // faces a CTA
+  constexpr int BLK = CT * NFP;
+  __shared__ T sh[FB][4][BLK];                        // master q, master v, slave q, slave v
+  const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
+  const int64_t fidx = (int64_t)blockIdx.x * FB + lf;
+  const bool valid = lf < FB && fidx < a.n;
+  FaceRec r{};
+  CFaceGeo<T, ND> g{};
+  if (valid) {
+    r = a.recs[fidx];
+    // compact trace blocks of the two sides: on a conforming mesh the compact
+    // offset is the trace-gradient one scaled by CT / nvt
+    const int64_t om = r.mt / a.nvt * CT, osl = r.st / a.nvt * CT;
+    T buf[4][CT];
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+      buf[0][c] = a.trq[om + c * NFP + t];
+      buf[1][c] = a.trv[om + c * NFP + t];
+      buf[2][c] = a.trq[osl + c * NFP + t];
+      buf[3][c] = a.trv[osl + c * NFP + t];
+    }
+    cface_geo<T, ND, P, DIAG>(a, r, t, g);
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int c = 0; c < CT; ++c) sh[lf][w][c * NFP + t] = buf[w][c];
+  }
+  __syncthreads();
+  if (!valid) return;
+  cface_point<T, ND, P, VISC, DIAG>(a, r, t, g, sh[lf][0], sh[lf][1], sh[lf][2], sh[lf][3]);
+}
+
+// ---------------------------------------------------------------------------
+// The same face work with the staging done by the copy engine: a persistent
+// CTA walks the groups' face tiles; for each tile one lane per face issues
+// four bulk asynchronous copies (cp.async.bulk, global -> shared, completion
+// counted in bytes on an mbarrier), one per compact block, and the copies of
+// the next tile are in flight while the threads compute the current one (two
+// buffers).  Blocks must be multiples of 16 bytes at 16-byte aligned offsets
+// (the host checks CT x NFP x sizeof(T)); a wait that exceeds its iteration
+// limit sets bit 0 of *status, stops the walk and waits, again bounded, for the
+// copies still in flight before the CTA exits.  Instantiated for FP32 only
+// (two buffers within the 48 KB of static shared memory).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: true when the phase of `parity` completed within `limit` tries
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+constexpr int kTmaWaitLimit = 1 << 22;   // tries of one wait before it gives up (far above any copy's latency)
+
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+__global__ void __launch_bounds__(128, 4) cface_tma_kernel(CFaceArgs<T> a, int* status) {
+  constexpr int NV = ND + 2;
+  constexpr int NFP = ND == 2 ? P : P * P;
+  constexpr int CT = CompactWidth<VISC, NV>::value;
+  constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;
+  constexpr int BLK = CT * NFP;
+  constexpr uint32_t BYTES = BLK * sizeof(T);
+  static_assert(BYTES % 16 == 0 && FB <= 32, "bulk-copied blocks: multiples of 16 bytes, at most one warp of faces");
+  __shared__ __align__(128) T sh[2][FB][4][BLK];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int stop;
+  const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
+  const int ntiles = (a.n + FB - 1) / FB;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    stop = 0;
+  }
+  __syncthreads();
+  // one lane per face of the tile issues its four copies after lane 0 has
+  // announced the tile's bytes
+  auto issue = [&](int tile, int b) {
+    const int64_t f0 = (int64_t)tile * FB;
+    const int nf = (int)min((int64_t)FB, (int64_t)a.n - f0);
+    const int lane = threadIdx.x;   // warp 0
+    if (lane == 0) mbar_arrive_expect(&bar[b], (uint32_t)nf * 4u * BYTES);
+    __syncwarp();
+    if (lane < nf) {
+      const FaceRec r = a.recs[f0 + lane];
+      const int64_t om = r.mt / a.nvt * CT, osl = r.st / a.nvt * CT;
+      bulk_copy_g2s(sh[b][lane][0], a.trq + om, BYTES, &bar[b]);
+      bulk_copy_g2s(sh[b][lane][1], a.trv + om, BYTES, &bar[b]);
+      bulk_copy_g2s(sh[b][lane][2], a.trq + osl, BYTES, &bar[b]);
+      bulk_copy_g2s(sh[b][lane][3], a.trv + osl, BYTES, &bar[b]);
+    }
+  };
+  int it = 0;
+  if ((int)blockIdx.x < ntiles && threadIdx.x < 32) issue(blockIdx.x, 0);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const int next = tile + gridDim.x;
+    if (next < ntiles && threadIdx.x < 32) issue(next, b ^ 1);
+    const int64_t fidx = (int64_t)tile * FB + lf;
+    const bool valid = lf < FB && fidx < a.n;
+    FaceRec r{};
+    CFaceGeo<T, ND> g{};
+    if (valid) {
+      r = a.recs[fidx];
+      cface_geo<T, ND, P, DIAG>(a, r, t, g);
+    }
+    if (!mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitLimit)) {
+      atomicOr(status, 1);
+      stop = 1;
+    }
+    __syncthreads();
+    if (stop) break;
+    if (valid) cface_point<T, ND, P, VISC, DIAG>(a, r, t, g, sh[b][lf][0], sh[b][lf][1], sh[b][lf][2], sh[b][lf][3]);
+    __syncthreads();   // buffer b is free for the tile after next
+  }
+  if (stop) {
+    // copies of this and the next tile may still be in flight: wait for both
+    // buffers' current phases, bounded, before the CTA's shared memory goes away
+    mbar_wait(&bar[it & 1], (uint32_t)((it >> 1) & 1), kTmaWaitLimit);
+    mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitLimit);
   }
 }
 
