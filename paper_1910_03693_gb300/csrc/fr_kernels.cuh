@@ -236,21 +236,25 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
     const T Jinv = geo_face(a.geo, e, f, ND * ND + 1, t);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      T dq[ND];
-      dq[d] = dn[it][v];
       const T* face = sqf + (f * NV + v) * NFP;
       T y[P];
       load_contig<T, P, W>(face + (ND == 2 ? 0 : P * ib), y);   // the face line along its first axis
       Acc<T> ac = acc_init(T(0));
 #pragma unroll
       for (int m = 0; m < P; ++m) acc_madd(ac, B.D[ia][m], y[m]);
-      dq[ta] = acc_value(ac);
+      const T da = acc_value(ac);
+      T db = T(0);
       if (ND == 3) {
         ac = acc_init(T(0));
 #pragma unroll
         for (int m = 0; m < P; ++m) acc_madd(ac, B.D[ib][m], face[ia + P * m]);
-        dq[tb] = acc_value(ac);
+        db = acc_value(ac);
       }
+      // reference derivatives by axis through selects on the face's axes (a
+      // register array indexed by d / ta / tb would be placed in local memory)
+      T dq[ND];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) dq[j] = j == d ? dn[it][v] : (j == ta ? da : db);
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
         T g = T(0);
@@ -286,7 +290,7 @@ struct TraceMulti {
 // Every bucket in one persistent launch: CTAs walk the cost-ordered work
 // table with a grid stride and dispatch on the tile's degree.
 template <typename T, int ND, bool VISC, bool DIAG>
-__global__ void __launch_bounds__(256) trace_multi_kernel(TraceMulti<T> m) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trace_multi_kernel(const __grid_constant__ TraceMulti<T> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
     const WorkItem it = m.items[w];
@@ -817,7 +821,7 @@ struct VolMulti {
 };
 
 template <typename T, int ND, bool VISC, int MODE, bool DIAG>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : (is_dfloat<T>::value ? 2 : 1)) vol_multi_kernel(VolMulti<T> m) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 || is_dfloat<T>::value) ? 2 : 1) vol_multi_kernel(const __grid_constant__ VolMulti<T> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
     const WorkItem it = m.items[w];

@@ -136,8 +136,7 @@ __device__ __forceinline__ void face_grad_m(const T* Xq, const T* Xv, int fc, in
   const int tb = dc == 2 ? 1 : 2;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    Dual<T> dq[ND];
-    dq[dc] = Dual<T>{Xq[(NV + v) * NFP + t], Xv[(NV + v) * NFP + t]};
+    const Dual<T> dn{Xq[(NV + v) * NFP + t], Xv[(NV + v) * NFP + t]};
     const T* yq = Xq + v * NFP;
     const T* yv = Xv + v * NFP;
     T aq = T(0), av = T(0);
@@ -146,7 +145,8 @@ __device__ __forceinline__ void face_grad_m(const T* Xq, const T* Xv, int fc, in
       aq = xfma(B.D[ia][m], yq[m + P * ib], aq);
       av = xfma(B.D[ia][m], yv[m + P * ib], av);
     }
-    dq[ta] = Dual<T>{aq, av};
+    const Dual<T> da{aq, av};
+    Dual<T> db{T(0), T(0)};
     if (ND == 3) {
       aq = T(0);
       av = T(0);
@@ -155,8 +155,13 @@ __device__ __forceinline__ void face_grad_m(const T* Xq, const T* Xv, int fc, in
         aq = xfma(B.D[ib][m], yq[ia + P * m], aq);
         av = xfma(B.D[ib][m], yv[ia + P * m], av);
       }
-      dq[tb] = Dual<T>{aq, av};
+      db = Dual<T>{aq, av};
     }
+    // reference derivatives by axis, chosen by selects on the face's axes
+    // (indexing a register array by dc / ta / tb would place it in local memory)
+    Dual<T> dq[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) dq[j] = j == dc ? dn : (j == ta ? da : db);
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
       Dual<T> g{T(0), T(0)};
