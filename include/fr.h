@@ -396,7 +396,8 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
  * flags; elements per CTA outside [0, 256], choices outside [0, 2], weight
  * models outside [0, 3] or unknown flag bits give FR_ERR_INVALID. */
 #define FR_TUNE_MULTI_LAUNCH 1  /* one persistent launch over all degree buckets */
-#define FR_TUNE_GRAPHS 2        /* Arnoldi products replayed from a CUDA graph */
+#define FR_TUNE_GRAPHS 2        /* host-driven GMRES: the Arnoldi products
+                                   replayed from a CUDA graph               */
 #define FR_TUNE_DIAG_METRICS 4  /* 3D meshes of axis-aligned affine elements:
                                    kernels that skip the zero metric terms   */
 #define FR_TUNE_FUSED_JVP 8     /* meshes whose faces are all interior and
@@ -419,6 +420,22 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
                                    double-buffered in a persistent walk, where
                                    every block is a multiple of 16 bytes (the
                                    default; off: loads by the threads)       */
+#define FR_TUNE_DEVICE_GMRES 128 /* GMRES with exact products and one or two
+                                   Gram-Schmidt passes: the Givens rotations
+                                   and the convergence test on the device;
+                                   the host launches the Arnoldi iterations
+                                   in batches and reads the cycle's state once
+                                   per batch; launches past convergence
+                                   return at entry (the default; off: one
+                                   host round trip per iteration, products
+                                   replayed from a CUDA graph)               */
+#define FR_TUNE_F32_BASIS 256   /* GMRES with exact FP32 products, no
+                                   preconditioner and rtol >= 1e-4: the
+                                   Krylov basis and the products stored in
+                                   FP32, the dots and norms summed in FP32
+                                   over 16 values and in FP64 beyond (about
+                                   1e-6 relative, the products' own accuracy;
+                                   the default; off: FP64 basis)            */
 fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
 fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
 fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);
@@ -435,6 +452,14 @@ fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);
  * FR_ERR_INVALID if too small) and the number of launches since the last
  * fr_timing call into *launches (optional). */
 fr_status fr_timing(fr_ctx* ctx, int32_t enable);
+/* Restrict the event pairs to the kernels whose timing names appear in the
+ * comma-separated list `names` (NULL or empty: every kernel, the default);
+ * the other launches are still counted, with their algorithmic bytes and
+ * operations, and report 0 ms.  Every event pair adds two stream operations
+ * around its kernel, so timing one kernel family perturbs a step far less
+ * than timing all of them.  Synchronises the device and accumulates what was
+ * recorded under the previous selection first. */
+fr_status fr_timing_select(fr_ctx* ctx, const char* names);
 fr_status fr_timing_report(fr_ctx* ctx, char* buf, int64_t len, int64_t* launches);
 
 /* Device status word of the context (no counterpart in the paper): kernels

@@ -101,6 +101,7 @@ SIGNATURES = {
     "spectral_decay_indicator": [C.c_void_p, C.c_void_p, C.c_int, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_void_p],
     "fr_timing": [C.c_void_p, C.c_int32],
+    "fr_timing_select": [C.c_void_p, C.c_char_p],
     "fr_autotune": [C.c_void_p, C.c_void_p, C.c_void_p],
     "fr_tuning_get": [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "fr_tuning_set": [C.c_void_p, C.POINTER(C.c_int32), C.c_int32],

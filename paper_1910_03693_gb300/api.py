@@ -207,14 +207,16 @@ class FRContext:
 
     def tuning(self):
         """{"epb": 42 ints [prec][kernel][P], "multi_launch": bool, "graphs": bool, "diag_metrics": bool,
-        "fused_jvp": bool, "df_arnoldi": bool, "arnoldi_runs": bool, "tma_faces": bool}"""
+        "fused_jvp": bool, "df_arnoldi": bool, "arnoldi_runs": bool, "tma_faces": bool, "device_gmres": bool,
+        "f32_basis": bool}"""
         tab = (C.c_int32 * 42)()
         fl = C.c_int32(0)
         _check(lib().fr_tuning_get(self.h, tab, C.byref(fl)), "fr_tuning_get")
         return {"epb": [int(x) for x in tab], "multi_launch": bool(fl.value & 1), "graphs": bool(fl.value & 2),
                 "diag_metrics": bool(fl.value & 4), "fused_jvp": bool(fl.value & 8),
                 "df_arnoldi": bool(fl.value & 16), "arnoldi_runs": bool(fl.value & 32),
-                "tma_faces": bool(fl.value & 64)}
+                "tma_faces": bool(fl.value & 64), "device_gmres": bool(fl.value & 128),
+                "f32_basis": bool(fl.value & 256)}
 
     def set_tuning(self, t):
         """Set what `tuning()` returns; a missing "epb" keeps the table, missing switches default to on."""
@@ -222,7 +224,8 @@ class FRContext:
         flags = ((1 if t.get("multi_launch", True) else 0) | (2 if t.get("graphs", True) else 0) |
                  (4 if t.get("diag_metrics", True) else 0) | (8 if t.get("fused_jvp", True) else 0) |
                  (16 if t.get("df_arnoldi", False) else 0) | (32 if t.get("arnoldi_runs", True) else 0) |
-                 (64 if t.get("tma_faces", True) else 0))
+                 (64 if t.get("tma_faces", True) else 0) | (128 if t.get("device_gmres", True) else 0) |
+                 (256 if t.get("f32_basis", True) else 0))
         _check(lib().fr_tuning_set(self.h, tab, flags), "fr_tuning_set")
 
     # ---------------------------------------------------------- instrumentation
@@ -234,6 +237,12 @@ class FRContext:
 
     def timing(self, enable=True):
         _check(lib().fr_timing(self.h, 1 if enable else 0), "fr_timing")
+
+    def timing_select(self, names=None):
+        """Time only the kernels named (an iterable of timing names; None: all);
+        the others are counted with 0 ms."""
+        arg = None if not names else ",".join(names).encode()
+        _check(lib().fr_timing_select(self.h, arg), "fr_timing_select")
 
     def timing_report(self):
         """{kernel name: (launches, total device ms, algorithmic bytes, algorithmic flops)} and

@@ -167,10 +167,7 @@ void clear_graphs(fr_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     if (c->jvp_graph[k]) cudaGraphExecDestroy(c->jvp_graph[k]);
     c->jvp_graph[k] = nullptr;
-    for (auto& r : c->graph_timers[k]) {
-      c->timing.pool.push_back(r.a);
-      c->timing.pool.push_back(r.b);
-    }
+    for (auto& r : c->graph_timers[k]) c->timing.give_back(r);
     c->graph_timers[k].clear();
     c->graph_timers_live[k] = false;
     for (auto& p : c->jvp_graph_key[k]) p = nullptr;
@@ -657,6 +654,7 @@ static void destroy_impl(fr_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_jidx) cudaFreeHost(c->h_jidx);
   cudaFree(c->d_krylov);
+  cudaFree(c->d_krylov32);
   cudaFree(c->d_step);
   cudaFree(c->d_pc);
   cudaFree(c->d_pc_off);
@@ -666,6 +664,8 @@ static void destroy_impl(fr_ctx* c) {
   for (auto& v : c->d_vec32) cudaFree(v);
   cudaFree(c->d_red);
   if (c->h_red) cudaFreeHost(c->h_red);
+  cudaFree(c->d_gm);
+  if (c->h_gm) cudaFreeHost(c->h_gm);
   cudaFree(c->d_xfer);
   cudaFree(c->d_adapt_i32);
   cudaFree(c->d_adapt_i8);

@@ -151,6 +151,7 @@ static void launch_trace_p(const TraceArgs<T>& a, int epb, cudaStream_t s) {
 template <typename T, int ND, bool VISC>
 static TraceArgs<T> trace_args(fr_ctx* c, const Bucket& b, const T* q, T* trace) {
   TraceArgs<T> a;
+  a.gate = c->gate;
   a.q = q;
   a.trace = trace;
   a.slot_elem = c->d_slot_elem;
@@ -230,6 +231,8 @@ template <typename T>
 static VolArgs<T> vol_args(fr_ctx* c, const Bucket& b, const T* q, const T* v, T* out, double* out_neg64 = nullptr,
                            double* out64 = nullptr) {
   VolArgs<T> a;
+  a.gate = c->gate;
+  a.vscale = c->vscale;
   a.q = q;
   a.v = v;
   a.out = out;
@@ -309,6 +312,7 @@ template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
 static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) {
   for (const auto& g : c->fgroups) {
     FaceArgs<T> a;
+    a.gate = c->gate;
     a.recs = g.d_recs;
     a.trq = trq;
     a.trv = trv;
@@ -341,6 +345,7 @@ static void launch_faces(fr_ctx* c, const T* trq, const T* trv, cudaStream_t s) 
   }
   for (const auto& g : c->bgroups) {
     BndArgs<T> a;
+    a.gate = c->gate;
     a.recs = g.d_recs;
     a.trq = trq;
     a.trv = trv;
@@ -411,6 +416,7 @@ static void launch_ctraces(fr_ctx* c, const T* q, T* out, cudaStream_t s) {
   for (const auto& b : c->buckets) {
     const int P = b.p + 1, e = epb_multi(ND, P);
     CTraceArgs<T> a;
+    a.gate = c->gate;
     a.q = q;
     a.out = out;
     a.basis = basis_ptr<T>(c);
@@ -459,6 +465,8 @@ static void jvp_fused_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_
   launch_ctraces<T, ND, VISC>(c, v, trv, s);
   for (const auto& b : c->buckets) {
     FusedArgs<T> a;
+    a.gate = c->gate;
+    a.vscale = c->vscale;
     a.q = q;
     a.v = v;
     a.trq = trq;
@@ -524,6 +532,7 @@ static void jvp_compact_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStrea
   launch_ctraces<T, ND, VISC>(c, v, trv, s);
   for (const auto& g : c->fgroups) {
     CFaceArgs<T> a;
+    a.gate = c->gate;
     a.recs = g.d_recs;
     a.trq = trq;
     a.trv = trv;

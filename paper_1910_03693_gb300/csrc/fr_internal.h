@@ -206,6 +206,9 @@ struct fr_ctx {
   double pc_sigma = 0.0;
   int64_t step_cap = 0;                  // doubles in d_step            // (m+1) * n_dof_cap basis
   int krylov_m = 0;
+  float* d_krylov32 = nullptr;            // the FP32 Krylov basis ((m+1) * ld), when used
+  int krylov32_m = 0;
+  bool f32_basis = true;                 // GMRES with FP32 products: FP32 Krylov basis
   double* d_vec64[13] = {};   // 0-2 FD Jv, 3 Jv, 4-5 GMRES, 6-9 ESDIRK, 10-11 adaptation, 12 host staging
   float* d_vec32[4] = {};
   double* d_red = nullptr;               // reduction scratch
@@ -241,6 +244,17 @@ struct fr_ctx {
   int arnoldi_map = 1;        // slot walk of the Arnoldi reductions (0 grid-strided, 1 warp runs)
   bool use_tma = true;        // compact face kernel staged by bulk asynchronous copies where it can be
   int* d_status = nullptr;    // device status word: bit 0, a bounded wait of a kernel gave up
+  // device-driven GMRES cycles (exact products): the gate word the cycle's
+  // Arnoldi launches read (non-null only while such a cycle launches them;
+  // see gate_closed), the cycle's Hessenberg columns, rotations, residual
+  // vector and control words on the device with their pinned host mirror, and
+  // the iteration count of the last cycle (the size of the next first batch)
+  const int* gate = nullptr;
+  const double* vscale = nullptr;   // scale of the stored column a device-driven product reads (VolArgs)
+  bool device_gmres = true;
+  double* d_gm = nullptr;
+  double* h_gm = nullptr;
+  int gm_last_k = 4;
   cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
   bool jvp_graph_ok = true;
   int* d_jidx = nullptr;

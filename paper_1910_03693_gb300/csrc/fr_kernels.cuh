@@ -91,6 +91,13 @@ __device__ __forceinline__ T load_state(const T* q, int64_t i) {
   else return q[i];
 }
 
+// Gate of a device-driven GMRES cycle (null elsewhere): the launches of the
+// cycle's Arnoldi products read it on entry and return at once when it is set,
+// which the device-side Givens step does when the cycle has converged.  The
+// word is written by an earlier kernel of the same stream and only read here;
+// nothing waits on it.
+__device__ __forceinline__ bool gate_closed(const int* gate) { return gate != nullptr && *gate != 0; }
+
 template <typename T>
 __device__ __forceinline__ T geo_vol(const GeoView<T>& g, int64_t e, int k, int sp) {
   return g.vol[e * g.ves + (int64_t)k * g.vks + (int64_t)sp * g.vps];
@@ -113,6 +120,7 @@ struct TraceArgs {
   GeoView<T> geo;
   int64_t state_base, trace_base;
   int count, slot_begin, nvt;
+  const int* gate = nullptr;   // see gate_closed
 };
 
 template <int ND, int P>
@@ -273,6 +281,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
 template <typename T, int ND, int P, bool VISC, bool DIAG>
 __global__ void __launch_bounds__(256) trace_kernel(TraceArgs<T> a, int epb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(a.gate)) return;
   trace_body<T, ND, P, VISC, DIAG>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
 }
 
@@ -292,6 +301,7 @@ struct TraceMulti {
 template <typename T, int ND, bool VISC, bool DIAG>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trace_multi_kernel(const __grid_constant__ TraceMulti<T> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(m.b[0].gate)) return;
   for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
     const WorkItem it = m.items[w];
     const int b = it.bucket;
@@ -324,6 +334,7 @@ struct FaceArgs {
   int n, Pm, Ps, nvt;
   int flux;            // common inviscid flux: 0 Rusanov, 1 Roe
   int64_t scratch_base;
+  const int* gate = nullptr;   // see gate_closed
 };
 
 template <int ND, typename S, typename T>
@@ -396,6 +407,7 @@ __device__ __forceinline__ void slave_coef_at_mortar(const FaceArgs<T>& a, const
 template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
 __global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
   constexpr int NV = ND + 2;
+  if (gate_closed(a.gate)) return;
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
   const int Pm = a.Pm;
   const int NFPm = ND == 2 ? Pm : Pm * Pm;
@@ -523,6 +535,7 @@ __global__ void __launch_bounds__(128) face_kernel(FaceArgs<T> a) {
 template <typename T, int ND, bool VISC, int MODE>
 __global__ void __launch_bounds__(128) mortar_project_kernel(FaceArgs<T> a) {
   constexpr int NV = ND + 2;
+  if (gate_closed(a.gate)) return;
   const int Pm = a.Pm, Ps = a.Ps;
   const int NFPm = ND == 2 ? Pm : Pm * Pm;
   const int NFPs = ND == 2 ? Ps : Ps * Ps;
@@ -574,11 +587,13 @@ struct BndArgs {
   T qinf[5];
   int n, P, kind;
   int flux;            // common inviscid flux: 0 Rusanov, 1 Roe
+  const int* gate = nullptr;   // see gate_closed
 };
 
 template <typename T, int ND, bool VISC, int MODE>
 __global__ void __launch_bounds__(128) bnd_kernel(BndArgs<T> a) {
   constexpr int NV = ND + 2;
+  if (gate_closed(a.gate)) return;
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
   const int P = a.P;
   const int NFP = ND == 2 ? P : P * P;
@@ -658,6 +673,10 @@ struct VolArgs {
   T gamma, mu, kappa;
   int64_t state_base, out_base;
   int count, slot_begin;
+  const int* gate = nullptr;   // see gate_closed
+  // JVP, optional: J v is multiplied by *vscale (v is a stored Krylov column
+  // whose scale lives on the device; J is linear in v)
+  const double* vscale = nullptr;
 };
 
 
@@ -791,6 +810,7 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
       div[v] = div[v] + acc_value(acc);
     }
   }
+  const double vs = (MODE == 1 && a.vscale) ? *a.vscale : 1.0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     S r = (T(0) - div[v]) * Jinv;
@@ -798,9 +818,11 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
       a.out64[a.state_base + (i * NV + v) * NSP + sp] = to_double(value(r));
     } else {
       if (MODE == 1 && a.out_neg64)
-        a.out_neg64[a.state_base + (i * NV + v) * NSP + sp] = -(double)tangent(r);
+        a.out_neg64[a.state_base + (i * NV + v) * NSP + sp] = -vs * (double)tangent(r);
+      else if (MODE == 1)
+        a.out[a.state_base + (i * NV + v) * NSP + sp] = a.vscale ? (T)vs * tangent(r) : tangent(r);
       else
-        a.out[a.state_base + (i * NV + v) * NSP + sp] = MODE == 1 ? tangent(r) : value(r);
+        a.out[a.state_base + (i * NV + v) * NSP + sp] = value(r);
     }
   }
 }
@@ -808,6 +830,7 @@ __device__ __forceinline__ void vol_body(const VolArgs<T>& a, int64_t i0, int ep
 template <typename T, int ND, int P, bool VISC, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : (is_dfloat<T>::value ? 2 : 1)) vol_kernel(VolArgs<T> a, int epb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(a.gate)) return;
   vol_body<T, ND, P, VISC, MODE, DIAG>(a, (int64_t)blockIdx.x * epb, epb, smem_raw);
 }
 
@@ -823,6 +846,7 @@ struct VolMulti {
 template <typename T, int ND, bool VISC, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 || is_dfloat<T>::value) ? 2 : 1) vol_multi_kernel(const __grid_constant__ VolMulti<T> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(m.b[0].gate)) return;
   for (int w = blockIdx.x; w < m.n_items; w += gridDim.x) {
     const WorkItem it = m.items[w];
     const int b = it.bucket;

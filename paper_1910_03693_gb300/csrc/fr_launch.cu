@@ -134,6 +134,28 @@ fr_status fr_timing(fr_ctx* c, int32_t enable) {
   return FR_OK;
 }
 
+fr_status fr_timing_select(fr_ctx* c, const char* names) {
+  if (!c) return FR_ERR_INVALID;
+  cudaDeviceSynchronize();
+  c->timing.collect();
+  collect_graph_timers(c);
+  c->timing.select.clear();
+  if (names) {
+    std::string cur;
+    for (const char* p = names;; ++p) {
+      if (*p == ',' || *p == '\0') {
+        if (!cur.empty()) c->timing.select.push_back(cur);
+        cur.clear();
+        if (*p == '\0') break;
+      } else if (*p != ' ') {
+        cur += *p;
+      }
+    }
+  }
+  c->timing.select_gen += 1;
+  return FR_OK;
+}
+
 fr_status fr_timing_report(fr_ctx* c, char* buf, int64_t len, int64_t* launches) {
   if (!c || !buf || len <= 0) return FR_ERR_INVALID;
   cudaDeviceSynchronize();
@@ -193,14 +215,16 @@ fr_status fr_tuning_get(const fr_ctx* c, int32_t* table, int32_t* flags) {
     *flags = (c->multi_launch ? FR_TUNE_MULTI_LAUNCH : 0) | (c->use_graphs ? FR_TUNE_GRAPHS : 0) |
              (c->use_diag ? FR_TUNE_DIAG_METRICS : 0) | (c->use_fused ? FR_TUNE_FUSED_JVP : 0) |
              (c->df_arnoldi ? FR_TUNE_DF_ARNOLDI : 0) | (c->arnoldi_map == 1 ? FR_TUNE_ARNOLDI_RUNS : 0) |
-             (c->use_tma ? FR_TUNE_TMA_FACES : 0);
+             (c->use_tma ? FR_TUNE_TMA_FACES : 0) | (c->device_gmres ? FR_TUNE_DEVICE_GMRES : 0) |
+             (c->f32_basis ? FR_TUNE_F32_BASIS : 0);
   return FR_OK;
 }
 
 fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   if (!c) return FR_ERR_INVALID;
   if (flags & ~(FR_TUNE_MULTI_LAUNCH | FR_TUNE_GRAPHS | FR_TUNE_DIAG_METRICS | FR_TUNE_FUSED_JVP | FR_TUNE_DF_ARNOLDI |
-                FR_TUNE_ARNOLDI_RUNS | FR_TUNE_TMA_FACES)) {
+                FR_TUNE_ARNOLDI_RUNS | FR_TUNE_TMA_FACES | FR_TUNE_DEVICE_GMRES |
+                FR_TUNE_F32_BASIS)) {
     set_error("fr_tuning_set: unknown flag bits");
     return FR_ERR_INVALID;
   }
@@ -220,6 +244,8 @@ fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   c->df_arnoldi = (flags & FR_TUNE_DF_ARNOLDI) != 0;
   c->arnoldi_map = (flags & FR_TUNE_ARNOLDI_RUNS) != 0 ? 1 : 0;
   c->use_tma = (flags & FR_TUNE_TMA_FACES) != 0;
+  c->device_gmres = (flags & FR_TUNE_DEVICE_GMRES) != 0;
+  c->f32_basis = (flags & FR_TUNE_F32_BASIS) != 0;
   c->diag = c->diag_mesh && c->use_diag;
   clear_work_cache(c);
   return FR_OK;

@@ -47,8 +47,11 @@ fr_status launch_jvp_prepared(fr_ctx* c, const void* q, const void* v, void* Jv,
 fr_status launch_jvp_prepared_neg64(fr_ctx* c, const void* q, const void* v, double* w, fr_prec prec,
                                     cudaStream_t s);
 
-// z = M^-1 (a w + b u) with the element-Jacobi preconditioner (u optional; z may alias w)
-fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s);
+// z = M^-1 (a w + b u) with the element-Jacobi preconditioner (u optional; z may alias w).
+// bscale (optional, device): b is multiplied by *bscale on the device; gate
+// (optional): the launches return at entry when *gate is set (gate_closed).
+fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s,
+                        const int* gate = nullptr, const double* bscale = nullptr);
 
 // Jv = (R(q + eps v) - R0) / eps in FP64; R0 = R(q) is computed when null.
 fr_status launch_fd_jv(fr_ctx* c, const double* q, const double* v, double* Jv, double eps,

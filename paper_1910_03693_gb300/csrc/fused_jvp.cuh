@@ -75,6 +75,7 @@ struct CTraceArgs {
   const BasisTab<T>* basis;
   int64_t state_base, ctrace_base;
   int count;
+  const int* gate = nullptr;   // see gate_closed
 };
 
 template <typename T, int ND, int P, bool VISC>
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(256) ctrace_kernel(CTraceArgs<T> a, int epb) {
   constexpr int CT = CompactWidth<VISC, NV>::value;
   constexpr int NFPT = NF * NFP, ITERS = (NFPT + NSP - 1) / NSP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(a.gate)) return;
   const int le = threadIdx.x / NSP, lt = threadIdx.x % NSP;
   const int64_t i = (int64_t)blockIdx.x * epb + le;
   const bool valid = le < epb && i < a.count;
@@ -204,6 +206,8 @@ struct FusedArgs {
   int flux;
   int64_t state_base, ctrace_base;
   int count, slot_begin;
+  const int* gate = nullptr;   // see gate_closed
+  const double* vscale = nullptr;   // optional: J v multiplied by *vscale (see VolArgs)
 };
 
 // Shared memory of one element, in values of T: the state and tangent, the
@@ -230,6 +234,7 @@ __global__ void __launch_bounds__(256, 2) fused_jvp_kernel(FusedArgs<T> a, int e
   constexpr int CT = Sm::CT, TB = Sm::TB, FO = Sm::FO;
   constexpr int NFPT = NF * NFP, ITERS = (NFPT + NSP - 1) / NSP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(a.gate)) return;
   const int le = threadIdx.x / NSP, lt = threadIdx.x % NSP;
   const int64_t i = (int64_t)blockIdx.x * epb + le;
   const bool valid = le < epb && i < a.count;
@@ -488,12 +493,13 @@ __global__ void __launch_bounds__(256, 2) fused_jvp_kernel(FusedArgs<T> a, int e
       div[v] = div[v] + acc_value(acc);
     }
   }
+  const double vs = a.vscale ? *a.vscale : 1.0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const S r = (T(0) - div[v]) * Jinv;
     const int64_t k = a.state_base + (i * NV + v) * NSP + lt;
-    if (a.out_neg64) a.out_neg64[k] = -(double)tangent(r);
-    else a.out[k] = tangent(r);
+    if (a.out_neg64) a.out_neg64[k] = -vs * (double)tangent(r);
+    else a.out[k] = a.vscale ? (T)vs * tangent(r) : tangent(r);
   }
 }
 
@@ -525,6 +531,7 @@ struct CFaceArgs {
   int flux;
   int n;                    // faces in the group
   int nvt;                  // components of the trace-gradient layout (its offsets scale to compact ones)
+  const int* gate = nullptr;   // see gate_closed
 };
 
 // Geometry of one face point read ahead of the staged traces (the master's
@@ -656,6 +663,7 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
   constexpr int FB = NFP >= 128 ? 1 : 128 / NFP;    // faces a CTA
   constexpr int BLK = CT * NFP;
   __shared__ T sh[FB][4][BLK];                        // master q, master v, slave q, slave v
+  if (gate_closed(a.gate)) return;
   const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
   const int64_t fidx = (int64_t)blockIdx.x * FB + lf;
   const bool valid = lf < FB && fidx < a.n;
@@ -747,6 +755,7 @@ __global__ void __launch_bounds__(128, 4) cface_tma_kernel(CFaceArgs<T> a, int* 
   __shared__ __align__(128) T sh[2][FB][4][BLK];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int stop;
+  if (gate_closed(a.gate)) return;   // before any barrier is armed or copy issued
   const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
   const int ntiles = (a.n + FB - 1) / FB;
   if (threadIdx.x == 0) {

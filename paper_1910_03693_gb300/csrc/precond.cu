@@ -340,8 +340,11 @@ static size_t pc_blocked_smem(int nb) {
 __global__ void __launch_bounds__(256) k_pc_apply_big(const float* __restrict__ B, const int64_t* __restrict__ pc_off,
                                                       const int64_t* __restrict__ state_off, int slot_begin, int nb,
                                                       double a, const double* w, double b,
-                                                      const double* __restrict__ u, double* z, double inv_sigma) {
+                                                      const double* __restrict__ u, double* z, double inv_sigma,
+                                                      const int* __restrict__ gate, const double* __restrict__ bscale) {
   extern __shared__ __align__(16) float xs[];   // [nb]
+  if (gate && *gate) return;
+  if (bscale) b *= *bscale;
   const int s = slot_begin + blockIdx.x;
   const int64_t base = state_off[s], off = pc_off[s];
   double xv[kPcMax / 256 + 1];
@@ -369,8 +372,10 @@ __global__ void __launch_bounds__(256) k_pc_apply_big(const float* __restrict__ 
 __global__ void k_pc_apply(const float* __restrict__ B, const int64_t* __restrict__ pc_off,
                            const int64_t* __restrict__ state_off, int slot_begin, int count, int nb, int epb,
                            double a, const double* w, double b, const double* __restrict__ u, double* z,
-                           double inv_sigma) {
+                           double inv_sigma, const int* __restrict__ gate, const double* __restrict__ bscale) {
   extern __shared__ __align__(16) float xs[];   // [epb][nb]
+  if (gate && *gate) return;
+  if (bscale) b *= *bscale;
   const int le = threadIdx.x / nb, i = threadIdx.x % nb;
   const int e = blockIdx.x * epb + le;
   const bool valid = le < epb && e < count;
@@ -398,7 +403,10 @@ __global__ void k_pc_apply(const float* __restrict__ B, const int64_t* __restric
 
 // z = (a w + b u) / sigma on every DOF of a bucket without stored blocks
 __global__ void k_pc_scale(const int64_t* __restrict__ state_off, int slot_begin, int count, int nb, double a,
-                           const double* w, double b, const double* __restrict__ u, double* z, double inv_sigma) {
+                           const double* w, double b, const double* __restrict__ u, double* z, double inv_sigma,
+                           const int* __restrict__ gate, const double* __restrict__ bscale) {
+  if (gate && *gate) return;
+  if (bscale) b *= *bscale;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)count * nb) return;
   const int64_t idx = state_off[slot_begin + (int)(t / nb)] + (int)(t % nb);
@@ -548,7 +556,8 @@ fr_status fr_precond_release(fr_ctx* c) {
 namespace frgb {
 
 // z = M^-1 (a w + b u) on every element (z may alias w)
-fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s) {
+fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s,
+                        const int* gate, const double* bscale) {
   if (!c->pc_ready) {
     set_error("element-Jacobi preconditioner not built (fr_precond_build) for the current layout");
     return FR_ERR_INVALID;
@@ -561,7 +570,8 @@ fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const do
       const int64_t nt = (int64_t)bk.count * nb;
       FR_LAUNCH_B(c, "precond_apply", s, 24.0 * nt,
                   k_pc_scale<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c->d_state_off, bk.slot_begin, bk.count, nb,
-                                                                        a, w, b, u, z, 1.0 / c->pc_sigma));
+                                                                        a, w, b, u, z, 1.0 / c->pc_sigma, gate,
+                                                                        bscale));
       continue;
     }
     const double bytes = (double)bk.count * nb * (24.0 + 4.0 * nb);
@@ -569,7 +579,7 @@ fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const do
       FR_LAUNCH_B(c, "precond_apply", s, bytes,
                   k_pc_apply_big<<<bk.count, 256, sizeof(float) * nb, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
                                                                            bk.slot_begin, nb, a, w, b, u, z,
-                                                                           1.0 / c->pc_sigma));
+                                                                           1.0 / c->pc_sigma, gate, bscale));
       continue;
     }
     const int epb = 256 / nb;
@@ -578,7 +588,7 @@ fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const do
     FR_LAUNCH_B(c, "precond_apply", s, bytes,
                 k_pc_apply<<<grid, threads, sizeof(float) * threads, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
                                                                           bk.slot_begin, bk.count, nb, epb, a, w, b,
-                                                                          u, z, 1.0 / c->pc_sigma));
+                                                                          u, z, 1.0 / c->pc_sigma, gate, bscale));
   }
   return cuda_check(cudaGetLastError(), "precond_apply");
 }

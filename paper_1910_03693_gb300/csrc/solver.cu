@@ -30,6 +30,18 @@ constexpr int64_t kOutY = kOutN + kMaxK;
 constexpr int64_t kOutS = kOutY + kMaxK;    // scales of the stored Krylov columns
 constexpr int64_t kTicket = kOutS + kMaxK;
 
+// State of a device-driven GMRES cycle (doubles of fr_ctx::d_gm): the
+// Hessenberg columns (column j at j * kMaxK, rows 0..j+1, rotated in place),
+// the Givens rotations, the right-hand side g of the small least-squares
+// problem, then the control words (ints): the gate, the iterations completed
+// in the cycle, and a flag set when an Arnoldi vector was not finite.
+constexpr int64_t kGmH = 0;
+constexpr int64_t kGmCs = kGmH + (int64_t)kMaxK * kMaxK;
+constexpr int64_t kGmSn = kGmCs + kMaxK;
+constexpr int64_t kGmG = kGmSn + kMaxK;
+constexpr int64_t kGmCtl = kGmG + kMaxK + 1;
+constexpr int64_t kGmSize = kGmCtl + 2;
+
 static fr_status ensure_red(fr_ctx* c) {
   if (c->d_red) return FR_OK;
   c->red_cap = kTicket + 1;
@@ -115,6 +127,76 @@ __device__ __forceinline__ bool grid_sum(const double (&vals)[KC], int k, double
   }
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
+}
+
+// Bookkeeping of Arnoldi iteration j in a device-driven GMRES cycle, run by
+// the block that completes the iteration's last Gram-Schmidt update: column j
+// of the Hessenberg matrix of the operator (h_ij = s_i raw_ij from the
+// coefficients of the unnormalised basis, plus the second pass's, plus the
+// shift on the diagonal, h_{j+1,j} = ||w_new||), the earlier Givens rotations
+// applied to it, the new rotation and the least-squares residual estimate
+// |g_{j+1}|.  The gate closes when that estimate reaches tol, when the new
+// vector is zero (the Krylov space is invariant), after the iteration limit
+// (last) or when ||w_new|| is not finite (then ctl[2] = 1 and the column is
+// not counted); ctl[1] counts the iterations of the cycle that completed.
+// The column and the rotations are staged in shared memory so that the one
+// thread applying the rotations in order waits on no global load.
+struct StepArgs {
+  double* gm = nullptr;              // cycle state (kGm* layout); null: no step after this pass
+  const double* dots1 = nullptr;     // the Gram-Schmidt coefficients of the pass(es)
+  const double* dots2 = nullptr;
+  const double* scale = nullptr;     // scales of the stored columns
+  const double* nrm2 = nullptr;      // ||w_new||^2
+  double shift = 0.0, tol = 0.0;
+  int j = 0, last = 0, two_pass = 0;
+};
+
+__device__ void arnoldi_step_block(const StepArgs& a) {
+  __shared__ double col[kMaxK + 1], rc[kMaxK], rs[kMaxK];
+  __shared__ int keep;
+  double* gm = a.gm;
+  int* ctl = reinterpret_cast<int*>(gm + kGmCtl);
+  const int j = a.j;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double h1 = a.scale[i] * a.dots1[i];
+    col[i] = a.two_pass ? h1 + a.scale[i] * a.dots2[i] : h1;
+    if (i < j) {
+      rc[i] = gm[kGmCs + i];
+      rs[i] = gm[kGmSn + i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(*a.nrm2);
+    keep = isfinite(hn) ? 1 : 0;
+    if (!keep) {
+      ctl[2] = 1;
+      ctl[0] = 1;
+    } else {
+      col[j] += a.shift;
+      col[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = rc[i] * col[i] + rs[i] * col[i + 1];
+        col[i + 1] = -rs[i] * col[i] + rc[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double den = hypot(col[j], col[j + 1]);
+      const double rcj = den == 0.0 ? 1.0 : col[j] / den;
+      const double sj = den == 0.0 ? 0.0 : col[j + 1] / den;
+      col[j] = rcj * col[j] + sj * col[j + 1];
+      col[j + 1] = 0.0;
+      gm[kGmCs + j] = rcj;
+      gm[kGmSn + j] = sj;
+      const double gj = gm[kGmG + j];
+      gm[kGmG + j + 1] = -sj * gj;
+      gm[kGmG + j] = rcj * gj;
+      ctl[1] = j + 1;
+      if (fabs(sj * gj) <= a.tol || hn == 0.0 || a.last) ctl[0] = 1;
+    }
+  }
+  __syncthreads();
+  if (keep)
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) gm[kGmH + (int64_t)j * kMaxK + i] = col[i];
 }
 
 // Slot q of a vector seen as pairs (VEC: 16-byte loads of two values) or
@@ -242,7 +324,9 @@ template <int KC, bool VEC, typename WT, bool NEG, int MAP = 0>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int k,
                                                            const WT* __restrict__ w, int64_t n,
                                                            double* __restrict__ partial, double* __restrict__ out,
-                                                           unsigned* __restrict__ ticket, int with_norm) {
+                                                           unsigned* __restrict__ ticket, int with_norm,
+                                                           const int* __restrict__ gate) {
+  if (gate && *gate) return;   // past the end of a device-driven GMRES cycle
   constexpr int U = Unroll<KC, MAP>::U, CH = Unroll<KC, MAP>::CH;
   using L = Slots<VEC>;
   using LW = WSlots<VEC, WT, NEG>;
@@ -371,8 +455,10 @@ template <int KC, bool VEC, typename WT, bool NEG, int MAP = 0>
 __global__ void __launch_bounds__(kRedThreads) k_multidot_df(const double* __restrict__ V, int64_t ldv, int k,
                                                               const WT* __restrict__ w, int64_t n,
                                                               double* __restrict__ partial, double* __restrict__ out,
-                                                              unsigned* __restrict__ ticket, int with_norm) {
+                                                              unsigned* __restrict__ ticket, int with_norm,
+                                                              const int* __restrict__ gate) {
   static_assert(sizeof(WT) == 8 && !NEG, "FP64 vectors only");
+  if (gate && *gate) return;
   constexpr int U = Unroll<KC>::U, CH = Unroll<KC>::CH;
   using L = Slots<VEC>;
   float S[KC + 1], E[KC + 1];
@@ -441,7 +527,8 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
                                                               double* w_out, int64_t n, double* __restrict__ partial,
                                                               double* __restrict__ out, unsigned* __restrict__ ticket,
                                                               double* __restrict__ next_scale, int* __restrict__ jidx,
-                                                              int next_j) {
+                                                              int next_j, const int* __restrict__ gate, StepArgs step) {
+  if (gate && *gate) return;
   constexpr int U = Unroll<KC, MAP>::U, CH = Unroll<KC, MAP>::CH;
   using L = Slots<VEC>;
   using LW = WSlots<VEC, WT, NEG>;
@@ -485,10 +572,13 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_update(const double* __res
   double acc[1] = {accu[0]};
 #pragma unroll
   for (int u = 1; u < U; ++u) acc[0] += accu[u];
-  if (grid_sum<1>(acc, 1, partial, out, ticket) && threadIdx.x == 0 && next_scale) {
-    const double hn = sqrt(out[0]);
-    *next_scale = hn != 0.0 ? 1.0 / hn : 0.0;
-    *jidx = next_j;
+  if (grid_sum<1>(acc, 1, partial, out, ticket)) {   // the block that completed the sum
+    if (threadIdx.x == 0 && next_scale) {
+      const double hn = sqrt(out[0]);
+      *next_scale = hn != 0.0 ? 1.0 / hn : 0.0;
+      *jidx = next_j;
+    }
+    if (step.gm) arnoldi_step_block(step);
   }
 }
 
@@ -510,6 +600,204 @@ static unsigned wave_grid(unsigned grid) {
     resident = std::max(1, per_sm * std::max(sms, 1));
   }
   return std::max(1u, std::min(grid, (unsigned)resident));
+}
+
+// ---------------------------------------------------------------------------
+// Krylov basis stored in FP32 (GMRES with FP32 products and a tolerance those
+// products can meet).  The columns and the product J v are FP32, so every
+// Arnoldi kernel moves 4 bytes a value where the FP64 basis moves 8.  The
+// arithmetic must leave the FP64 pipe for that to pay: on GB300 one FP64 FMA
+// per value already runs at about the rate HBM delivers 8-byte values.  Each
+// thread therefore sums its 16 products of a loop step (four float4 slots a
+// column) with FP32 FMAs and adds that partial sum to an FP64 accumulator, one
+// FP64 addition per 16 values and column, before the usual deterministic FP64
+// grid reduction.  A partial sum carries a relative error of about 16 x 2^-24
+// of its sixteen |u_i w_i|: the dots, norms and hence the orthogonality of the
+// stored basis hold to about 1e-6, the accuracy of the FP32 products
+// themselves.  Compressed-basis GMRES (Aliaga, Anzt, Gruetzmacher,
+// Quintana-Orti, Tomas, IJHPCA 2022) stores the basis in reduced precision for
+// the same reason.
+// ---------------------------------------------------------------------------
+
+// Slot q of an FP32 vector of n values as four values; the slot n / 4 holds
+// the ragged tail, slots past the vector read as zero.
+struct F4Slots {
+  __device__ static float4 tail(const float* p, int64_t n4, int64_t n) {
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t b = 4 * n4;
+    if (b < n) r.x = p[b];
+    if (b + 1 < n) r.y = p[b + 1];
+    if (b + 2 < n) r.z = p[b + 2];
+    return r;
+  }
+  // streaming load (the Krylov columns: read once per pass)
+  __device__ static float4 load_stream(const float* __restrict__ p, int64_t q, int64_t n4, int64_t n) {
+    if (q < n4) return __ldcs(reinterpret_cast<const float4*>(p) + q);
+    return q == n4 ? tail(p, n4, n) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __device__ static float4 load(const float* p, int64_t q, int64_t n4, int64_t n) {
+    if (q < n4) return reinterpret_cast<const float4*>(p)[q];
+    return q == n4 ? tail(p, n4, n) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __device__ static void store(float* p, int64_t q, int64_t n4, int64_t n, float4 v) {
+    if (q < n4) {
+      reinterpret_cast<float4*>(p)[q] = v;
+    } else if (q == n4) {
+      const int64_t b = 4 * n4;
+      if (b < n) p[b] = v.x;
+      if (b + 1 < n) p[b + 1] = v.y;
+      if (b + 2 < n) p[b + 2] = v.z;
+    }
+  }
+};
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+}
+
+// out[kk] = s_w V[kk]^T w for kk < k (s_w = -1 with NEG: w holds J v and the
+// Arnoldi vector is -J v), and with with_norm out[k] = ||w||^2; FP32 columns
+// and w, walked as warp runs of U x 32 float4 slots.
+template <int KC, bool NEG>
+__global__ void __launch_bounds__(kRedThreads) k_multidot32(const float* __restrict__ V, int64_t ldv, int k,
+                                                             const float* __restrict__ w, int64_t n,
+                                                             double* __restrict__ partial, double* __restrict__ out,
+                                                             unsigned* __restrict__ ticket, int with_norm,
+                                                             const int* __restrict__ gate) {
+  if (gate && *gate) return;
+  constexpr int U = 4, CH = KC < 4 ? KC : 4;
+  double acc[KC + 1];
+#pragma unroll
+  for (int kk = 0; kk <= KC; ++kk) acc[kk] = 0.0;
+  const int64_t n4 = n / 4, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t last = n4 + ((n & 3) ? 0 : -1);   // highest slot holding data
+  const SlotWalk<1, U> sw(stride);
+  for (int64_t q0 = sw.first; q0 - (threadIdx.x & 31) <= last; q0 += sw.step) {
+    float4 wv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) wv[u] = F4Slots::load(w, q0 + u * sw.du, n4, n);
+#pragma unroll
+    for (int c0 = 0; c0 < KC; c0 += CH) {
+      if (c0 < k) {
+        float4 vv[U][CH];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (c0 + t < k) vv[u][t] = F4Slots::load_stream(V + (c0 + t) * ldv, q0 + u * sw.du, n4, n);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+          if (c0 + t < k) {
+            float sp = 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) sp = dot4(vv[u][t], wv[u], sp);
+            acc[c0 + t] += (double)sp;
+          }
+      }
+    }
+    if (with_norm) {
+      float sp = 0.f;
+#pragma unroll
+      for (int u = 0; u < U; ++u) sp = dot4(wv[u], wv[u], sp);
+      acc[KC] += (double)sp;
+    }
+  }
+  // slots 0..k-1: the dots; slot k: ||w||^2 (selects only, no runtime indexing)
+  double o[KC + 1];
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) o[kk] = kk < k ? (NEG ? -acc[kk] : acc[kk]) : acc[KC];
+  o[KC] = acc[KC];
+  grid_sum<KC + 1>(o, with_norm ? k + 1 : k, partial, out, ticket);
+}
+
+// w_out = s_w w_in - sum_kk s_kk^2 raw[kk] V[kk] in FP32 (s_w = -1 with NEG),
+// out[0] = ||w_out||^2; w_out may be w_in.  With next_scale, the block that
+// finishes the norm stores 1/||w_out|| and next_j as k_orth_update does.
+template <int KC, bool NEG>
+__global__ void __launch_bounds__(kRedThreads) k_orth_update32(const float* __restrict__ V, int64_t ldv, int k,
+                                                                const double* __restrict__ raw,
+                                                                const double* __restrict__ scale, const float* w_in,
+                                                                float* w_out, int64_t n, double* __restrict__ partial,
+                                                                double* __restrict__ out, unsigned* __restrict__ ticket,
+                                                                double* __restrict__ next_scale, int* __restrict__ jidx,
+                                                                int next_j, const int* __restrict__ gate, StepArgs step) {
+  if (gate && *gate) return;
+  constexpr int U = 4, CH = KC < 4 ? KC : 4;
+  __shared__ float hs[KC];
+  if (threadIdx.x < KC)
+    hs[threadIdx.x] = threadIdx.x < k ? (float)(scale[threadIdx.x] * scale[threadIdx.x] * raw[threadIdx.x]) : 0.f;
+  __syncthreads();
+  double accn = 0.0;
+  const int64_t n4 = n / 4, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t last = n4 + ((n & 3) ? 0 : -1);
+  const SlotWalk<1, U> sw(stride);
+  for (int64_t q0 = sw.first; q0 - (threadIdx.x & 31) <= last; q0 += sw.step) {
+    float4 x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      x[u] = F4Slots::load(w_in, q0 + u * sw.du, n4, n);
+      if (NEG) x[u] = make_float4(-x[u].x, -x[u].y, -x[u].z, -x[u].w);
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < KC; c0 += CH) {
+      if (c0 < k) {
+        float4 vv[U][CH];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (c0 + t < k) vv[u][t] = F4Slots::load_stream(V + (c0 + t) * ldv, q0 + u * sw.du, n4, n);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+          if (c0 + t < k) {
+            const float h = -hs[c0 + t];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              x[u].x = fmaf(h, vv[u][t].x, x[u].x);
+              x[u].y = fmaf(h, vv[u][t].y, x[u].y);
+              x[u].z = fmaf(h, vv[u][t].z, x[u].z);
+              x[u].w = fmaf(h, vv[u][t].w, x[u].w);
+            }
+          }
+      }
+    }
+    float sp = 0.f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      F4Slots::store(w_out, q0 + u * sw.du, n4, n, x[u]);
+      sp = dot4(x[u], x[u], sp);
+    }
+    accn += (double)sp;
+  }
+  const double acc[1] = {accn};
+  if (grid_sum<1>(acc, 1, partial, out, ticket)) {   // the block that completed the sum
+    if (threadIdx.x == 0 && next_scale) {
+      const double hn = sqrt(out[0]);
+      *next_scale = hn != 0.0 ? 1.0 / hn : 0.0;
+      *jidx = next_j;
+    }
+    if (step.gm) arnoldi_step_block(step);
+  }
+}
+
+// x (+)= sum_kk y[kk] V[kk] with FP32 columns: the column sum in FP32, one
+// FP64 addition a value (x is the FP64 Newton correction); accumulate 0 writes x
+__global__ void k_combine32(const float* __restrict__ V, int64_t ldv, int k, const double* __restrict__ y,
+                            double* __restrict__ x, int64_t n, int accumulate) {
+  __shared__ float ys[kMaxK];
+  if (threadIdx.x < k) ys[threadIdx.x] = (float)y[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float sp = 0.f;
+    for (int kk = 0; kk < k; ++kk) sp = fmaf(ys[kk], V[kk * ldv + i], sp);
+    x[i] = accumulate ? x[i] + (double)sp : (double)sp;
+  }
+}
+
+// y = (float)(a x): the first Krylov column from the FP64 residual
+__global__ void k_scale32(const double* __restrict__ x, double a, float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)(a * x[i]);
 }
 
 // launch KERNEL<KC, VEC, WT, NEG> with the smallest KC >= k; VEC when every
@@ -537,6 +825,28 @@ static unsigned wave_grid(unsigned grid) {
     else FR_KC_CASES(k, false, grid, KERNEL, WT, NEG, __VA_ARGS__);                                     \
   } while (0)
 
+// the FP32-basis kernels KERNEL<KC, NEG> with the smallest KC >= k
+#define FR_KC32_LAUNCH(KC_, NEG_, grid, KERNEL, ...) \
+  KERNEL<KC_, NEG_><<<wave_grid<KERNEL<KC_, NEG_>>(grid), kRedThreads, 0, s>>>(__VA_ARGS__)
+#define FR_KC32_CASES(k, NEG_, grid, KERNEL, ...)                        \
+  do {                                                                  \
+    if ((k) <= 1) FR_KC32_LAUNCH(1, NEG_, grid, KERNEL, __VA_ARGS__);   \
+    else if ((k) <= 2) FR_KC32_LAUNCH(2, NEG_, grid, KERNEL, __VA_ARGS__); \
+    else if ((k) <= 4) FR_KC32_LAUNCH(4, NEG_, grid, KERNEL, __VA_ARGS__); \
+    else if ((k) <= 8) FR_KC32_LAUNCH(8, NEG_, grid, KERNEL, __VA_ARGS__); \
+    else if ((k) <= 16) FR_KC32_LAUNCH(16, NEG_, grid, KERNEL, __VA_ARGS__); \
+    else if ((k) <= 32) FR_KC32_LAUNCH(32, NEG_, grid, KERNEL, __VA_ARGS__); \
+    else FR_KC32_LAUNCH(64, NEG_, grid, KERNEL, __VA_ARGS__);            \
+  } while (0)
+#define FR_KC32_DISPATCH(k, neg, grid, KERNEL, ...)               \
+  do {                                                           \
+    if (neg) FR_KC32_CASES(k, true, grid, KERNEL, __VA_ARGS__);  \
+    else FR_KC32_CASES(k, false, grid, KERNEL, __VA_ARGS__);     \
+  } while (0)
+
+// smallest GMRES tolerance run with the FP32 Krylov basis
+constexpr double kF32BasisMinRtol = 1e-4;
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // column stride of the Krylov basis: n_dof_capacity rounded up to 32 values,
@@ -549,13 +859,14 @@ __global__ void k_scale(const double* __restrict__ x, double a, double* __restri
 }
 
 // x += sum_kk y[kk] V[kk]   (y on the device)
+// x (+)= sum_kk y[kk] V[kk]; accumulate 0 (the first cycle) writes x
 __global__ void k_combine(const double* __restrict__ V, int64_t ldv, int k, const double* __restrict__ y,
-                          double* __restrict__ x, int64_t n) {
+                          double* __restrict__ x, int64_t n, int accumulate) {
   __shared__ double ys[kMaxK];
   if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = x[i];
+    double s = accumulate ? x[i] : 0.0;
     for (int kk = 0; kk < k; ++kk) s += ys[kk] * V[kk * ldv + i];
     x[i] = s;
   }
@@ -590,7 +901,8 @@ static fr_status multidot(fr_ctx* c, const double* V, int64_t ldv, int k, const 
   const bool vec = aligned16(w) && (!V || (aligned16(V) && ldv % 2 == 0));
   const unsigned g = red_blocks(n);
   FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * ((V ? k : 0) + 1),
-              FR_KC_DISPATCH(kk, vec, g, k_multidot, double, false, V, ldv, kk, w, n, part, dout, ticket_of(c), 0));
+              FR_KC_DISPATCH(kk, vec, g, k_multidot, double, false, V, ldv, kk, w, n, part, dout, ticket_of(c), 0,
+                             nullptr));
   cudaMemcpyAsync(c->h_red, dout, sizeof(double) * (V ? k : 1), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "multidot");
   std::memcpy(out_host, c->h_red, sizeof(double) * (V ? k : 1));
@@ -606,11 +918,13 @@ static fr_status norm2(fr_ctx* c, const double* w, int64_t n, double* out, cudaS
 
 // x = (T)(s_j V[j]) with j = *jidx and s_j = scale[j]: the orthonormal Krylov
 // vector from its stored column (FP32: the scale applied after the rounding)
-template <typename T>
-__global__ void k_gather_col(const double* __restrict__ V, int64_t ld, const int* __restrict__ jidx,
-                             const double* __restrict__ scale, T* __restrict__ x, int64_t n) {
+template <typename T, typename VT>
+__global__ void k_gather_col(const VT* __restrict__ V, int64_t ld, const int* __restrict__ jidx,
+                             const double* __restrict__ scale, T* __restrict__ x, int64_t n,
+                             const int* __restrict__ gate) {
+  if (gate && *gate) return;
   const int j = *jidx;
-  const double* src = V + (int64_t)j * ld;
+  const VT* src = V + (int64_t)j * ld;
   const T sc = (T)scale[j];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = (T)src[i] * sc;
@@ -622,24 +936,41 @@ __global__ void k_gather_col(const double* __restrict__ V, int64_t ld, const int
 // straight into w.  Replayed from a CUDA graph captured on first use and again
 // whenever q, V, w or the timing state changed (the layout and the launch
 // tuning drop it); launched directly when graphs are off or cannot be used.
-static void gather_col(fr_ctx* c, int pi, const double* V, int64_t ld, void* x, int64_t n, cudaStream_t s) {
-  const double nb = (double)n * (8 + (pi ? 4 : 8));
+static void gather_col(fr_ctx* c, int pi, const void* V, bool b32, int64_t ld, void* x, int64_t n, cudaStream_t s) {
+  const double nb = (double)n * ((b32 ? 4 : 8) + (pi ? 4 : 8));
   const double* sc = c->d_red + kOutS;
-  if (pi) FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<float><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, sc, (float*)x, n));
-  else FR_LAUNCH_B(c, "vec", s, nb, k_gather_col<double><<<egrid(n), 256, 0, s>>>(V, ld, c->d_jidx, sc, (double*)x, n));
+  if (b32)
+    FR_LAUNCH_B(c, "vec", s, nb,
+                k_gather_col<float, float><<<egrid(n), 256, 0, s>>>((const float*)V, ld, c->d_jidx, sc, (float*)x, n,
+                                                                   c->gate));
+  else if (pi)
+    FR_LAUNCH_B(c, "vec", s, nb,
+                k_gather_col<float, double><<<egrid(n), 256, 0, s>>>((const double*)V, ld, c->d_jidx, sc, (float*)x,
+                                                                    n, c->gate));
+  else
+    FR_LAUNCH_B(c, "vec", s, nb,
+                k_gather_col<double, double><<<egrid(n), 256, 0, s>>>((const double*)V, ld, c->d_jidx, sc,
+                                                                     (double*)x, n, c->gate));
 }
 
 static void release_graph_timers(fr_ctx* c, int pi) {
-  for (auto& r : c->graph_timers[pi]) {
-    c->timing.pool.push_back(r.a);
-    c->timing.pool.push_back(r.b);
-  }
+  for (auto& r : c->graph_timers[pi]) c->timing.give_back(r);
   c->graph_timers[pi].clear();
 }
 
 // The column index is read from c->d_jidx: the caller sets it (the update
-// of the previous Arnoldi step stores it on the device).
-static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double* V, double* w, cudaStream_t s) {
+// of the previous Arnoldi step stores it on the device).  graph_ok false:
+// direct launches (the device-driven cycle, whose launches carry the gate and
+// need events of their own for every product).  b32: FP32 basis V, and w
+// receives J v in FP32 (the Arnoldi kernels negate it); else FP64 basis and
+// w = -J v in FP64.  col >= 0 (direct launches whose basis has the products'
+// precision): the product reads the stored column u_col itself, no gather
+// runs, and the volume kernel multiplies J u_col by the column's scale s_col
+// read on the device (J is linear; the stored columns are unnormalised, so
+// the scale has to enter: products of u_col alone would grow the next column
+// by |J| every iteration).
+static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const void* V, void* w, cudaStream_t s,
+                               bool graph_ok = true, bool b32 = false, int col = -1) {
   const int pi = op->jv_prec == FR_F64 ? 0 : 1;   // FP32 kernels for FR_F32 and FR_BF16OP
   const fr_prec prec = op->jv_prec;
   const int64_t n = c->n_dof, ld = krylov_ld(c);
@@ -649,11 +980,22 @@ static fr_status exact_product(fr_ctx* c, const fr_shifted_op* op, const double*
   if (!qptr || !x) return FR_ERR_NOMEM;
   collect_graph_timers(c);
   auto direct = [&](cudaStream_t st) -> fr_status {
-    gather_col(c, pi, V, ld, x, n, st);
-    return launch_jvp_prepared_neg64(c, qptr, x, w, prec, st);
+    gather_col(c, pi, V, b32, ld, x, n, st);
+    if (b32) return launch_jvp_prepared(c, qptr, x, w, prec, st);
+    return launch_jvp_prepared_neg64(c, qptr, x, (double*)w, prec, st);
   };
-  if (!c->use_graphs || !c->jvp_graph_ok) return direct(s);
-  const void* timed = c->timing.on ? (const void*)c : nullptr;
+  if (col >= 0 && (b32 ? pi == 1 : pi == 0)) {
+    const void* vcol = b32 ? (const void*)((const float*)V + (int64_t)col * ld)
+                           : (const void*)((const double*)V + (int64_t)col * ld);
+    c->vscale = c->d_red + kOutS + col;
+    const fr_status e = b32 ? launch_jvp_prepared(c, qptr, vcol, w, prec, s)
+                            : launch_jvp_prepared_neg64(c, qptr, vcol, (double*)w, prec, s);
+    c->vscale = nullptr;
+    return e;
+  }
+  if (!graph_ok || !c->use_graphs || !c->jvp_graph_ok) return direct(s);
+  // the graph holds the event nodes of the kernels timed when it was captured
+  const void* timed = c->timing.on ? (const void*)(intptr_t)(1 + c->timing.select_gen) : nullptr;
   const void* key[5] = {qptr, V, w, timed, (const void*)(intptr_t)(prec + 1)};
   if (c->jvp_graph[pi] && std::equal(key, key + 5, c->jvp_graph_key[pi])) {
     if (cudaGraphLaunch(c->jvp_graph[pi], s) != cudaSuccess) {
@@ -769,7 +1111,11 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
     for (int k = 0; k < kMaxK; ++k) c->h_jidx[k] = k;
   }
-  if (!c->d_krylov || c->krylov_m < m) {
+  // FP32 basis: exact FP32 products, no preconditioner, and a tolerance the
+  // FP32 products can meet (the attainable accuracy of both is about 1e-6)
+  const bool b32 = c->f32_basis && op->mode == FR_JV_EXACT && op->jv_prec != FR_F64 && !op->precond &&
+                   o->rtol >= kF32BasisMinRtol;
+  if (!b32 && (!c->d_krylov || c->krylov_m < m)) {
     cudaFree(c->d_krylov);
     c->d_krylov = nullptr;
     if (cudaMalloc(&c->d_krylov, sizeof(double) * (m + 1) * ld) != cudaSuccess) {
@@ -777,6 +1123,16 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       return FR_ERR_NOMEM;
     }
     c->krylov_m = m;
+    clear_graphs(c);
+  }
+  if (b32 && (!c->d_krylov32 || c->krylov32_m < m)) {
+    cudaFree(c->d_krylov32);
+    c->d_krylov32 = nullptr;
+    if (cudaMalloc(&c->d_krylov32, sizeof(float) * (m + 1) * ld) != cudaSuccess) {
+      set_error("gmres_solve: Krylov basis allocation failed");
+      return FR_ERR_NOMEM;
+    }
+    c->krylov32_m = m;
     clear_graphs(c);
   }
   if (op->mode == FR_JV_EXACT && op->jv_prec != FR_F64) {
@@ -797,6 +1153,9 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   // gather in front of the JVP applies s_j.  In the exact modes the JVP's
   // volume kernel writes w = -J v_j in FP64 directly.
   double* V = c->d_krylov;
+  float* V32 = c->d_krylov32;
+  float* w32 = b32 ? vec32(c, 2) : nullptr;   // J v of the FP32 products (the FP32 basis)
+  if (b32 && !w32) return FR_ERR_NOMEM;
   double* w = vec64(c, 4);
   double* r = vec64(c, 5);
   double* xs = vec64(c, 10);   // s_j u_j for the finite-difference product
@@ -805,20 +1164,22 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   double* sh = c->h_red + 3 * kMaxK;   // pinned host copy of the scales
   if (!w || !r || !xs) return FR_ERR_NOMEM;
   std::memset(st, 0, sizeof(*st));
-  cudaMemsetAsync(x, 0, sizeof(double) * n, s);
-  // left preconditioning: GMRES on M^-1 (sigma I - J) x = M^-1 b
+  // x0 = 0: the residual of the first cycle is b (left preconditioning: GMRES
+  // on M^-1 (sigma I - J) x = M^-1 b, so M^-1 b), read in place; the first
+  // combination writes x, later ones add to it
   const bool pc = op->precond != 0;
   double beta0 = pc ? -1.0 : b_norm;
   fr_status e = FR_OK;
-  cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-  if (pc && (e = precond_apply(c, 1.0, r, 0.0, nullptr, r, s)) != FR_OK) return e;
-  if (!(beta0 >= 0.0) && (e = norm2(c, r, n, &beta0, s)) != FR_OK) return e;
+  if (pc && (e = precond_apply(c, 1.0, b, 0.0, nullptr, r, s)) != FR_OK) return e;
+  const double* r0 = pc ? r : b;
+  if (!(beta0 >= 0.0) && (e = norm2(c, r0, n, &beta0, s)) != FR_OK) return e;
   if (!std::isfinite(beta0)) {
     set_error("gmres_solve: non-finite right-hand side");
     return FR_ERR_NONFINITE;
   }
   if (beta0 == 0.0) {
     st->converged = 1;
+    cudaMemsetAsync(x, 0, sizeof(double) * n, s);
     return cuda_check(cudaStreamSynchronize(s), "gmres");
   }
   int it = 0;
@@ -837,18 +1198,133 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   // then w_out = w_in - sum s_i^2 raw_i u_i with ||w_out||^2 into N
   // (the update also stores the scale of the new column and the index of
   // the next product on the device: kk is the new column's index)
-  auto gs_pass = [&](int kk, const double* w_in, double* w_out, double* raw, int with_norm) {
+  auto gs_pass = [&](int kk, const double* w_in, double* w_out, double* raw, int with_norm, StepArgs step) {
     if (c->df_arnoldi)
       FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
                   FR_KC_DISPATCH(kk, vec, grid, k_multidot_df, double, false, V, ld, kk, w_in, n, part, raw, ticket,
-                                 with_norm));
+                                 with_norm, c->gate));
     else
       FR_LAUNCH_B(c, "arnoldi_dot", s, 8.0 * n * (kk + 1),
                   FR_KC_DISPATCH(kk, vec, grid, k_multidot, double, false, V, ld, kk, w_in, n, part, raw, ticket,
-                                 with_norm));
+                                 with_norm, c->gate));
     FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (kk + 2),
                 FR_KC_DISPATCH(kk, vec, grid, k_orth_update, double, false, V, ld, kk, raw, sdev, w_in, w_out, n,
-                               part, c->d_red + kOutN, ticket, sdev + kk, c->d_jidx, kk));
+                               part, c->d_red + kOutN, ticket, sdev + kk, c->d_jidx, kk, c->gate, step));
+  };
+  auto gs_pass32 = [&](int kk, const float* w_in, bool neg, float* w_out, double* raw, int with_norm,
+                       StepArgs step) {
+    FR_LAUNCH_B(c, "arnoldi_dot", s, 4.0 * n * (kk + 1),
+                FR_KC32_DISPATCH(kk, neg, grid, k_multidot32, V32, ld, kk, w_in, n, part, raw, ticket, with_norm,
+                                 c->gate));
+    FR_LAUNCH_B(c, "arnoldi_update", s, 4.0 * n * (kk + 2),
+                FR_KC32_DISPATCH(kk, neg, grid, k_orth_update32, V32, ld, kk, raw, sdev, w_in, w_out, n, part,
+                                 c->d_red + kOutN, ticket, sdev + kk, c->d_jidx, kk, c->gate, step));
+  };
+  // the first Gram-Schmidt pass of column kk, on the product's output; a
+  // further pass works on the new column in place; `step` (device-driven
+  // cycles): the Givens bookkeeping run by the update that ends the iteration
+  auto gs_first = [&](int kk, double* raw, int with_norm, StepArgs step = {}) {
+    if (b32) gs_pass32(kk, w32, true, V32 + (int64_t)kk * ld, raw, with_norm, step);
+    else gs_pass(kk, w, V + (int64_t)kk * ld, raw, with_norm, step);
+  };
+  auto gs_again = [&](int kk, double* raw, StepArgs step = {}) {
+    if (b32) gs_pass32(kk, V32 + (int64_t)kk * ld, false, V32 + (int64_t)kk * ld, raw, 0, step);
+    else gs_pass(kk, V + (int64_t)kk * ld, V + (int64_t)kk * ld, raw, 0, step);
+  };
+  const void* Vb = b32 ? (const void*)V32 : (const void*)V;
+  void* wb = b32 ? (void*)w32 : (void*)w;
+  // Device-driven cycle (exact products, one or two Gram-Schmidt passes): the
+  // host launches the Arnoldi iterations in batches without waiting between
+  // them.  Each iteration is the product, the preconditioner and the
+  // Gram-Schmidt pass(es); the block that completes the last update keeps the
+  // Hessenberg column, the Givens rotations and the residual estimate on the
+  // device (arnoldi_step_block) and closes the gate when the cycle has
+  // converged; every later launch of the batch then returns at entry.  The
+  // host reads the cycle state once per batch.  A launch past the gate still
+  // costs its grid's start-up (about 20 us for a volume kernel of 32,768
+  // CTAs against a few us of host round trip), so the first batch is one
+  // iteration shorter than the previous cycle and later batches are single
+  // iterations.  Timing records of launches past the gate are dropped, so the
+  // per-kernel counts hold only iterations that ran.
+  const bool dev = c->device_gmres && exact && o->reorth != 1;
+  auto drop_timers_from = [&](int64_t mark_p, long long mark_l) {
+    auto& pend = c->timing.pending;
+    for (int64_t i = mark_p; i < (int64_t)pend.size(); ++i) c->timing.give_back(pend[i]);
+    if ((int64_t)pend.size() > mark_p) pend.resize(mark_p);
+    c->timing.launches = mark_l;
+  };
+  auto device_cycle = [&](double beta, int& k, double& res_out) -> fr_status {
+    if (!c->d_gm) {
+      if (cudaMalloc(&c->d_gm, sizeof(double) * kGmSize) != cudaSuccess) return FR_ERR_NOMEM;
+      if (cudaMallocHost(&c->h_gm, sizeof(double) * kGmSize) != cudaSuccess) return FR_ERR_NOMEM;
+    }
+    double* gm = c->d_gm;
+    int* ctl = reinterpret_cast<int*>(gm + kGmCtl);
+    const int* hctl = reinterpret_cast<const int*>(c->h_gm + kGmCtl);
+    c->h_gm[kGmG] = beta;
+    cudaMemcpyAsync(gm + kGmG, c->h_gm + kGmG, sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(ctl, 0, 2 * sizeof(double), s);
+    const int jmax = std::min(m, o->max_it - it);
+    std::vector<int64_t> mark_p(m + 1, 0);
+    std::vector<long long> mark_l(m + 1, 0);
+    int batch = std::max(1, std::min(jmax, c->gm_last_k - 1));
+    // products straight from the stored columns when the basis has the
+    // products' precision (no gather; the volume kernel applies the scale)
+    const bool direct_col = b32 ? op->jv_prec != FR_F64 : op->jv_prec == FR_F64;
+    int j = 0;
+    fr_status ee = FR_OK;
+    k = 0;
+    while (true) {
+      const int jend = std::min(jmax, j + batch);
+      c->gate = ctl;
+      for (; j < jend && ee == FR_OK; ++j) {
+        mark_p[j] = (int64_t)c->timing.pending.size();
+        mark_l[j] = c->timing.launches;
+        if (j == 0) cudaMemcpyAsync(c->d_jidx, c->h_jidx, sizeof(int), cudaMemcpyHostToDevice, s);
+        if ((ee = exact_product(c, op, Vb, wb, s, false, b32, direct_col ? j : -1)) != FR_OK) break;
+        if (pc && (ee = precond_apply(c, 1.0, w, op->sigma, V + (int64_t)j * ld, w, s, ctl, sdev + j)) != FR_OK) break;
+        const int kk = j + 1;
+        StepArgs step;
+        step.gm = gm;
+        step.dots1 = c->d_red + kOutH1;
+        step.dots2 = c->d_red + kOutH2;
+        step.scale = sdev;
+        step.nrm2 = c->d_red + kOutN;
+        step.shift = pc ? 0.0 : op->sigma;
+        step.tol = o->rtol * beta0;
+        step.j = j;
+        step.last = it + kk >= o->max_it;
+        step.two_pass = o->reorth == 2;
+        if (o->reorth == 2) {
+          gs_first(kk, c->d_red + kOutH1, 0);
+          gs_again(kk, c->d_red + kOutH2, step);
+        } else {
+          gs_first(kk, c->d_red + kOutH1, 0, step);
+        }
+      }
+      c->gate = nullptr;
+      if (ee != FR_OK) return ee;
+      mark_p[j] = (int64_t)c->timing.pending.size();
+      mark_l[j] = c->timing.launches;
+      cudaMemcpyAsync(c->h_gm, gm, sizeof(double) * kGmSize, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(sh, sdev, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
+      k = hctl[1];
+      if (k < j) drop_timers_from(mark_p[k], mark_l[k]);
+      if (hctl[2]) {
+        set_error("gmres_solve: non-finite Arnoldi vector");
+        return FR_ERR_NONFINITE;
+      }
+      if (hctl[0] || j >= jmax) break;
+      batch = 1;
+    }
+    c->gm_last_k = std::max(1, k);
+    // the rotated Hessenberg (row-major, as the host-driven cycle keeps it) and g
+    for (int jj = 0; jj < k; ++jj)
+      for (int i = 0; i <= jj; ++i) H[i * m + jj] = c->h_gm[kGmH + (int64_t)jj * kMaxK + i];
+    for (int i = 0; i <= k; ++i) g[i] = c->h_gm[kGmG + i];
+    res_out = std::fabs(g[k]);
+    return FR_OK;
   };
   bool first = true;
   while (true) {
@@ -864,18 +1340,24 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       res = beta;
       break;
     }
-    FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(r, 1.0 / beta, V, n));
+    const double* rc = st->restarts == 0 ? r0 : r;
+    if (b32) FR_LAUNCH_B(c, "vec", s, 12.0 * n, k_scale32<<<egrid(n), 256, 0, s>>>(rc, 1.0 / beta, V32, n));
+    else FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(rc, 1.0 / beta, V, n));
     set_scale(0, 1.0);
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
     res = beta;
-    for (int j = 0; j < m; ++j) {
+    if (dev) {
+      if ((e = device_cycle(beta, k, res)) != FR_OK) return e;
+      it += k;
+    }
+    for (int j = 0; !dev && j < m; ++j) {
       // product w = -J v_j
       if (exact) {
         if (j == 0) cudaMemcpyAsync(c->d_jidx, c->h_jidx, sizeof(int), cudaMemcpyHostToDevice, s);
-        if ((e = exact_product(c, op, V, w, s)) != FR_OK) return e;
+        if ((e = exact_product(c, op, Vb, wb, s, true, b32)) != FR_OK) return e;
       } else {
         FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(V + (int64_t)j * ld, sh[j], xs, n));
         if ((e = apply_op(c, op, R0, xs, w, s, false)) != FR_OK) return e;
@@ -889,9 +1371,8 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
       // new column u_{j+1}, the second works on it in place.
       const int kk = j + 1;
       const int ro = o->reorth;
-      double* unew = V + (int64_t)(j + 1) * ld;
-      gs_pass(kk, w, unew, c->d_red + kOutH1, ro == 1 ? 1 : 0);
-      if (ro == 2) gs_pass(kk, unew, unew, c->d_red + kOutH2, 0);
+      gs_first(kk, c->d_red + kOutH1, ro == 1 ? 1 : 0);
+      if (ro == 2) gs_again(kk, c->d_red + kOutH2);
       cudaMemcpyAsync(c->h_red, c->d_red + kOutH1, sizeof(double) * 3 * kMaxK, cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
       for (int i = 0; i <= j; ++i) {
@@ -899,7 +1380,7 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
         h2[i] = ro == 2 ? sh[i] * c->h_red[kMaxK + i] : 0.0;
       }
       if (ro == 1 && std::sqrt(c->h_red[2 * kMaxK]) < 0.7 * std::sqrt(c->h_red[kk])) {
-        gs_pass(kk, unew, unew, c->d_red + kOutH2, 0);
+        gs_again(kk, c->d_red + kOutH2);
         cudaMemcpyAsync(c->h_red + kMaxK, c->d_red + kOutH2, sizeof(double) * 2 * kMaxK, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "gmres");
         for (int i = 0; i <= j; ++i) h2[i] = sh[i] * c->h_red[kMaxK + i];
@@ -942,7 +1423,13 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     // x += sum_i y_i v_i = sum_i (y_i s_i) u_i
     for (int i = 0; i < k; ++i) y[i] *= sh[i];
     cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
-    FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (k + 2), k_combine<<<egrid(n), 256, 0, s>>>(V, ld, k, ydev, x, n));
+    const int acc = st->restarts > 0;
+    if (b32)
+      FR_LAUNCH_B(c, "arnoldi_update", s, 4.0 * n * k + (acc ? 16.0 : 8.0) * n,
+                  k_combine32<<<egrid(n), 256, 0, s>>>(V32, ld, k, ydev, x, n, acc));
+    else
+      FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (k + (acc ? 2 : 1)),
+                  k_combine<<<egrid(n), 256, 0, s>>>(V, ld, k, ydev, x, n, acc));
     st->restarts += 1;
     if (res <= o->rtol * beta0) {
       st->converged = 1;

@@ -1,6 +1,10 @@
 // Per-launch instrumentation: a launch counter that is always kept, and,
 // when enabled, a pair of CUDA events recorded on the launch stream around
-// every kernel so that per-kernel device time can be read after a sync.
+// every kernel so that per-kernel device time can be read after a sync.  A
+// selection of kernel names restricts the events to those kernels (the
+// others are only counted): each event pair adds two stream operations around
+// its kernel, so a step instrumented everywhere runs slower than the work it
+// measures.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,7 +19,7 @@ namespace frgb {
 
 struct TimerRec {
   const char* name;
-  cudaEvent_t a, b;
+  cudaEvent_t a, b;        // null for a launch that is only counted
   double bytes, flops;
 };
 
@@ -31,6 +35,8 @@ struct Timing {
   bool capture = false;     // launches are being captured into a CUDA graph
   int64_t mark = 0;         // pending.size() when the current capture began
   long long launches = 0;
+  std::vector<std::string> select;   // names whose launches get events (empty: all)
+  int select_gen = 0;                // bumped on every change of the selection
   std::vector<cudaEvent_t> pool;
   std::vector<TimerRec> pending;
   std::map<std::string, TimerAcc> acc;
@@ -44,38 +50,43 @@ struct Timing {
     }
     return e;
   }
-  void collect() {
-    for (auto& r : pending) {
-      float ms = 0.f;
+  bool selected(const char* name) const {
+    if (select.empty()) return true;
+    for (const auto& n : select)
+      if (n == name) return true;
+    return false;
+  }
+  void give_back(const TimerRec& r) {
+    if (r.a) pool.push_back(r.a);
+    if (r.b) pool.push_back(r.b);
+  }
+  void add(const TimerRec& r) {
+    float ms = 0.f;
+    if (r.a) {
       cudaEventSynchronize(r.b);
       cudaEventElapsedTime(&ms, r.a, r.b);
-      auto& x = acc[r.name];
-      x.ms += ms;
-      x.count += 1;
-      x.bytes += r.bytes;
-      x.flops += r.flops;
-      pool.push_back(r.a);
-      pool.push_back(r.b);
+    }
+    auto& x = acc[r.name];
+    x.ms += ms;
+    x.count += 1;
+    x.bytes += r.bytes;
+    x.flops += r.flops;
+  }
+  void collect() {
+    for (auto& r : pending) {
+      add(r);
+      give_back(r);
     }
     pending.clear();
   }
   // Accumulate the timers of one replay of a graph (the events belong to the graph).
   void accumulate(const std::vector<TimerRec>& recs) {
-    for (const auto& r : recs) {
-      float ms = 0.f;
-      cudaEventSynchronize(r.b);
-      cudaEventElapsedTime(&ms, r.a, r.b);
-      auto& x = acc[r.name];
-      x.ms += ms;
-      x.count += 1;
-      x.bytes += r.bytes;
-      x.flops += r.flops;
-    }
+    for (const auto& r : recs) add(r);
   }
   ~Timing() {
     for (auto& r : pending) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
+      if (r.a) cudaEventDestroy(r.a);
+      if (r.b) cudaEventDestroy(r.b);
     }
     for (auto e : pool) cudaEventDestroy(e);
   }
@@ -93,7 +104,7 @@ struct LaunchScope {
   LaunchScope(fr_ctx* c, const char* n, cudaStream_t st, double b = 0.0, double f = 0.0)
       : t(timing_of(c)), name(n), s(st), bytes(b), flops(f) {
     ++t.launches;
-    if (t.on) {
+    if (t.on && t.selected(n)) {
       a = t.take();
       record(a);
     }
@@ -105,8 +116,11 @@ struct LaunchScope {
   }
   ~LaunchScope() {
     if (t.on) {
-      cudaEvent_t b = t.take();
-      record(b);
+      cudaEvent_t b = nullptr;
+      if (a) {
+        b = t.take();
+        record(b);
+      }
       t.pending.push_back(TimerRec{name, a, b, bytes, flops});
     }
   }

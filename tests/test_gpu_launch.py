@@ -136,8 +136,10 @@ def test_autotune_keeps_parity(built, works, name):
 @pytest.mark.parametrize("jv_dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("name", ["vortex2d_mixed_p1-4", "tgv_5^3_p3"])
 def test_graph_arnoldi_matches_direct(built, works, name, jv_dtype):
-    """GMRES with the Arnoldi product replayed from a CUDA graph and with direct
-    launches: same iterations, same solution bit for bit, across three solves
+    """Host-driven GMRES (one round trip per iteration; the device-driven cycle
+    always launches directly) with the Arnoldi product replayed from a CUDA
+    graph and with direct launches: same iterations, same solution bit for
+    bit, across three solves
     (timing off, then on twice: turning it on recaptures the graph with event
     nodes, the third solve replays it).  The timed JVP volume launches count
     every product, replayed ones included: the same number as with direct
@@ -150,7 +152,7 @@ def test_graph_arnoldi_matches_direct(built, works, name, jv_dtype):
     sigma = 1.0 / (0.4358665215 * 0.01)
     res, counts = {}, {}
     for graphs in (False, True):
-        ctx.set_tuning({"graphs": graphs})
+        ctx.set_tuning({"graphs": graphs, "device_gmres": False})
         runs = []
         for timing in (False, True, True):
             ctx.timing(timing)
@@ -250,3 +252,30 @@ def test_work_weight_models_do_not_change_results(built, works, name):
         bad = [0] * 42
         bad[1] = 4
         ctx.set_tuning({"epb": bad})
+
+
+def test_timing_select(built, works):
+    """With a selection only the named kernels carry event pairs (device time
+    above zero); every launch is still counted, with the same counts, bytes
+    and launch total as with every kernel timed."""
+    m, q, ph = works["tgv_5^3_p3"]
+    ctx = gpu_ctx(m, ph)
+    q64 = ctx.pack(torch.from_numpy(generic_state(q)).cuda())
+    q32, v32 = q64.float(), ctx.pack(torch.from_numpy(cases.uniform(306, q.size) - 0.5).cuda()).float()
+    out = {}
+    for sel in (None, ["vol_jvp_f32"]):
+        ctx.timing_select(sel)
+        ctx.timing(True)
+        ctx.residual(q64)
+        for _ in range(2):
+            ctx.jvp(q32, v32)
+        rep, n = ctx.timing_report()
+        ctx.timing(False)
+        out[sel is None] = ({k: (v[0], v[2]) for k, v in rep.items()}, n)
+        if sel:
+            assert rep["vol_jvp_f32"][0] == 2 and rep["vol_jvp_f32"][1] > 0
+            assert all(v[1] == 0.0 for k, v in rep.items() if k != "vol_jvp_f32"), rep
+        else:
+            assert all(v[1] > 0.0 for v in rep.values()), rep
+    ctx.timing_select(None)
+    assert out[True] == out[False]

@@ -180,3 +180,109 @@ def test_arnoldi_slot_walks_agree(built):
         out[runs] = (x.cpu().numpy(), st["iterations"])
     assert out[True][1] == out[False][1]
     assert np.abs(out[True][0] - out[False][0]).max() <= 1e-12 * np.abs(out[False][0]).max()
+
+
+def _set_flag(ctx, key, value):
+    t = ctx.tuning()
+    t[key] = value
+    ctx.set_tuning(t)
+
+
+@pytest.mark.parametrize("name,jv,reorth,pc", [
+    ("tgv_5^3_p3", torch.float64, 0, False),
+    ("tgv_5^3_p3", torch.float32, 2, False),
+    ("diff_3^3_p4_mu0.05", torch.float32, 0, False),
+    ("cylinder_4x12x2_mixed", torch.float64, 0, True),
+    ("box_mixed_p4-5_ns", torch.float32, 0, True)])
+def test_device_gmres_matches_host_driven(built, name, jv, reorth, pc):
+    """GMRES with the Givens rotations and the convergence test on the device
+    (iterations launched in batches, the default) against one host round trip
+    per iteration: the products and Gram-Schmidt passes are the same kernels,
+    so the iteration and restart counts agree and x agrees to rounding, with
+    restarts (m = 8), one or two passes, and the element-Jacobi
+    preconditioner (its column scale then read on the device; the blocks are
+    rebuilt after the tuning change, which drops them).  Tolerances the
+    products can meet: 1e-9 with FP64 products, 1e-5 with FP32 ones (below
+    1e-4 the basis stays FP64); FP32 products after a restart start from a
+    true residual that carries their rounding, so the final residual
+    estimates agree to 1e-2 there and to 1e-6 with FP64 products."""
+    m, q, ph = WL[name]
+    ctx = gpu_ctx(m, ph)
+    qs = ctx.pack(torch.from_numpy(generic_state(q)).cuda())
+    b = ctx.pack(torch.from_numpy(cases.uniform(917, q.size) - 0.5).cuda())
+    sigma = 40.0 if name.startswith("tgv") else 500.0
+    rtol = 1e-9 if jv == torch.float64 else 1e-5
+    out = {}
+    for dev in (False, True):
+        _set_flag(ctx, "device_gmres", dev)
+        if pc:
+            ctx.precond_build(qs, sigma)
+        x, st = ctx.gmres(qs, b, sigma, mode="exact", jv_dtype=jv, m=8, rtol=rtol, max_it=400, reorth=reorth,
+                          precond=pc)
+        assert st["converged"], (dev, st)
+        out[dev] = (x.cpu().numpy(), st)
+    assert out[True][1]["iterations"] == out[False][1]["iterations"]
+    assert out[True][1]["restarts"] == out[False][1]["restarts"]
+    rtol_res = 1e-6 if jv == torch.float64 else 1e-2
+    assert abs(out[True][1]["rel_res"] - out[False][1]["rel_res"]) <= rtol_res * out[False][1]["rel_res"] + 1e-13
+    x0 = out[False][0]
+    tol = 1e-10 if jv == torch.float64 else 1e-5
+    assert np.abs(out[True][0] - x0).max() <= tol * np.abs(x0).max()
+
+
+def test_device_gmres_batch_past_convergence(built):
+    """A first batch longer than the cycle needs (the previous cycle ran 30
+    iterations): the launches past convergence return at entry, leave x as
+    the host-driven loop computes it, and their timing records are dropped,
+    so the per-kernel launch counts equal the iterations that ran."""
+    m, q, ph = WL["tgv_5^3_p3"]
+    ctx = gpu_ctx(m, ph)
+    qs = ctx.pack(torch.from_numpy(generic_state(q)).cuda())
+    b = ctx.pack(torch.from_numpy(cases.uniform(918, q.size) - 0.5).cuda())
+    kw = dict(mode="exact", jv_dtype=torch.float32, m=30)
+    _, st_long = ctx.gmres(qs, b, 40.0, rtol=1e-14, max_it=30, **kw)
+    assert st_long["iterations"] == 30
+    ctx.timing(True)
+    x, st = ctx.gmres(qs, b, 40.0, rtol=1e-1, max_it=100, **kw)
+    rep, _ = ctx.timing_report()
+    ctx.timing(False)
+    its = st["iterations"]
+    assert st["converged"] and 1 <= its < 29, st
+    products = sum(rep.get(k, (0,))[0] for k in ("vol_jvp_f32", "fused_jvp_f32"))
+    assert products == its, (products, its)
+    # + the norm of b before the cycle, + the final combination x += V y
+    assert rep["arnoldi_dot"][0] == its + 1 and rep["arnoldi_update"][0] == its + 1
+    _set_flag(ctx, "device_gmres", False)
+    xh, sth = ctx.gmres(qs, b, 40.0, rtol=1e-1, max_it=100, **kw)
+    assert sth["iterations"] == its
+    xh = xh.cpu().numpy()
+    assert np.abs(x.cpu().numpy() - xh).max() <= 1e-6 * np.abs(xh).max()
+
+
+@pytest.mark.parametrize("name,m,rtol", [("tgv_5^3_p3", 30, 1e-1), ("tgv_5^3_p3", 8, 1e-4),
+                                         ("diff_3^3_p4_mu0.05", 30, 1e-2), ("vortex2d_mixed_p1-4", 8, 1e-4),
+                                         ("box_mixed_p4-5_ns", 30, 1e-1)])
+def test_f32_basis_matches_f64_basis(built, name, m, rtol):
+    """GMRES with FP32 products and the Krylov basis stored in FP32 (dots and
+    norms summed in FP32 over 16 values, FP64 beyond; the default for such
+    products at rtol >= 1e-4) against the FP64 basis, both device-driven and
+    host-driven: the same Krylov space to about 1e-6, so the iteration counts
+    agree within one and x to 1e-4 of max|x|, with and without restarts, on
+    one and on several degree buckets, and on a vector whose length is not a
+    multiple of four (the 3^3 p = 4 box: 16,875 values)."""
+    mm, q, ph = WL[name]
+    ctx = gpu_ctx(mm, ph)
+    qs = ctx.pack(torch.from_numpy(generic_state(q)).cuda())
+    b = ctx.pack(torch.from_numpy(cases.uniform(919, q.size) - 0.5).cuda())
+    out = {}
+    for dev in (True, False):
+        for b32 in (True, False):
+            _set_flag(ctx, "device_gmres", dev)
+            _set_flag(ctx, "f32_basis", b32)
+            x, st = ctx.gmres(qs, b, 40.0, mode="exact", jv_dtype=torch.float32, m=m, rtol=rtol, max_it=400)
+            assert st["converged"], (dev, b32, st)
+            out[dev, b32] = (x.cpu().numpy(), st["iterations"])
+    x0, i0 = out[False, False]
+    for key, (x, its) in out.items():
+        assert abs(its - i0) <= 1, (key, its, i0)
+        assert np.abs(x - x0).max() <= 1e-4 * np.abs(x0).max(), key
