@@ -880,12 +880,23 @@ __global__ void k_shift(double sigma, const double* __restrict__ v, const T* __r
     out[i] = sigma * v[i] - (double)J[i];
 }
 
-// F = -q / (w dt) + R + rhs   (R in FP64 or FP32)
+// F = -q / (w dt) + R + rhs (R in FP64 or FP32) and ||F||^2 summed on the
+// way (FP64, the deterministic grid reduction into out[0]): the stage
+// residual and its norm in one pass
 template <typename T>
-__global__ void k_stage_F(const double* __restrict__ q, const T* __restrict__ R,
-                          const double* __restrict__ rhs, double inv_wdt, double* __restrict__ F, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    F[i] = -q[i] * inv_wdt + (double)R[i] + rhs[i];
+__global__ void __launch_bounds__(kRedThreads) k_stage_F_norm(const double* __restrict__ q, const T* __restrict__ R,
+                                                               const double* __restrict__ rhs, double inv_wdt,
+                                                               double* __restrict__ F, int64_t n,
+                                                               double* __restrict__ partial, double* __restrict__ out,
+                                                               unsigned* __restrict__ ticket) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double f = -q[i] * inv_wdt + (double)R[i] + rhs[i];
+    F[i] = f;
+    acc = fma(f, f, acc);
+  }
+  const double a1[1] = {acc};
+  grid_sum<1>(a1, 1, partial, out, ticket);
 }
 
 static unsigned egrid(int64_t n) {
@@ -1092,9 +1103,13 @@ static fr_status apply_op(fr_ctx* c, const fr_shifted_op* op, const double* R0, 
 // b_norm: ||b|| when the caller already has it, else negative.
 // sync_at_end: return only when x is complete (the public call); the stage
 // passes false and lets its next residual overlap the final combination.
+// add_to (optional): when the first cycle converges, the combination adds
+// V y to *add_to instead of writing x (x is then left as it was) and
+// *applied is set; otherwise x is written as usual.
 static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0, const double* b, double* x,
                             const fr_gmres_opts* o, fr_gmres_stats* st, cudaStream_t s, double b_norm = -1.0,
-                            bool sync_at_end = true) {
+                            bool sync_at_end = true, double* add_to = nullptr, bool* applied = nullptr) {
+  if (applied) *applied = false;
   const int m = o->m;
   const int64_t n = c->n_dof, ld = krylov_ld(c);
   if (m < 1 || m + 1 > kMaxK || o->max_it < 1 || !(o->rtol > 0.0) || o->reorth < 0 || o->reorth > 2) {
@@ -1423,13 +1438,18 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     // x += sum_i y_i v_i = sum_i (y_i s_i) u_i
     for (int i = 0; i < k; ++i) y[i] *= sh[i];
     cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
-    const int acc = st->restarts > 0;
+    // the first cycle converged and the caller wants the correction added to
+    // its vector: one pass, x untouched
+    const bool direct = add_to && st->restarts == 0 && res <= o->rtol * beta0;
+    double* dst = direct ? add_to : x;
+    const int acc = direct || st->restarts > 0;
     if (b32)
       FR_LAUNCH_B(c, "arnoldi_update", s, 4.0 * n * k + (acc ? 16.0 : 8.0) * n,
-                  k_combine32<<<egrid(n), 256, 0, s>>>(V32, ld, k, ydev, x, n, acc));
+                  k_combine32<<<egrid(n), 256, 0, s>>>(V32, ld, k, ydev, dst, n, acc));
     else
       FR_LAUNCH_B(c, "arnoldi_update", s, 8.0 * n * (k + (acc ? 2 : 1)),
-                  k_combine<<<egrid(n), 256, 0, s>>>(V, ld, k, ydev, x, n, acc));
+                  k_combine<<<egrid(n), 256, 0, s>>>(V, ld, k, ydev, dst, n, acc));
+    if (direct) *applied = true;
     st->restarts += 1;
     if (res <= o->rtol * beta0) {
       st->converged = 1;
@@ -1532,20 +1552,28 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
   float* R32 = low32 ? vec32(c, 2) : nullptr;
   if (low32 && (!q32 || !R32)) return FR_ERR_NOMEM;
   bool low = mixedF;
+  const unsigned rgrid = red_blocks(n);
+  double* nout = c->d_red + kOutH1;
   auto evalF = [&](double* norm) -> fr_status {
     fr_status ee;
     if (low && low32) {
       vcast_f64_f32(c, qi_dev, q32, n, s);
       if ((ee = launch_residual(c, q32, R32, FR_F32, s)) != FR_OK) return ee;
-      FR_LAUNCH_B(c, "vec", s, 28.0 * n, k_stage_F<float><<<egrid(n), 256, 0, s>>>(qi_dev, R32, rhs, inv_wdt, F, n));
+      FR_LAUNCH_B(c, "vec", s, 28.0 * n,
+                  k_stage_F_norm<float><<<rgrid, kRedThreads, 0, s>>>(qi_dev, R32, rhs, inv_wdt, F, n, c->d_red, nout,
+                                                                       ticket_of(c)));
       st->low_evaluations += 1;
     } else {
       if ((ee = launch_residual(c, qi_dev, R, low ? FR_DF : FR_F64, s)) != FR_OK) return ee;
-      FR_LAUNCH_B(c, "vec", s, 32.0 * n, k_stage_F<double><<<egrid(n), 256, 0, s>>>(qi_dev, R, rhs, inv_wdt, F, n));
+      FR_LAUNCH_B(c, "vec", s, 32.0 * n,
+                  k_stage_F_norm<double><<<rgrid, kRedThreads, 0, s>>>(qi_dev, R, rhs, inv_wdt, F, n, c->d_red, nout,
+                                                                        ticket_of(c)));
       if (low) st->low_evaluations += 1;
       else st->f64_evaluations += 1;
     }
-    if ((ee = norm2(c, F, n, norm, s)) != FR_OK) return ee;
+    cudaMemcpyAsync(c->h_red, nout, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "stage residual");
+    *norm = std::sqrt(c->h_red[0]);
     if (!std::isfinite(*norm)) {
       set_error("esdirk_stage: non-finite stage residual");
       return FR_ERR_NONFINITE;
@@ -1576,15 +1604,16 @@ fr_status esdirk_stage(fr_ctx* c, const fr_tableau* tab, int32_t stage, double d
     }
     if (norm_prev > 0.0) dtau = std::min(dtau * norm_prev / norm, o->dtau_max);
     fr_gmres_stats gs;
+    bool applied = false;   // the solve added its correction to q itself
     for (int h = 0; h <= o->max_halvings; ++h) {
       op.sigma = inv_wdt + 1.0 / dtau;
-      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s, norm, false)) != FR_OK) return e;
+      if ((e = gmres_impl(c, &op, R, F, dq, &o->gmres, &gs, s, norm, false, qi_dev, &applied)) != FR_OK) return e;
       st->gmres_iterations += gs.iterations;
       if (gs.converged) break;
       dtau *= 0.5;
       st->halvings += 1;
     }
-    vaxpby(c, 1.0, dq, 1.0, qi_dev, n, s);
+    if (!applied) vaxpby(c, 1.0, dq, 1.0, qi_dev, n, s);
     norm_prev = norm;
     if ((e = evalF(&norm)) != FR_OK) return e;
     st->newton_iterations += 1;
