@@ -226,9 +226,18 @@ typedef struct {
 
 /* Restarted GMRES(m) (Sec. 2.3: the matrix-free Krylov solve of the
  * linearised pseudo-transient system, Eq. linearized_pseudo_transient_final)
- * from x = 0 in FP64: classical Gram-Schmidt as opts->reorth says, Givens
- * rotations on the host.  b, x: device FP64, n_dof.  One host
- * synchronisation per Arnoldi iteration. */
+ * from x = 0: classical Gram-Schmidt as opts->reorth says, Givens rotations.
+ * b, x: device FP64, n_dof, distinct buffers (b is read during the first
+ * cycle).
+ *  - Exact products with one or two Gram-Schmidt passes run device-driven
+ *    (FR_TUNE_DEVICE_GMRES, the default). The rotations and the convergence
+ *    test happen on the device; the host launches the Arnoldi iterations in
+ *    batches and synchronises once per batch; launches past convergence
+ *    return at entry.
+ *  - Otherwise (finite-difference products, the DGKS second pass, or the
+ *    flag off), the host synchronises once per Arnoldi iteration.
+ *  - The Krylov basis is FP64, or FP32 with FP32 products at rtol >= 1e-4
+ *    (FR_TUNE_F32_BASIS). */
 fr_status gmres_solve(fr_ctx* ctx, const fr_shifted_op* op, const double* b_dev, double* x_dev,
                       const fr_gmres_opts* opts, fr_gmres_stats* stats, void* stream);
 
@@ -429,13 +438,13 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
                                    return at entry (the default; off: one
                                    host round trip per iteration, products
                                    replayed from a CUDA graph)               */
-#define FR_TUNE_F32_BASIS 256   /* GMRES with exact FP32 products, no
-                                   preconditioner and rtol >= 1e-4: the
-                                   Krylov basis and the products stored in
-                                   FP32, the dots and norms summed in FP32
-                                   over 16 values and in FP64 beyond (about
-                                   1e-6 relative, the products' own accuracy;
-                                   the default; off: FP64 basis)            */
+#define FR_TUNE_F32_BASIS 256   /* GMRES with exact FP32 products and
+                                   rtol >= 1e-4: the Krylov basis, the
+                                   products and the preconditioned vectors
+                                   stored in FP32, the dots and norms summed
+                                   in FP32 over 16 values and in FP64 beyond
+                                   (about 1e-6 relative, the products' own
+                                   accuracy; the default; off: FP64 basis)  */
 fr_status fr_autotune(fr_ctx* ctx, const double* q64_dev, void* stream);
 fr_status fr_tuning_get(const fr_ctx* ctx, int32_t* table, int32_t* flags);
 fr_status fr_tuning_set(fr_ctx* ctx, const int32_t* table, int32_t flags);

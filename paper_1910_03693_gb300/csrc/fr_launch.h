@@ -52,6 +52,9 @@ fr_status launch_jvp_prepared_neg64(fr_ctx* c, const void* q, const void* v, dou
 // (optional): the launches return at entry when *gate is set (gate_closed).
 fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s,
                         const int* gate = nullptr, const double* bscale = nullptr);
+// The same on FP32 vectors (the FP32 Krylov basis).
+fr_status precond_apply(fr_ctx* c, double a, const float* w, double b, const float* u, float* z, cudaStream_t s,
+                        const int* gate = nullptr, const double* bscale = nullptr);
 
 // Jv = (R(q + eps v) - R0) / eps in FP64; R0 = R(q) is computed when null.
 fr_status launch_fd_jv(fr_ctx* c, const double* q, const double* v, double* Jv, double eps,

@@ -337,10 +337,12 @@ static size_t pc_blocked_smem(int nb) {
 
 // z_e = M_e^-1 (a w_e + b u_e) for blocks of more than 256 rows: one CTA per
 // element, the rows strided over its threads (coalesced column-major reads).
+// The vectors are FP64 or FP32 (VT; the FP32 Krylov basis), the sums FP32.
+template <typename VT>
 __global__ void __launch_bounds__(256) k_pc_apply_big(const float* __restrict__ B, const int64_t* __restrict__ pc_off,
                                                       const int64_t* __restrict__ state_off, int slot_begin, int nb,
-                                                      double a, const double* w, double b,
-                                                      const double* __restrict__ u, double* z, double inv_sigma,
+                                                      double a, const VT* w, double b,
+                                                      const VT* __restrict__ u, VT* z, double inv_sigma,
                                                       const int* __restrict__ gate, const double* __restrict__ bscale) {
   extern __shared__ __align__(16) float xs[];   // [nb]
   if (gate && *gate) return;
@@ -350,28 +352,29 @@ __global__ void __launch_bounds__(256) k_pc_apply_big(const float* __restrict__ 
   double xv[kPcMax / 256 + 1];
   int nr = 0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x, ++nr) {
-    xv[nr] = a * w[base + i] + (u ? b * u[base + i] : 0.0);
+    xv[nr] = a * (double)w[base + i] + (u ? b * (double)u[base + i] : 0.0);
     xs[i] = (float)xv[nr];
   }
   __syncthreads();
   nr = 0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x, ++nr) {
     if (off < 0) {
-      z[base + i] = xv[nr] * inv_sigma;
+      z[base + i] = (VT)(xv[nr] * inv_sigma);
       continue;
     }
     const float* Bc = B + off;
     float acc = 0.0f;
     for (int j = 0; j < nb; ++j) acc = fmaf(Bc[(int64_t)j * nb + i], xs[j], acc);
-    z[base + i] = (double)acc;
+    z[base + i] = (VT)acc;
   }
 }
 
 // z_e = M_e^-1 (a w_e + b u_e); epb elements per CTA, one thread per row.
 // Elements without a stored block (pc_off < 0): z_e = (a w_e + b u_e) / sigma.
+template <typename VT>
 __global__ void k_pc_apply(const float* __restrict__ B, const int64_t* __restrict__ pc_off,
                            const int64_t* __restrict__ state_off, int slot_begin, int count, int nb, int epb,
-                           double a, const double* w, double b, const double* __restrict__ u, double* z,
+                           double a, const VT* w, double b, const VT* __restrict__ u, VT* z,
                            double inv_sigma, const int* __restrict__ gate, const double* __restrict__ bscale) {
   extern __shared__ __align__(16) float xs[];   // [epb][nb]
   if (gate && *gate) return;
@@ -385,32 +388,33 @@ __global__ void k_pc_apply(const float* __restrict__ B, const int64_t* __restric
     const int s = slot_begin + e;
     base = state_off[s];
     off = pc_off[s];
-    x = a * w[base + i] + (u ? b * u[base + i] : 0.0);
+    x = a * (double)w[base + i] + (u ? b * (double)u[base + i] : 0.0);
     xs[le * nb + i] = (float)x;
   }
   __syncthreads();
   if (!valid) return;
   if (off < 0) {
-    z[base + i] = x * inv_sigma;
+    z[base + i] = (VT)(x * inv_sigma);
     return;
   }
   const float* Bc = B + off;
   const float* xe = xs + le * nb;
   float acc = 0.0f;
   for (int j = 0; j < nb; ++j) acc = fmaf(Bc[(int64_t)j * nb + i], xe[j], acc);
-  z[base + i] = (double)acc;
+  z[base + i] = (VT)acc;
 }
 
 // z = (a w + b u) / sigma on every DOF of a bucket without stored blocks
+template <typename VT>
 __global__ void k_pc_scale(const int64_t* __restrict__ state_off, int slot_begin, int count, int nb, double a,
-                           const double* w, double b, const double* __restrict__ u, double* z, double inv_sigma,
+                           const VT* w, double b, const VT* __restrict__ u, VT* z, double inv_sigma,
                            const int* __restrict__ gate, const double* __restrict__ bscale) {
   if (gate && *gate) return;
   if (bscale) b *= *bscale;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)count * nb) return;
   const int64_t idx = state_off[slot_begin + (int)(t / nb)] + (int)(t % nb);
-  z[idx] = (a * w[idx] + (u ? b * u[idx] : 0.0)) * inv_sigma;
+  z[idx] = (VT)((a * (double)w[idx] + (u ? b * (double)u[idx] : 0.0)) * inv_sigma);
 }
 
 // Distance-1 colouring of the face graph (greedy in element order), once per context.
@@ -556,41 +560,54 @@ fr_status fr_precond_release(fr_ctx* c) {
 namespace frgb {
 
 // z = M^-1 (a w + b u) on every element (z may alias w)
-fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s,
-                        const int* gate, const double* bscale) {
+template <typename VT>
+static fr_status precond_apply_t(fr_ctx* c, double a, const VT* w, double b, const VT* u, VT* z, cudaStream_t s,
+                                 const int* gate, const double* bscale) {
   if (!c->pc_ready) {
     set_error("element-Jacobi preconditioner not built (fr_precond_build) for the current layout");
     return FR_ERR_INVALID;
   }
   const int nd = c->nd, nv = c->nv;
+  const double vb = 3.0 * sizeof(VT);   // a w, b u in, z out
   for (const auto& bk : c->buckets) {
     if (bk.count == 0) continue;
     const int nb = nv * nsp_host(nd, bk.p);
     if (nb > kPcMax) {   // no stored blocks in this bucket: 1/sigma
       const int64_t nt = (int64_t)bk.count * nb;
-      FR_LAUNCH_B(c, "precond_apply", s, 24.0 * nt,
-                  k_pc_scale<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c->d_state_off, bk.slot_begin, bk.count, nb,
-                                                                        a, w, b, u, z, 1.0 / c->pc_sigma, gate,
-                                                                        bscale));
+      FR_LAUNCH_B(c, "precond_apply", s, vb * nt,
+                  k_pc_scale<VT><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c->d_state_off, bk.slot_begin, bk.count,
+                                                                            nb, a, w, b, u, z, 1.0 / c->pc_sigma,
+                                                                            gate, bscale));
       continue;
     }
-    const double bytes = (double)bk.count * nb * (24.0 + 4.0 * nb);
+    const double bytes = (double)bk.count * nb * (vb + 4.0 * nb);
     if (nb > 256) {
       FR_LAUNCH_B(c, "precond_apply", s, bytes,
-                  k_pc_apply_big<<<bk.count, 256, sizeof(float) * nb, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
-                                                                           bk.slot_begin, nb, a, w, b, u, z,
-                                                                           1.0 / c->pc_sigma, gate, bscale));
+                  k_pc_apply_big<VT><<<bk.count, 256, sizeof(float) * nb, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
+                                                                               bk.slot_begin, nb, a, w, b, u, z,
+                                                                               1.0 / c->pc_sigma, gate, bscale));
       continue;
     }
     const int epb = 256 / nb;
     const int threads = epb * nb;
     const unsigned grid = (unsigned)((bk.count + epb - 1) / epb);
     FR_LAUNCH_B(c, "precond_apply", s, bytes,
-                k_pc_apply<<<grid, threads, sizeof(float) * threads, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
-                                                                          bk.slot_begin, bk.count, nb, epb, a, w, b,
-                                                                          u, z, 1.0 / c->pc_sigma, gate, bscale));
+                k_pc_apply<VT><<<grid, threads, sizeof(float) * threads, s>>>(c->d_pc, c->d_pc_off, c->d_state_off,
+                                                                              bk.slot_begin, bk.count, nb, epb, a, w,
+                                                                              b, u, z, 1.0 / c->pc_sigma, gate,
+                                                                              bscale));
   }
   return cuda_check(cudaGetLastError(), "precond_apply");
+}
+
+fr_status precond_apply(fr_ctx* c, double a, const double* w, double b, const double* u, double* z, cudaStream_t s,
+                        const int* gate, const double* bscale) {
+  return precond_apply_t<double>(c, a, w, b, u, z, s, gate, bscale);
+}
+
+fr_status precond_apply(fr_ctx* c, double a, const float* w, double b, const float* u, float* z, cudaStream_t s,
+                        const int* gate, const double* bscale) {
+  return precond_apply_t<float>(c, a, w, b, u, z, s, gate, bscale);
 }
 
 }  // namespace frgb

@@ -665,7 +665,9 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot32(const float* __restr
                                                              unsigned* __restrict__ ticket, int with_norm,
                                                              const int* __restrict__ gate) {
   if (gate && *gate) return;
-  constexpr int U = 4, CH = KC < 4 ? KC : 4;
+  // two columns a load batch: 32 registers of column values in flight, so
+  // that two CTAs of 256 threads fit on an SM up to KC = 8
+  constexpr int U = 4, CH = KC < 2 ? KC : 2;
   double acc[KC + 1];
 #pragma unroll
   for (int kk = 0; kk <= KC; ++kk) acc[kk] = 0.0;
@@ -1126,10 +1128,10 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
     if (cudaMallocHost(&c->h_jidx, sizeof(int) * kMaxK) != cudaSuccess) return FR_ERR_NOMEM;
     for (int k = 0; k < kMaxK; ++k) c->h_jidx[k] = k;
   }
-  // FP32 basis: exact FP32 products, no preconditioner, and a tolerance the
-  // FP32 products can meet (the attainable accuracy of both is about 1e-6)
-  const bool b32 = c->f32_basis && op->mode == FR_JV_EXACT && op->jv_prec != FR_F64 && !op->precond &&
-                   o->rtol >= kF32BasisMinRtol;
+  // FP32 basis: exact FP32 products and a tolerance they can meet (the
+  // attainable accuracy of both is about 1e-6); the element-Jacobi
+  // preconditioner then works on the FP32 vectors (its sums are FP32 anyway)
+  const bool b32 = c->f32_basis && op->mode == FR_JV_EXACT && op->jv_prec != FR_F64 && o->rtol >= kF32BasisMinRtol;
   if (!b32 && (!c->d_krylov || c->krylov_m < m)) {
     cudaFree(c->d_krylov);
     c->d_krylov = nullptr;
@@ -1239,7 +1241,8 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
   // further pass works on the new column in place; `step` (device-driven
   // cycles): the Givens bookkeeping run by the update that ends the iteration
   auto gs_first = [&](int kk, double* raw, int with_norm, StepArgs step = {}) {
-    if (b32) gs_pass32(kk, w32, true, V32 + (int64_t)kk * ld, raw, with_norm, step);
+    // FP32 basis: w32 holds J v, or M^-1 (sigma v - J v) once preconditioned
+    if (b32) gs_pass32(kk, w32, !op->precond, V32 + (int64_t)kk * ld, raw, with_norm, step);
     else gs_pass(kk, w, V + (int64_t)kk * ld, raw, with_norm, step);
   };
   auto gs_again = [&](int kk, double* raw, StepArgs step = {}) {
@@ -1297,7 +1300,12 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
         mark_l[j] = c->timing.launches;
         if (j == 0) cudaMemcpyAsync(c->d_jidx, c->h_jidx, sizeof(int), cudaMemcpyHostToDevice, s);
         if ((ee = exact_product(c, op, Vb, wb, s, false, b32, direct_col ? j : -1)) != FR_OK) break;
-        if (pc && (ee = precond_apply(c, 1.0, w, op->sigma, V + (int64_t)j * ld, w, s, ctl, sdev + j)) != FR_OK) break;
+        if (pc && b32 &&
+            (ee = precond_apply(c, -1.0, w32, op->sigma, V32 + (int64_t)j * ld, w32, s, ctl, sdev + j)) != FR_OK)
+          break;
+        if (pc && !b32 &&
+            (ee = precond_apply(c, 1.0, w, op->sigma, V + (int64_t)j * ld, w, s, ctl, sdev + j)) != FR_OK)
+          break;
         const int kk = j + 1;
         StepArgs step;
         step.gm = gm;
@@ -1377,7 +1385,10 @@ static fr_status gmres_impl(fr_ctx* c, const fr_shifted_op* op, const double* R0
         FR_LAUNCH_B(c, "vec", s, 16.0 * n, k_scale<<<egrid(n), 256, 0, s>>>(V + (int64_t)j * ld, sh[j], xs, n));
         if ((e = apply_op(c, op, R0, xs, w, s, false)) != FR_OK) return e;
       }
-      if (pc && (e = precond_apply(c, 1.0, w, op->sigma * sh[j], V + (int64_t)j * ld, w, s)) != FR_OK) return e;
+      if (pc && b32 && (e = precond_apply(c, -1.0, w32, op->sigma * sh[j], V32 + (int64_t)j * ld, w32, s)) != FR_OK)
+        return e;
+      if (pc && !b32 && (e = precond_apply(c, 1.0, w, op->sigma * sh[j], V + (int64_t)j * ld, w, s)) != FR_OK)
+        return e;
       ++it;
       // classical Gram-Schmidt: one pass (reorth 0), a second pass when the
       // first removed more than half of ||w||^2, ||w_new|| < 0.7 ||w|| (DGKS,

@@ -259,27 +259,35 @@ def test_device_gmres_batch_past_convergence(built):
     assert np.abs(x.cpu().numpy() - xh).max() <= 1e-6 * np.abs(xh).max()
 
 
-@pytest.mark.parametrize("name,m,rtol", [("tgv_5^3_p3", 30, 1e-1), ("tgv_5^3_p3", 8, 1e-4),
-                                         ("diff_3^3_p4_mu0.05", 30, 1e-2), ("vortex2d_mixed_p1-4", 8, 1e-4),
-                                         ("box_mixed_p4-5_ns", 30, 1e-1)])
-def test_f32_basis_matches_f64_basis(built, name, m, rtol):
+@pytest.mark.parametrize("name,m,rtol,pc", [("tgv_5^3_p3", 30, 1e-1, False), ("tgv_5^3_p3", 8, 1e-4, False),
+                                            ("diff_3^3_p4_mu0.05", 30, 1e-2, False),
+                                            ("vortex2d_mixed_p1-4", 8, 1e-4, False),
+                                            ("box_mixed_p4-5_ns", 30, 1e-1, False),
+                                            ("box_mixed_p4-5_ns", 8, 1e-4, True),
+                                            ("cylinder_4x12x2_mixed", 30, 1e-2, True)])
+def test_f32_basis_matches_f64_basis(built, name, m, rtol, pc):
     """GMRES with FP32 products and the Krylov basis stored in FP32 (dots and
     norms summed in FP32 over 16 values, FP64 beyond; the default for such
     products at rtol >= 1e-4) against the FP64 basis, both device-driven and
     host-driven: the same Krylov space to about 1e-6, so the iteration counts
     agree within one and x to 1e-4 of max|x|, with and without restarts, on
-    one and on several degree buckets, and on a vector whose length is not a
-    multiple of four (the 3^3 p = 4 box: 16,875 values)."""
+    one and on several degree buckets, on a vector whose length is not a
+    multiple of four (the 3^3 p = 4 box: 16,875 values), and with the
+    element-Jacobi preconditioner applied to the FP32 vectors."""
     mm, q, ph = WL[name]
     ctx = gpu_ctx(mm, ph)
     qs = ctx.pack(torch.from_numpy(generic_state(q)).cuda())
     b = ctx.pack(torch.from_numpy(cases.uniform(919, q.size) - 0.5).cuda())
     out = {}
+    sigma = 500.0 if pc else 40.0
     for dev in (True, False):
         for b32 in (True, False):
             _set_flag(ctx, "device_gmres", dev)
             _set_flag(ctx, "f32_basis", b32)
-            x, st = ctx.gmres(qs, b, 40.0, mode="exact", jv_dtype=torch.float32, m=m, rtol=rtol, max_it=400)
+            if pc:
+                ctx.precond_build(qs, sigma)   # the tuning change dropped the blocks
+            x, st = ctx.gmres(qs, b, sigma, mode="exact", jv_dtype=torch.float32, m=m, rtol=rtol, max_it=400,
+                              precond=pc)
             assert st["converged"], (dev, b32, st)
             out[dev, b32] = (x.cpu().numpy(), st["iterations"])
     x0, i0 = out[False, False]
