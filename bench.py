@@ -426,12 +426,13 @@ def mixed_degree_ops(peak_gbs):
     return out
 
 
-def stage_fd64(ctx, tab, qn, N, R1, opts, tuning=None, precond_sigma=None, **over):
+def stage_fd64(ctx, tab, qn, N, R1, opts, tuning=None, precond_sigma=None, label="fd_f64", **over):
     """The same ESDIRK3 stage in another product mode, timed once after one
     untimed solve: by default mode (A), FP64 finite-difference Jv.  ``tuning``
     overrides launch choices for the run (restored after it);
     ``precond_sigma``: element-Jacobi blocks built at q^n with that shift before
-    the stage (the build timed apart)."""
+    the stage (the build timed apart).  The timed solve sits in the NVTX range
+    ``bench_mode_<label>``, so that a profiler can select it."""
     import torch
     saved = ctx.tuning()
     if tuning:
@@ -464,10 +465,14 @@ def stage_fd64(ctx, tab, qn, N, R1, opts, tuning=None, precond_sigma=None, **ove
         qi.copy_(qn[:N])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if rep == 1:
+            torch.cuda.nvtx.range_push(f"bench_mode_{label}")
         e0.record()
         st = ctx.esdirk_stage(tab, 2, DT, qn[:N], [R1, R2, None, None], qi, **o)
         e1.record()
         torch.cuda.synchronize()
+        if rep == 1:
+            torch.cuda.nvtx.range_pop()
     out = {"ms": round(e0.elapsed_time(e1), 3), "newton": st["newton"], "gmres": st["gmres"],
            "converged": st["converged"], "rel_final": st["norm_final"] / st["norm0"],
            "norm_final": st["norm_final"], "F_evals_low": st["low_evaluations"],
@@ -704,25 +709,29 @@ def main():
     # per-operator throughput (graph-replayed) and the FP64 finite-difference stage
     ops = op_throughput(ctx, qn[:N], N, peak)
     fd = stage_fd64(ctx, tab, qn, N, R1, opts)
-    bf = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype="bf16op")
-    f64F = stage_fd64(ctx, tab, qn, N, R1, opts, mode="exact", jv_dtype=torch.float32, low_above=0.0)
+    bf = stage_fd64(ctx, tab, qn, N, R1, opts, label="bf16op", mode="exact", jv_dtype="bf16op")
+    f64F = stage_fd64(ctx, tab, qn, N, R1, opts, label="f64_F", mode="exact", jv_dtype=torch.float32, low_above=0.0)
     same = dict(mode="exact", jv_dtype=torch.float32)
     # (FP64 F throughout, so that they compare with exact_f32_jvp_f64_F) the
     # Arnoldi dots in double-float arithmetic; each of the three exact-JVP
     # kernel choices forced (fused, trace-gradient and compact three passes);
     # the element-Jacobi preconditioner (blocks at q^n with the shift
     # 1/(w dt) + 1/dtau_max, 320-DOF blocks inverted on the device)
-    f64dots = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"df_arnoldi": True}, **same)
-    fusedst = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 1}}, **same)
-    classic = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 2}}, **same)
-    compact = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 3}}, **same)
-    pcst = stage_fd64(ctx, tab, qn, N, R1, opts, precond_sigma=1.0 / (tab[1][1] * DT) + 1.0 / DT, **same)
+    f64dots = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"df_arnoldi": True}, label="df_dots", **same)
+    fusedst = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 1}},
+                         label="fused", **same)
+    classic = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 2}},
+                         label="classic", **same)
+    compact = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 3}},
+                         label="compact", **same)
+    pcst = stage_fd64(ctx, tab, qn, N, R1, opts, precond_sigma=1.0 / (tab[1][1] * DT) + 1.0 / DT,
+                      label="element_jacobi", **same)
     # the timed configuration with one host round trip per GMRES iteration
     # (rotations on the host, products replayed from a CUDA graph)
-    hostgm = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"device_gmres": False}, mode="exact",
+    hostgm = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"device_gmres": False}, label="host_gmres", mode="exact",
                         jv_dtype=torch.float32, low_above=opts["low_above"], low_precision=opts["low_precision"])
     # the timed configuration as the timed steps run it, without any events
-    devgm = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"device_gmres": True}, mode="exact",
+    devgm = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"device_gmres": True}, label="device_gmres", mode="exact",
                        jv_dtype=torch.float32, low_above=opts["low_above"], low_precision=opts["low_precision"])
     roof["frac_alg"] = {k: ops[k]["hbm_frac"] for k in ("jvp_exact_f32", "residual_f32", "residual_df",
                                                          "residual_f64", "vjp_f32")}

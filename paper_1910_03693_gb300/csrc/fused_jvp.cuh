@@ -699,11 +699,12 @@ __global__ void __launch_bounds__(128, 4) cface_kernel(CFaceArgs<T> a) {
 // four bulk asynchronous copies (cp.async.bulk, global -> shared, completion
 // counted in bytes on an mbarrier), one per compact block, and the copies of
 // the next tile are in flight while the threads compute the current one (two
-// buffers).  Blocks must be multiples of 16 bytes at 16-byte aligned offsets
-// (the host checks CT x NFP x sizeof(T)); a wait that exceeds its iteration
-// limit sets bit 0 of *status, stops the walk and waits, again bounded, for the
-// copies still in flight before the CTA exits.  Instantiated for FP32 only
-// (two buffers within the 48 KB of static shared memory).
+// buffers, one barrier a tile).  Blocks must be multiples of 16 bytes at
+// 16-byte aligned offsets (the host checks CT x NFP x sizeof(T)); a wait that
+// exceeds its iteration limit sets bit 0 of *status, stops the walk and waits,
+// again bounded, for the copies still in flight before the CTA exits.
+// Instantiated for FP32 only (two buffers within the 48 KB of static shared
+// memory).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -754,7 +755,6 @@ __global__ void __launch_bounds__(128, 4) cface_tma_kernel(CFaceArgs<T> a, int* 
   static_assert(BYTES % 16 == 0 && FB <= 32, "bulk-copied blocks: multiples of 16 bytes, at most one warp of faces");
   __shared__ __align__(128) T sh[2][FB][4][BLK];
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int stop;
   if (gate_closed(a.gate)) return;   // before any barrier is armed or copy issued
   const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP;
   const int ntiles = (a.n + FB - 1) / FB;
@@ -762,7 +762,6 @@ __global__ void __launch_bounds__(128, 4) cface_tma_kernel(CFaceArgs<T> a, int* 
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    stop = 0;
   }
   __syncthreads();
   // one lane per face of the tile issues its four copies after lane 0 has
@@ -783,6 +782,7 @@ __global__ void __launch_bounds__(128, 4) cface_tma_kernel(CFaceArgs<T> a, int* 
     }
   };
   int it = 0;
+  bool stop = false;
   if ((int)blockIdx.x < ntiles && threadIdx.x < 32) issue(blockIdx.x, 0);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int b = it & 1;
@@ -796,14 +796,17 @@ __global__ void __launch_bounds__(128, 4) cface_tma_kernel(CFaceArgs<T> a, int* 
       r = a.recs[fidx];
       cface_geo<T, ND, P, DIAG>(a, r, t, g);
     }
-    if (!mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitLimit)) {
-      atomicOr(status, 1);
-      stop = 1;
+    // every thread waits for the tile's bytes itself; one barrier a tile then
+    // frees buffer b for the tile after next and carries a timeout to the
+    // whole CTA
+    const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitLimit);
+    if (!ok) atomicOr(status, 1);
+    if (ok && valid)
+      cface_point<T, ND, P, VISC, DIAG>(a, r, t, g, sh[b][lf][0], sh[b][lf][1], sh[b][lf][2], sh[b][lf][3]);
+    if (__syncthreads_or(!ok)) {
+      stop = true;
+      break;
     }
-    __syncthreads();
-    if (stop) break;
-    if (valid) cface_point<T, ND, P, VISC, DIAG>(a, r, t, g, sh[b][lf][0], sh[b][lf][1], sh[b][lf][2], sh[b][lf][3]);
-    __syncthreads();   // buffer b is free for the tile after next
   }
   if (stop) {
     // copies of this and the next tile may still be in flight: wait for both
