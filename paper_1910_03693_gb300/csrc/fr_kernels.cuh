@@ -404,11 +404,12 @@ __device__ __forceinline__ void slave_coef_at_mortar(const FaceArgs<T>& a, const
 // area vector and the BR2 lifting coefficients point along the master face's
 // axis dm and only the viscous flux row dm is needed.  Face records are sorted
 // by dm, so the branches on it are warp-uniform.
-// Double-float: four CTAs an SM (128 registers; the viscous instance spills
-// 160 bytes, and still streams its traces faster than at three CTAs: 252 ->
-// 234 us at 32^3).
+// FP32 and double-float: four CTAs an SM (128 registers).  Uncapped, the
+// FP32 JVP instance for general metrics held 183 registers (two CTAs); the
+// double-float viscous instance spills 160 bytes at the cap and still streams
+// its traces faster than at three CTAs (252 -> 234 us at 32^3).
 template <typename T, int ND, bool VISC, int MODE, bool DIAG = false>
-__global__ void __launch_bounds__(128, is_dfloat<T>::value ? 4 : 1) face_kernel(FaceArgs<T> a) {
+__global__ void __launch_bounds__(128, (is_dfloat<T>::value || sizeof(T) == 4) ? 4 : 1) face_kernel(FaceArgs<T> a) {
   constexpr int NV = ND + 2;
   if (gate_closed(a.gate)) return;
   using S = typename std::conditional<MODE == 1, Dual<T>, T>::type;
