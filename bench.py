@@ -744,7 +744,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 JVP; F double-float above 1e-8 ||F0||, f64 below (convergence on f64 F); f64 Arnoldi/update",
+        "dtype": ("f32 JVP; F double-float above 1e-8 ||F0||, f64 below (convergence on f64 F); f32 Krylov basis "
+                  "(f64-accumulated dots, f64 Hessenberg and rotations) while the f32 JVP runs"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.n == 32 else f"tgv_ns_{args.n}^3_p3", "n_dof": N,
                    "dt": DT, "tableau": "ESDIRK3 stage 2", "gmres": "GMRES(60), rtol 0.1, <= 100 it, one CGS pass",
