@@ -713,8 +713,9 @@ def main():
     f64F = stage_fd64(ctx, tab, qn, N, R1, opts, label="f64_F", mode="exact", jv_dtype=torch.float32, low_above=0.0)
     same = dict(mode="exact", jv_dtype=torch.float32)
     # (FP64 F throughout, so that they compare with exact_f32_jvp_f64_F) the
-    # Arnoldi dots in double-float arithmetic; each of the three exact-JVP
-    # kernel choices forced (fused, trace-gradient and compact three passes);
+    # Arnoldi dots in double-float arithmetic; each of the four exact-JVP
+    # kernel choices forced (fused, trace-gradient and compact three passes,
+    # compact passes with the tangent's traces formed in the face kernel);
     # the element-Jacobi preconditioner (blocks at q^n with the shift
     # 1/(w dt) + 1/dtau_max, 320-DOF blocks inverted on the device)
     f64dots = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"df_arnoldi": True}, label="df_dots", **same)
@@ -724,6 +725,8 @@ def main():
                          label="classic", **same)
     compact = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 3}},
                          label="compact", **same)
+    compact_vt = stage_fd64(ctx, tab, qn, N, R1, opts, tuning={"fused_jvp": True, "epb": {21 + 2 * 7 + 1: 4}},
+                            label="compact_vt", **same)
     pcst = stage_fd64(ctx, tab, qn, N, R1, opts, precond_sigma=1.0 / (tab[1][1] * DT) + 1.0 / DT,
                       label="element_jacobi", **same)
     # the timed configuration with one host round trip per GMRES iteration
@@ -757,7 +760,9 @@ def main():
                                      "launched in batches)" if tuning["device_gmres"] else
                                      "host round trip per iteration",
                        "jvp_kernels_f32": {0: "compact three passes (undecided)", 1: "fused", 2: "trace-gradient three passes",
-                                           3: "compact three passes"}[tuning["epb"][21 + 2 * 7 + 1]]}},
+                                           3: "compact three passes",
+                                           4: "compact two passes (the tangent's traces formed in the face kernel)"}[
+                                               tuning["epb"][21 + 2 * 7 + 1]]}},
         "stage": {"newton": [s["newton"] for s in stats], "gmres": [s["gmres"] for s in stats],
                   "F_evals_low": [s["low_evaluations"] for s in stats],
                   "F_evals_f64": [s["f64_evaluations"] for s in stats],
@@ -773,6 +778,7 @@ def main():
                         "fd_f64": fd, "exact_bf16op_jvp": bf, "exact_f32_jvp_f64_F": f64F,
                         "exact_f32_jvp_double_float_arnoldi_dots": f64dots, "exact_f32_fused_jvp": fusedst,
                         "exact_f32_trace_gradient_jvp": classic, "exact_f32_compact_jvp": compact,
+                        "exact_f32_compact_vt_jvp": compact_vt,
                         "exact_f32_jvp_element_jacobi": pcst, "host_driven_gmres": hostgm,
                         "device_driven_gmres_untimed": devgm},
         "kernels": kernels,

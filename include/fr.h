@@ -400,10 +400,15 @@ fr_status esdirk_step(fr_ctx* ctx, const fr_tableau* tab, double dt, double* q_i
  * chooses the exact JVP's kernels where FR_TUNE_FUSED_JVP allows the
  * compact-trace ones (every face interior and conforming): 1 the fused
  * face-and-volume kernel, 2 the trace-gradient three passes, 3 (and 0,
- * undecided) the compact three passes; fr_autotune times the three; and the
- * flags below.  fr_tuning_set with table NULL changes only the
- * flags; elements per CTA outside [0, 256], choices outside [0, 2], weight
- * models outside [0, 3] or unknown flag bits give FR_ERR_INVALID. */
+ * undecided) the compact three passes, 4 two compact passes, the face kernel
+ * forming the tangent's traces itself (FP32 with FR_TUNE_TMA_FACES, degrees
+ * whose face points fit a warp: 3D p = 1, 3 and 2D p = 3; elsewhere, or when
+ * v's element blocks are not 16-byte aligned, the compact three passes run;
+ * the two compact choices give the same bits); fr_autotune times those that
+ * apply; and the flags below.  fr_tuning_set with table NULL changes only the
+ * flags; elements per CTA outside [0, 256], multi-bucket choices outside
+ * [0, 2], weight models outside [0, 3], the exact JVP's choice outside [0, 4]
+ * or unknown flag bits give FR_ERR_INVALID. */
 #define FR_TUNE_MULTI_LAUNCH 1  /* one persistent launch over all degree buckets */
 #define FR_TUNE_GRAPHS 2        /* host-driven GMRES: the Arnoldi products
                                    replayed from a CUDA graph               */

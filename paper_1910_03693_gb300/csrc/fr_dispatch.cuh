@@ -401,7 +401,35 @@ static inline bool fused_jvp_on(const fr_ctx* c) {
 template <typename T>
 static inline bool compact_jvp_on(const fr_ctx* c) {
   const int ch = c->epb_tab[prec_row<T>()][2][1];
-  return c->fused_ok && c->use_fused && (ch == 3 || ch == 0);
+  return c->fused_ok && c->use_fused && (ch == 3 || ch == 0 || ch == 4);
+}
+
+// The compact passes with the tangent's traces formed in the face kernel
+// (slot value 4): FP32 with bulk-copy staging, every face group of a degree
+// whose face points lie within one warp and whose blocks are multiples of 16
+// bytes, and v's element blocks 16-byte aligned in every bucket (else the
+// three compact passes run).
+template <typename T, int ND, bool VISC>
+static bool cface_vt_usable(const fr_ctx* c, const T* v) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return false;
+  } else {
+    if (!c->use_tma) return false;
+    for (const auto& g : c->fgroups) {
+      bool ok = false;
+      switch (g.pm + 1) {
+        case 2: ok = CFaceVt<T, ND, 2, VISC>::OK; break;
+        case 3: ok = CFaceVt<T, ND, 3, VISC>::OK; break;
+        case 4: ok = CFaceVt<T, ND, 4, VISC>::OK; break;
+        case 5: ok = CFaceVt<T, ND, 5, VISC>::OK; break;
+        case 6: ok = CFaceVt<T, ND, 6, VISC>::OK; break;
+      }
+      if (!ok) return false;
+    }
+    for (const auto& b : c->buckets)
+      if (reinterpret_cast<uintptr_t>(v + b.state_base) % 16 != 0) return false;
+    return true;
+  }
 }
 
 template <typename T, int ND, int P, bool VISC>
@@ -522,6 +550,26 @@ static void launch_cface_p(fr_ctx* c, const CFaceArgs<T>& a, cudaStream_t s) {
   cface_kernel<T, ND, P, VISC, DIAG><<<nblocks(a.n, FB), FB * NFP, 0, s>>>(a);
 }
 
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+static void launch_cface_vt_p(fr_ctx* c, const CFaceArgs<T>& a, cudaStream_t s) {
+  using C = CFaceVt<T, ND, P, VISC>;
+  if constexpr (std::is_same<T, float>::value && C::OK) {
+    auto kern = cface_vt_kernel<T, ND, P, VISC, DIAG>;
+    static size_t configured = 0;
+    static int per_sm = 0;
+    if (configured == 0)
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    ensure_smem(kern, C::SMEM, configured);
+    if (per_sm == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, C::SMEM);
+      per_sm = std::max(per_sm, 1);
+    }
+    const int ntiles = (a.n + C::FB - 1) / C::FB;
+    const unsigned grid = (unsigned)std::max(1, std::min(ntiles, per_sm * (int)sm_count(c)));
+    kern<<<grid, 128, C::SMEM, s>>>(a, c->d_status);
+  }
+}
+
 template <typename T, int ND, bool VISC, bool DIAG>
 static void jvp_compact_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStream_t s, bool q_traces_ready,
                              double* neg64) {
@@ -529,6 +577,46 @@ static void jvp_compact_impl(fr_ctx* c, const T* q, const T* v, T* Jv, cudaStrea
   T* trq = (T*)c->d_trace_q;
   T* trv = (T*)c->d_trace_v;
   if (!q_traces_ready) launch_ctraces<T, ND, VISC>(c, q, trq, s);
+  const bool vt = c->epb_tab[prec_row<T>()][2][1] == 4 && cface_vt_usable<T, ND, VISC>(c, v);
+  if (vt) {
+    for (const auto& g : c->fgroups) {
+      const Bucket* bk = nullptr;
+      for (const auto& b : c->buckets)
+        if (b.p == g.pm) bk = &b;
+      CFaceArgs<T> a;
+      a.gate = c->gate;
+      a.recs = g.d_recs;
+      a.trq = trq;
+      a.fout = (T*)c->d_fout;
+      a.basis = basis_ptr<T>(c);
+      a.geo = geo_view<T>(c, g.pm);
+      a.gamma = (T)c->phys.gamma;
+      a.mu = (T)c->phys.mu;
+      a.kappa = (T)c->phys.kappa;
+      a.flux = c->phys.flux;
+      a.n = g.n;
+      a.nvt = c->nvt;
+      a.v = v;
+      a.state_base = bk->state_base;
+      a.trace_base = bk->trace_base;
+      a.ctrace_base = bk->ctrace_base;
+      const int P = g.pm + 1, NFP = ipow(P, ND - 1), NSP = nsp_of(ND, P);
+      // both sides' compact traces of q and elements of v in; both sides' face outputs out
+      const double nb =
+          (double)g.n * (NFP * (2.0 * CT + 2.0 * (VISC ? 3 : 1) * NV) + 2.0 * NV * NSP) * sizeof(T);
+      FR_LAUNCH_B(c, kname<T>("cface_vt_jvp_f64", "cface_vt_jvp_f32", "cface_vt_jvp_df"), s, nb, {
+        switch (P) {
+          case 2: launch_cface_vt_p<T, ND, 2, VISC, DIAG>(c, a, s); break;
+          case 3: launch_cface_vt_p<T, ND, 3, VISC, DIAG>(c, a, s); break;
+          case 4: launch_cface_vt_p<T, ND, 4, VISC, DIAG>(c, a, s); break;
+          case 5: launch_cface_vt_p<T, ND, 5, VISC, DIAG>(c, a, s); break;
+          case 6: launch_cface_vt_p<T, ND, 6, VISC, DIAG>(c, a, s); break;
+        }
+      });
+    }
+    launch_vols<T, ND, VISC, 1, DIAG>(c, q, v, Jv, s, neg64);
+    return;
+  }
   launch_ctraces<T, ND, VISC>(c, v, trv, s);
   for (const auto& g : c->fgroups) {
     CFaceArgs<T> a;
@@ -839,7 +927,10 @@ static void autotune_impl(fr_ctx* c, const T* q, T* scratch, int reps, cudaStrea
     if (c->fused_ok && c->use_fused) {
       float best = 1e30f;
       int choice = 2;
-      for (int m = 1; m <= 3; ++m) {   // 1 fused, 2 trace-gradient three passes, 3 compact three passes
+      // 1 fused, 2 trace-gradient three passes, 3 compact three passes, 4 the
+      // compact passes with the tangent's traces formed in the face kernel
+      for (int m = 1; m <= 4; ++m) {
+        if (m == 4 && !cface_vt_usable<T, ND, VISC>(c, q)) continue;
         c->epb_tab[prec][2][1] = m;
         clear_graphs(c);
         const float t = time_best(reps + 2, s, [&] { jvp_impl<T, ND, VISC, DIAG>(c, q, q, scratch, s); });

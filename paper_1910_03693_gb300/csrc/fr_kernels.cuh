@@ -234,8 +234,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs<T>& a, int64_t i0, in
     if (fp >= NFPT) break;
     const int f = fp / NFP, t = fp % NFP, d = f >> 1;
     const int ia = t % P, ib = ND == 3 ? t / P : 0;
-    const int ta = d == 0 ? 1 : 0;              // first tangential direction
-    const int tb = d == 2 ? 1 : 2;              // second (3D)
+    const int ta = d == 0 ? 1 : 0;              // first tangential direction (the second is the remaining axis)
     T Sf[ND][ND];
 #pragma unroll
     for (int dd = 0; dd < ND; ++dd)

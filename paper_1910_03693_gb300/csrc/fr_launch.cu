@@ -230,9 +230,12 @@ fr_status fr_tuning_set(fr_ctx* c, const int32_t* table, int32_t flags) {
   }
   if (table) {
     for (int i = 0; i < 2 * 3 * (kPM + 1); ++i)
-      if (table[i] < 0 || table[i] > (i % (kPM + 1) == 0 ? 2 : (i % (kPM + 1) == 1 ? 3 : 256))) {
+      if (table[i] < 0 ||
+          table[i] > (i % (kPM + 1) == 0 ? 2
+                      : i % (kPM + 1) == 1 ? (i / (kPM + 1) % 3 == 2 ? 4 : 3)
+                                           : 256)) {
         set_error("fr_tuning_set: elements per CTA must lie in [0, 256], multi-bucket choices in [0, 2], "
-                  "the weight model in [0, 3]");
+                  "the weight model in [0, 3], the exact JVP's kernels in [0, 4]");
         return FR_ERR_INVALID;
       }
     std::memcpy(c->epb_tab, table, sizeof(c->epb_tab));

@@ -39,18 +39,42 @@ struct CompactWidth {
   static constexpr int value = VISC ? 2 * NV : NV;
 };
 
+// Widest vector load (16, 8 or 1 bytes) that every line along xi of elements
+// staged [NV][NSP] at multiples of BLOCK values from a 16-byte aligned base is
+// aligned to: the block, variable and line (a multiple of P) offsets.
+template <typename T, int P, int NSP, int BLOCK>
+constexpr int line_vec_width() {
+  constexpr int SZ = (int)sizeof(T);
+  return (BLOCK * SZ) % 16 == 0 && (NSP * SZ) % 16 == 0 && (P * SZ) % 16 == 0   ? 16
+         : (BLOCK * SZ) % 8 == 0 && (NSP * SZ) % 8 == 0 && (P * SZ) % 8 == 0 ? 8
+                                                                              : 1;
+}
+
 // q and (Navier-Stokes) the reference normal derivative at face point fp of an
-// element staged in shared memory as [NV][NSP].
-template <typename T, int ND, int P, bool VISC>
+// element staged in shared memory as [NV][NSP]; W > 1: the caller's element is
+// W-byte aligned as line_vec_width states, and lines along xi (contiguous) are
+// read as vectors (the same values).
+template <typename T, int ND, int P, bool VISC, int W = 1>
 __device__ __forceinline__ void trace_point(const T* sq, const BasisTab<T>& B, int fp, T* qf, T* dn) {
   using Sh = Shape<ND, P>;
   constexpr int NV = Sh::NV, NSP = Sh::NSP, NFP = Sh::NFP;
   const int f = fp / NFP, t = fp % NFP, d = f >> 1, s = f & 1;
+  // the normal line through face point t: solution points base + k stride
+  // (its offsets computed once for all variables)
+  const int base = line_sp<ND, P>(d, t, 0);
+  const int stride = d == 0 ? 1 : (d == 1 ? P : P * P);
+  int off[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) off[k] = base + k * stride;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     T x[P];
+    if (W > 1 && d == 0) {
+      load_contig<T, P, W>(sq + v * NSP + base, x);
+    } else {
 #pragma unroll
-    for (int k = 0; k < P; ++k) x[k] = sq[v * NSP + line_sp<ND, P>(d, t, k)];
+      for (int k = 0; k < P; ++k) x[k] = sq[v * NSP + off[k]];
+    }
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < P; ++k) acc = xfma(B.ext[s][k], x[k], acc);
@@ -104,7 +128,7 @@ __global__ void __launch_bounds__(256) ctrace_kernel(CTraceArgs<T> a, int epb) {
     if (fp >= NFPT) break;
     const int f = fp / NFP, t = fp % NFP;
     T qf[NV], dn[NV];
-    trace_point<T, ND, P, VISC>(sq, B, fp, qf, dn);
+    trace_point<T, ND, P, VISC, line_vec_width<T, P, NSP, NV * NSP>()>(sq, B, fp, qf, dn);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       out[(f * CT + v) * NFP + t] = qf[v];
@@ -134,8 +158,7 @@ __device__ __forceinline__ void face_grad_m(const T* Xq, const T* Xv, int fc, in
   constexpr int NFP = ND == 2 ? P : P * P;
   const int dc = fc >> 1;
   const int ia = t % P, ib = ND == 3 ? t / P : 0;
-  const int ta = dc == 0 ? 1 : 0;
-  const int tb = dc == 2 ? 1 : 2;
+  const int ta = dc == 0 ? 1 : 0;   // first tangential direction (the second is the remaining axis)
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const Dual<T> dn{Xq[(NV + v) * NFP + t], Xv[(NV + v) * NFP + t]};
@@ -532,6 +555,11 @@ struct CFaceArgs {
   int n;                    // faces in the group
   int nvt;                  // components of the trace-gradient layout (its offsets scale to compact ones)
   const int* gate = nullptr;   // see gate_closed
+  // the tangent's traces formed in the face kernel (cface_vt_kernel): v in the
+  // bucketed state layout and the group's bucket bases, which map a face
+  // record's trace offset to its element's state block
+  const T* v = nullptr;
+  int64_t state_base = 0, trace_base = 0, ctrace_base = 0;
 };
 
 // Geometry of one face point read ahead of the staged traces (the master's
@@ -816,4 +844,175 @@ __global__ void __launch_bounds__(128, 4) cface_tma_kernel(CFaceArgs<T> a, int* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The compact face pass with the tangent's traces formed in the face kernel
+// (two passes a product instead of three: no trace pass over v and no round
+// trip of its compact traces through memory).  Per face of a tile, four
+// blocks are copied into shared memory: the two sides' compact traces of q
+// (fixed during a GMRES solve) and the two sides' elements of v ([NV][NSP],
+// contiguous in the bucketed state).  Each thread forms the compact trace of
+// v at its point of both faces (the interpolation of the trace pass, with the
+// same explicit fused multiply-adds, so the values have the same bits), the
+// face's threads meet at a warp barrier, and the flux step follows.  A face's
+// points lie in one warp (32 a multiple of the face's points), so no CTA
+// barrier separates the two steps.
+//
+// Buffers: the q-trace blocks are double-buffered and issued one tile ahead
+// by warp 0, as in cface_tma_kernel; the element blocks, twice their size,
+// have one buffer, and the last warp to finish forming its traces (a shared
+// counter) issues the next tile's element copies, so that they overlap the
+// flux step.  Both land on the next tile's barrier, which expects all of its
+// bytes from the start.  One CTA barrier a tile frees the q-trace buffer and
+// the tangent traces; the bounded waits and the error path are those of
+// cface_tma_kernel.  Shared memory: 50 KB for 3D p = 3 (four CTAs an SM).
+// ---------------------------------------------------------------------------
+template <typename T, int ND, int P, bool VISC>
+struct CFaceVt {
+  static constexpr int NV = ND + 2;
+  static constexpr int NFP = ND == 2 ? P : P * P;
+  static constexpr int NSP = Shape<ND, P>::NSP;
+  static constexpr int CT = CompactWidth<VISC, NV>::value;
+  static constexpr int FB = 128 / NFP;                 // faces a tile
+  static constexpr int NW = 4;                         // warps a CTA
+  static constexpr int BLK = CT * NFP;                 // compact trace block of one face side
+  static constexpr int EL = NV * NSP;                  // state block of one element
+  static constexpr uint32_t QB = BLK * sizeof(T), EB = EL * sizeof(T);
+  static constexpr bool OK = 32 % NFP == 0 && FB <= 32 && QB % 16 == 0 && EB % 16 == 0;
+  // [2][FB][2][BLK] q traces, [FB][2][EL] elements of v, [FB][2][BLK] tangent traces
+  static constexpr size_t Q_OFF = 0, E_OFF = (size_t)2 * FB * 2 * BLK, V_OFF = E_OFF + (size_t)FB * 2 * EL;
+  static constexpr size_t SMEM = (V_OFF + (size_t)FB * 2 * BLK) * sizeof(T);
+};
+
+template <typename T, int ND, int P, bool VISC, bool DIAG>
+__global__ void __launch_bounds__(128, 4) cface_vt_kernel(CFaceArgs<T> a, int* status) {
+  using C = CFaceVt<T, ND, P, VISC>;
+  constexpr int NV = C::NV, NFP = C::NFP, NF = 2 * ND, FB = C::FB, BLK = C::BLK, EL = C::EL;
+  static_assert(C::OK, "a face's points within one warp; bulk-copied blocks multiples of 16 bytes");
+  extern __shared__ __align__(16) unsigned char smem_raw[];   // bulk-copy destinations: 16-byte aligned
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int64_t nidx[FB][2];    // the next tile's elements (bucket-local), for its element copies
+  __shared__ int done;               // warps done forming the current tile's traces
+  T* const sb = reinterpret_cast<T*>(smem_raw);
+  if (gate_closed(a.gate)) return;   // before any barrier is armed or copy issued
+  const int lf = threadIdx.x / NFP, t = threadIdx.x % NFP, lane = threadIdx.x & 31;
+  const int ntiles = (a.n + FB - 1) / FB;
+  const uint64_t per_elem = (uint64_t)a.nvt * NFP * NF;  // trace-gradient values of one element
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    done = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto faces_of = [&](int tile) { return (int)min((int64_t)FB, (int64_t)a.n - (int64_t)tile * FB); };
+  // warp 0: announce the tile's bytes (both kinds), copy its q-trace blocks
+  // into buffer b and leave its elements in nidx (one lane per face)
+  auto issue_q = [&](int tile, int b) {
+    const int nf = faces_of(tile);
+    if (lane == 0) mbar_arrive_expect(&bar[b], (uint32_t)nf * 2u * (C::QB + C::EB));
+    __syncwarp();
+    if (lane < nf) {
+      const FaceRec r = a.recs[(int64_t)tile * FB + lane];
+      // the two sides' bucket-local elements (a 32-bit division while the
+      // bucket's trace offsets fit), then their blocks
+      const uint64_t rm = (uint64_t)(r.mt - a.trace_base), rs = (uint64_t)(r.st - a.trace_base);
+      const int64_t im = rm >> 32 ? (int64_t)(rm / per_elem) : (int64_t)((uint32_t)rm / (uint32_t)per_elem);
+      const int64_t is = rs >> 32 ? (int64_t)(rs / per_elem) : (int64_t)((uint32_t)rs / (uint32_t)per_elem);
+      T* dst = sb + C::Q_OFF + (size_t)(b * FB + lane) * 2 * BLK;
+      bulk_copy_g2s(dst, a.trq + a.ctrace_base + (im * NF + r.mf) * BLK, C::QB, &bar[b]);
+      bulk_copy_g2s(dst + BLK, a.trq + a.ctrace_base + (is * NF + r.sf) * BLK, C::QB, &bar[b]);
+      nidx[lane][0] = im;
+      nidx[lane][1] = is;
+    }
+  };
+  // one warp: copy the elements recorded in nidx into the element buffer
+  auto issue_v = [&](int tile, int b) {
+    const int nf = faces_of(tile);
+    if (lane < nf) {
+      T* dst = sb + C::E_OFF + (size_t)lane * 2 * EL;
+      bulk_copy_g2s(dst, a.v + a.state_base + nidx[lane][0] * EL, C::EB, &bar[b]);
+      bulk_copy_g2s(dst + EL, a.v + a.state_base + nidx[lane][1] * EL, C::EB, &bar[b]);
+    }
+  };
+  const BasisTab<T>& B = a.basis[P];
+  T* const xv = sb + C::V_OFF + (size_t)lf * 2 * BLK;
+  int it = 0;
+  bool stop = false;
+  if ((int)blockIdx.x < ntiles && threadIdx.x < 32) {
+    issue_q(blockIdx.x, 0);
+    __syncwarp();
+    issue_v(blockIdx.x, 0);
+  }
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const int next = tile + gridDim.x;
+    if (next < ntiles && threadIdx.x < 32) issue_q(next, b ^ 1);
+    const int64_t fidx = (int64_t)tile * FB + lf;
+    const bool valid = fidx < a.n;
+    FaceRec r{};
+    CFaceGeo<T, ND> g{};
+    if (valid) {
+      r = a.recs[fidx];
+      cface_geo<T, ND, P, DIAG>(a, r, t, g);
+    }
+    // every thread waits for the tile's bytes itself (see cface_tma_kernel)
+    const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitLimit);
+    if (!ok) atomicOr(status, 1);
+    if (ok && valid) {
+      // the tangent's compact trace at this thread's point of the master face
+      // and at the same-numbered point of the slave face (slave numbering)
+      const T* el = sb + C::E_OFF + (size_t)lf * 2 * EL;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        T qf[NV], dn[NV];
+        trace_point<T, ND, P, VISC, line_vec_width<T, P, C::NSP, BLK>() < line_vec_width<T, P, C::NSP, EL>()
+                                         ? line_vec_width<T, P, C::NSP, BLK>()
+                                         : line_vec_width<T, P, C::NSP, EL>()>(
+            el + side * EL, B, (side ? r.sf : r.mf) * NFP + t, qf, dn);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          xv[side * BLK + v * NFP + t] = qf[v];
+          if (VISC) xv[side * BLK + (NV + v) * NFP + t] = dn[v];
+        }
+      }
+    }
+    // the face's points are this warp's lanes: its traces are complete here;
+    // the CTA barrier at the end of the previous tile ordered these writes
+    // after every read of the last tile's traces
+    __syncwarp();
+    // this warp is done with the element buffer: the last warp to get here
+    // refills it with the next tile's elements (the fences order the other
+    // warps' reads of the buffer and warp 0's nidx before the copies)
+    int last = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      last = atomicAdd(&done, 1) == C::NW - 1;
+      if (last) {
+        done = 0;   // the next tile's arrivals follow the CTA barrier below
+        __threadfence_block();
+      }
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    __syncwarp();   // the lanes' nidx reads follow lane 0's fence
+    if (last && ok && next < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_v(next, b ^ 1);
+    }
+    if (ok && valid) cface_point<T, ND, P, VISC, DIAG>(a, r, t, g, sb + C::Q_OFF + (size_t)(b * FB + lf) * 2 * BLK,
+                                                        xv, sb + C::Q_OFF + (size_t)(b * FB + lf) * 2 * BLK + BLK,
+                                                        xv + BLK);
+    if (__syncthreads_or(!ok)) {
+      stop = true;
+      break;
+    }
+  }
+  if (stop) {
+    // copies of this and the next tile may still be in flight: wait for both
+    // buffers' current phases, bounded, before the CTA's shared memory goes away
+    mbar_wait(&bar[it & 1], (uint32_t)((it >> 1) & 1), kTmaWaitLimit);
+    mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitLimit);
+  }
+}
+
 }  // namespace frgb
+

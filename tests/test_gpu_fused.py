@@ -239,7 +239,7 @@ def test_default_choice_and_autotune(built):
     ctx.timing(False)
     assert rep.get("cface_jvp_f32", (0,))[0] > 0 and rep.get("vol_jvp_f32", (0,))[0] > 0
     t = ctx.autotune(ctx.pack(torch.from_numpy(q).cuda()))
-    assert t["epb"][21 + 2 * 7 + 1] in (1, 2, 3) and t["epb"][2 * 7 + 1] in (1, 2, 3)
+    assert t["epb"][21 + 2 * 7 + 1] in (1, 2, 3, 4) and t["epb"][2 * 7 + 1] in (1, 2, 3)
 
 
 @pytest.mark.parametrize("name", ["tgv_5_p3", "box_p1_ns", "box_p5_ns", "sheared_box_rotated", "diff_3_p4_roe"])
@@ -265,3 +265,104 @@ def test_tma_staged_faces_match_thread_staged(built, name):
         out[tma] = ctx.unpack(ctx.jvp(qs, vs)).cpu().numpy()
         assert ctx.device_status() == 0
     assert np.array_equal(out[True], out[False])
+
+
+def _vt_cases():
+    out = {"tgv_5_p3": WL["tgv_5_p3"], "box_p1_ns": WL["box_p1_ns"],
+           "vortex2d_rotated_ns": WL["vortex2d_rotated_ns"]}
+    m, q, ph = WL["tgv_5_p3"]
+    out["tgv_5_p3_euler"] = (m, q, dict(ph, mu=0.0))
+    m, q, ph = _sheared_box(3, n=4)
+    rot = [e for e in range(m.n_elem) if ((e % 4) + (e // 4) % 4 + e // 16) % 2 == 0]
+    mr, qr = rotate_elements(m, q, rot)
+    out["box_p3_rotated"] = (mr, qr, ph)
+    return out
+
+
+VT = _vt_cases()
+
+
+def _jvp_choice(ctx, qs, vs, choice):
+    t = ctx.tuning()
+    t["fused_jvp"] = True
+    t["epb"][21 + 2 * 7 + 1] = choice
+    ctx.set_tuning(t)
+    ctx.timing(True)
+    J = ctx.unpack(ctx.jvp(qs, vs)).cpu().numpy()
+    rep, _ = ctx.timing_report()
+    ctx.timing(False)
+    return J, rep
+
+
+@pytest.mark.parametrize("name", list(VT))
+def test_face_kernel_tangent_traces_match_compact_passes(built, name):
+    """The compact face kernel that forms the tangent's traces itself (FP32,
+    tuning slot value 4; 3D p = 1 and 3, 2D p = 3) against the three compact
+    passes: both form the traces with the same explicit fused multiply-adds,
+    so the JVPs agree bit for bit.  The trace pass runs over q only, no
+    bounded wait gave up, and the product meets the oracle at the FP32
+    tolerance (Euler and Navier-Stokes; rotated elements give non-trivial
+    orientation codes between the two sides' point numberings)."""
+    from oracle import linearize as L
+    m, q, ph = VT[name]
+    q = generic_state(q)
+    v = cases.uniform(918, q.size) - 0.5
+    ctx = gpu_ctx(m, ph)
+    qs = ctx.pack(torch.from_numpy(q).cuda(), torch.float32)
+    vs = ctx.pack(torch.from_numpy(v).cuda(), torch.float32)
+    J3, rep3 = _jvp_choice(ctx, qs, vs, 3)
+    assert rep3.get("cface_jvp_f32", (0,))[0] > 0 and "cface_vt_jvp_f32" not in rep3
+    J4, rep4 = _jvp_choice(ctx, qs, vs, 4)
+    assert rep4.get("cface_vt_jvp_f32", (0,))[0] > 0 and "cface_jvp_f32" not in rep4, rep4.keys()
+    assert rep4["ctrace_f32"][0] == rep3["ctrace_f32"][0] // 2
+    assert ctx.device_status() == 0
+    assert np.array_equal(J4, J3)
+    Jref = L.jvp(oracle_fr(m, ph), torch.from_numpy(q), torch.from_numpy(v)).numpy()
+    ok, rel, fs = parity_ok(J4, Jref, m, q, 2e-5)
+    assert ok, (name, rel, fs)
+
+
+@pytest.mark.parametrize("name", ["tgv_5_p3", "box_p5_ns", "diff_3_p4_mu0.05", "vortex_batch_5"])
+def test_face_kernel_tangent_traces_fall_back(built, name):
+    """Where the face kernel cannot form the tangent's traces (FP64, or a
+    degree whose face points straddle warps or whose blocks are not
+    multiples of 16 bytes), slot value 4 runs the three compact passes."""
+    m, q, ph = WL[name]
+    q = generic_state(q)
+    v = cases.uniform(919, q.size) - 0.5
+    ctx = gpu_ctx(m, ph)
+    for dtype in ((torch.float64,) if name == "tgv_5_p3" else (torch.float64, torch.float32)):
+        qs = ctx.pack(torch.from_numpy(q).cuda(), dtype)
+        vs = ctx.pack(torch.from_numpy(v).cuda(), dtype)
+        J3, _ = _jvp_choice(ctx, qs, vs, 3)
+        J4, rep4 = _jvp_choice(ctx, qs, vs, 4)
+        assert not any(k.startswith("cface_vt") for k in rep4), rep4.keys()
+        assert np.array_equal(J4, J3)
+
+
+@pytest.mark.parametrize("rtol", [1e-6, 1e-3])
+def test_face_kernel_tangent_traces_in_gmres(built, rtol):
+    """GMRES with FP32 products (the compact traces of q prepared once per
+    solve, the Krylov column read in place; an FP64 basis at rtol 1e-6, the
+    FP32 basis at 1e-3) takes the same iterates with either compact choice."""
+    m, q, ph = VT["tgv_5_p3"]
+    q = generic_state(q)
+    ctx = gpu_ctx(m, ph)
+    q64 = ctx.pack(torch.from_numpy(q).cuda())
+    b = ctx.pack(torch.from_numpy(cases.uniform(920, q.size) - 0.5).cuda())
+    out = {}
+    for choice in (3, 4):
+        t = ctx.tuning()
+        t["fused_jvp"] = True
+        t["epb"][21 + 2 * 7 + 1] = choice
+        ctx.set_tuning(t)
+        ctx.timing(True)
+        x, st = ctx.gmres(q64, b, sigma=50.0, mode="exact", jv_dtype=torch.float32, m=30, rtol=rtol, max_it=200)
+        rep, _ = ctx.timing_report()
+        ctx.timing(False)
+        assert st["converged"], (choice, st)
+        assert ("cface_vt_jvp_f32" in rep) == (choice == 4), rep.keys()
+        out[choice] = (x.cpu().numpy(), st["iterations"])
+    assert ctx.device_status() == 0
+    assert out[3][1] == out[4][1]
+    assert np.array_equal(out[3][0], out[4][0])

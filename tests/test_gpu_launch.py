@@ -100,6 +100,20 @@ def test_tuning_rejects_bad_entries(built, works):
         ctx.set_tuning({"epb": [-1] + [0] * 41})
     with pytest.raises(FRError):
         ctx.set_tuning({"epb": [0] * 20 + [257] + [0] * 21})
+    # the exact JVP's choice (slot [precision][2][P = 1]) lies in [0, 4]; the
+    # weight model (slot [0][0][P = 1]) in [0, 3]
+    for prec in (0, 1):
+        bad = [0] * 42
+        bad[prec * 21 + 2 * 7 + 1] = 5
+        with pytest.raises(FRError):
+            ctx.set_tuning({"epb": bad})
+        ok = [0] * 42
+        ok[prec * 21 + 2 * 7 + 1] = 4
+        ctx.set_tuning({"epb": ok})
+    bad = [0] * 42
+    bad[1] = 4
+    with pytest.raises(FRError):
+        ctx.set_tuning({"epb": bad})
 
 
 @pytest.mark.parametrize("name", ["cylinder_4x12x2_mixed", "vortex_batch_5", "tgv_5^3_p3"])
