@@ -546,6 +546,12 @@ def main():
     ap.add_argument("--timestep", type=int, default=0,
                     help="instead of the stage benchmark: this many ESDIRK3 time steps of the NACA 0012 "
                          "C-grid with p-adaptation after every step, in both product modes")
+    ap.add_argument("--jvp-choice", default="auto", choices=["auto", "1", "2", "3", "4"],
+                    help="the exact FP32 JVP's kernels for the timed step (auto: the autotuner's choice; 1 fused, "
+                         "2 trace-gradient three passes, 3 compact three passes, 4 compact two passes). The "
+                         "autotuner runs in every process, and under a profiler the launches it does not capture "
+                         "run slower, which can tip a near tie: a profiling run pins the choice of the plain run "
+                         "it is compared with")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -589,6 +595,9 @@ def main():
 
     # launch tuning (elements per CTA, multi-bucket launch), untimed set-up
     tuning = ctx.autotune(qn[:N])
+    if args.jvp_choice != "auto":
+        tuning["epb"][21 + 2 * 7 + 1] = int(args.jvp_choice)
+        ctx.set_tuning(tuning)
     alu = _alu_peaks()
 
     def step(q_in):
@@ -759,6 +768,7 @@ def main():
                        "gmres_loop": "device-driven (rotations and convergence test on the device, iterations "
                                      "launched in batches)" if tuning["device_gmres"] else
                                      "host round trip per iteration",
+                       "jvp_kernels_from": "autotuner" if args.jvp_choice == "auto" else "--jvp-choice",
                        "jvp_kernels_f32": {0: "compact three passes (undecided)", 1: "fused", 2: "trace-gradient three passes",
                                            3: "compact three passes",
                                            4: "compact two passes (the tangent's traces formed in the face kernel)"}[
