@@ -39,6 +39,8 @@ def test_survey_roofline_charges_the_operator_bytes():
     assert r["bytes_per_launch"] == 8 * 3 * N and r["achieved"] == pytest.approx(8 * 3 * N / 0.5e-3 / 1e9)
     assert bench._operator_of("trace_f32") == ("jvp", 4) and bench._operator_of("trace_f64") == ("residual", 8)
     assert bench._operator_of("fused_jvp_f32") == ("jvp", 4) and bench._operator_of("ctrace_f32") == ("jvp", 4)
+    # both compact face kernels of the FP32 JVP charge the JVP's bytes
+    assert bench._operator_of("cface_jvp_f32") == ("jvp", 4) and bench._operator_of("cface_vt_jvp_f32") == ("jvp", 4)
 
 
 def test_double_float_instruction_count_matches_dfma():
